@@ -1,0 +1,60 @@
+"""The oracle against the numbers and claims the paper prints (Sec. II, IV.B).
+
+The fixture tests/golden/paper_constants.txt holds the printed values with
+their citations.
+"""
+
+import os
+
+import numpy as np
+import pytest
+
+import oracle.gs_oracle as O
+from paper_1302_0120_gb300 import synthetic as S
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "paper_constants.txt")
+
+
+def load_constants():
+    out = {}
+    with open(GOLDEN) as f:
+        for line in f:
+            line = line.strip()
+            if not line or line.startswith("#"):
+                continue
+            name, value = line.split()[:2]
+            out[name] = float(value)
+    return out
+
+
+def test_error_tolerances_match_paper():
+    c = load_constants()
+    assert O.TL_LIT == c["t_lit"] and O.TD_DARK == c["t_dark"]
+
+
+def test_single_and_double_precision_share_limits():
+    """Sec. IV.B: SP and DP runs reach the same limit values; the difference
+    is of the order of single-precision accuracy."""
+    I, phi0, iters = S.workload("spots64")
+    r64 = O.gs_run(I, phi0, iters)["r"]
+    r32 = O.gs_run(I, phi0, iters, dtype=np.float32)["r"]
+    rel = np.abs(r32 - r64) / r64
+    assert np.max(rel) <= 1e-5, np.max(rel)
+
+
+@pytest.mark.slow
+def test_gap_floor_scales_with_epsilon():
+    """Sec. IV.B: on a consistent problem with N ~ 1e6 pixels, the gap that
+    finite precision leaves is G_th ~ 1e3 eps (1e-5 in SP, 1e-13 in DP). The
+    unnormalised gap sqrt(N) r^0 at the exact solution is checked to lie within
+    a factor 30 of those floors."""
+    c = load_constants()
+    n = int(round(np.sqrt(c["npix_floor"])))
+    rng = np.random.default_rng(5)
+    phi_t = (rng.random((n, n)) * 2 * np.pi).astype(np.float32)
+    I = O.consistent_target(phi_t)
+    sqn = np.sqrt(I.size)
+    g_dp = sqn * O.gs_run(I, phi_t, 0)["r"][0]
+    g_sp = sqn * O.gs_run(I.astype(np.float32), phi_t, 0, dtype=np.float32)["r"][0]
+    assert c["gap_floor_dp"] / 30 <= g_dp <= 30 * c["gap_floor_dp"], g_dp
+    assert c["gap_floor_sp"] / 30 <= g_sp <= 30 * c["gap_floor_sp"], g_sp
