@@ -1,0 +1,409 @@
+"""Benchmark: milliseconds per 1024x1024 Gerchberg-Saxton phase mask (100 iterations).
+
+One step = one whole mask: target preparation, 100 iterations of Eq. (e:AP)
+(column pass + row pass each), the phase output and the final residual r^K,
+on a synthetic 50-spot target (peaks in [0.5, 1], sigma 1.5 px) with a
+uniform random initial phase. Inputs are resident in HBM; L2 is flushed
+(a 256 MiB write) between timed steps, outside the timed events.
+
+Prints one JSON line (rank 0). ``--impl reference`` times the FP64 CPU oracle
+on the same workload instead (a bounded sample per step, scaled to a mask).
+
+Multi-GPU: masks are independent, so N ranks run N replicas with no
+collective on the data path; the timing takes the max over ranks.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+WORKLOAD = "spots1024"
+METRIC = "ms per 1024² phase mask (100 GS iters) at matched residual; p99 latency"
+UNIT = "ms/mask"
+# Algorithmic DRAM bytes per pixel of one mask of K iterations:
+# A0 read I (4); amplitude: read I (4) + write m (4); init: read phi (4) + write B (8);
+# per iteration 36 (column pass 20, row pass 16); phase out (4); final residual pass 12.
+BYTES_PER_PX_FIXED = 4 + 8 + 12 + 4 + 12
+BYTES_PER_PX_ITER = 36
+# Algorithmic FLOPs per iteration: two 2D FFTs at 5 N log2 N each + ~20 N for
+# the projections and gap sums.
+FLOPS_PROJ_PER_PX = 20
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), float(d.get("sm_max_mhz", 2070.0)), "measured"
+    except Exception:
+        return 6800.0, 2070.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled while the GPU is busy."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "20"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[3:7]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        return {
+            "sm_mhz": statistics.median(sm) if sm else None,
+            "sm_max_mhz": max(smax) if smax else None,
+            "reasons": sorted(reasons),
+            "samples": len(sm),
+        }
+
+
+def dist_setup(backend):
+    import torch.distributed as dist
+
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    if ws > 1 and not dist.is_initialized():
+        dist.init_process_group(backend=backend)
+    rank = dist.get_rank() if ws > 1 else 0
+    return rank, ws
+
+
+def max_over_ranks(x: float, ws: int, device=None) -> float:
+    if ws <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(ws: int):
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+def oracle_mask_ms(I, phi0, iters_total, sample_iters):
+    """Time the oracle on `sample_iters` iterations and scale to a mask of
+    `iters_total` iterations: t(mask) = t(0) + iters_total * (t(k) - t(0)) / k."""
+    import oracle.gs_oracle as O
+
+    t0 = time.perf_counter()
+    O.gs_run(I, phi0, 0)
+    t_zero = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    O.gs_run(I, phi0, sample_iters)
+    t_k = time.perf_counter() - t0
+    per_iter = max(t_k - t_zero, 1e-9) / sample_iters
+    return 1e3 * (t_zero + iters_total * per_iter), t_zero + t_k
+
+
+def cpu_baseline(I, phi0, iters, budget_s=12.0):
+    import oracle.gs_oracle as O
+
+    # estimate the cost of one iteration, then fill the budget
+    _, spent = oracle_mask_ms(I, phi0, iters, 1)
+    k = int(max(1, min(iters, budget_s / max(spent, 1e-3))))
+    ms, _ = oracle_mask_ms(I, phi0, iters, k)
+    return {
+        "value": round(ms, 3),
+        "unit": UNIT,
+        "cores": O.WORKERS,
+        "kind": "oracle",
+        "sample": f"FP64 oracle on the {WORKLOAD} target: 0 and {k} iterations timed, scaled to {iters} "
+                  f"iterations; FFT by scipy/pocketfft with {O.WORKERS} threads, elementwise numpy on 1",
+    }
+
+
+def run_reference(args):
+    """The oracle arm: FP64 CPU oracle, same workload and metric."""
+    rank, ws = dist_setup("gloo")
+    if rank != 0:
+        return 0
+    from paper_1302_0120_gb300 import synthetic as S
+    import oracle.gs_oracle as O
+
+    I, phi0, iters = S.workload(WORKLOAD, seed=0)
+    sample = max(1, args.ref_sample_iters)
+    for _ in range(args.warmup):
+        oracle_mask_ms(I, phi0, iters, sample)
+    times = []
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        ms, _ = oracle_mask_ms(I, phi0, iters, sample)
+        times.append(ms)
+    wall = time.perf_counter() - t0
+    value = statistics.mean(times)
+    line = {
+        "impl": "reference",
+        "metric": METRIC,
+        "value": round(value, 3),
+        "unit": UNIT,
+        "n_gpus": args.gpus,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(value, 3),
+        "higher_is_better": False,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": f"{WORKLOAD}: 1024x1024, 50 Gaussian spots, 100 GS iterations, final residual",
+                   "flush_l2": "n/a (CPU)"},
+        "cpu_baseline": {"value": round(value, 3), "unit": UNIT, "cores": O.WORKERS, "kind": "oracle",
+                         "sample": f"per step: 0 and {sample} oracle iterations timed, scaled to {iters}"},
+        "e2e": {"value": round(value, 3), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "wall_s": round(wall, 3),
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def run_gpu(args):
+    import numpy as np
+    import torch
+
+    rank, ws = dist_setup("nccl")
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    from paper_1302_0120_gb300 import GerchbergSaxton, build_lib
+    from paper_1302_0120_gb300 import synthetic as S
+
+    build_lib.build()
+    I_np, phi_np, iters = S.workload(WORKLOAD, seed=rank)
+    ny, nx = I_np.shape
+    n = nx * ny
+    stream = torch.cuda.current_stream(dev)
+    gs = GerchbergSaxton(nx, ny, final_residual=True, stream=stream)
+    if args.grid:
+        gs.set_grid(args.grid)
+    I = torch.from_numpy(I_np).to(dev)
+    phi0 = torch.from_numpy(phi_np).to(dev)
+    phi_out = torch.empty_like(phi0)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    def step():
+        return gs.run(I, phi0, iters, phase_out=phi_out)
+
+    # warm-up
+    for _ in range(args.warmup):
+        flush.zero_()
+        step()
+    st = gs.status()
+    if st != 0:
+        raise RuntimeError(f"device status {st}")
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)  # let the sampler start
+    # keep the GPU busy while the sampler spins up, untimed
+    for _ in range(max(1, args.warmup)):
+        flush.zero_()
+        step()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    barrier(ws)
+    torch.cuda.synchronize(dev)
+    t_wall = time.perf_counter()
+    for k in range(args.steps):
+        flush.zero_()
+        starts[k].record(stream)
+        _, r, g = step()
+        ends[k].record(stream)
+    torch.cuda.synchronize(dev)
+    barrier(ws)
+    wall = time.perf_counter() - t_wall
+    clocks = sampler.stop()
+    st = gs.status()
+    if st != 0:
+        raise RuntimeError(f"device status {st}")
+    per = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    mean_ms = statistics.mean(per)
+    total_ms = max_over_ranks(sum(per), ws, dev)
+    value = total_ms / (args.steps * ws)
+    per_sorted = sorted(per)
+    p50 = per_sorted[len(per) // 2]
+    p99 = per_sorted[min(len(per) - 1, int(math.ceil(0.99 * len(per))) - 1)]
+
+    # final residual of the timed run, for the "matched residual" claim
+    r_final = float(r[-1].item())
+
+    # end to end through the public host-pointer call (gs_run_host)
+    pin_I = torch.from_numpy(I_np).pin_memory()
+    pin_phi = torch.from_numpy(phi_np).pin_memory()
+    pin_out = torch.empty_like(pin_phi).pin_memory()
+    r_h = np.empty(iters + 1, np.float64)
+    g_h = np.empty(iters, np.float64)
+    from paper_1302_0120_gb300 import _binding as B
+
+    def e2e_step():
+        rc = B.gs_run_host(gs.handle, pin_I.data_ptr(), pin_phi.data_ptr(), iters, pin_out.data_ptr(),
+                           r_h.ctypes.data, g_h.ctypes.data)
+        if rc != 0:
+            raise RuntimeError(f"gs_run_host: {B.gs_strerror(rc)}")
+
+    for _ in range(args.warmup):
+        flush.zero_()
+        torch.cuda.synchronize(dev)
+        e2e_step()
+    e2e_times = []
+    barrier(ws)
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        e2e_step()
+        e2e_times.append(1e3 * (time.perf_counter() - t0))
+    e2e_total = max_over_ranks(sum(e2e_times), ws, dev)
+    e2e_value = e2e_total / (args.steps * ws)
+    h2d = 2 * n * 4
+    d2h = n * 4 + (iters + 1) * 8 + iters * 8
+
+    # roofline of the dominant kernel (the persistent iteration kernel: one launch per mask)
+    hbm_peak, sm_max, peak_kind = peaks()
+    bytes_alg = (BYTES_PER_PX_FIXED + BYTES_PER_PX_ITER * iters) * n
+    achieved = bytes_alg / (mean_ms * 1e-3) / 1e9
+    flops_alg = iters * (2 * 5 * n * math.log2(n) + FLOPS_PROJ_PER_PX * n)
+    alu_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12  # FP32 FMA lanes x 2 flops x max clock
+    achieved_tf = flops_alg / (mean_ms * 1e-3) / 1e12
+    traffic = None
+    tpath = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(tpath):
+        try:
+            with open(tpath) as f:
+                traffic = json.load(f).get(WORKLOAD)
+        except Exception:
+            traffic = None
+
+    out = {
+        "metric": METRIC,
+        "value": round(value, 4),
+        "unit": UNIT,
+        "n_gpus": ws,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(mean_ms, 4),
+        "higher_is_better": False,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic",
+        "config": {
+            "workload": f"{WORKLOAD}: 1024x1024, 50 Gaussian spots (sigma 1.5 px, peaks U[0.5,1], DC avoided), "
+                        f"uniform random phase, {iters} GS iterations + final residual",
+            "flush_l2": "256 MiB write between timed steps (outside the events)",
+            "grid_ctas": gs.grid,
+            "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
+        },
+        "p50_ms": round(p50, 4),
+        "p99_ms": round(p99, 4),
+        "gs_iters_per_s": round(iters / (mean_ms * 1e-3), 1),
+        "final_residual": r_final,
+        "e2e": {"value": round(e2e_value, 4), "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": args.steps * ((iters + 127) // 128 if iters else 1),
+        "roofline": {
+            "bound": "hbm",
+            "achieved": round(achieved, 1),
+            "peak": hbm_peak,
+            "unit": "GB/s",
+            "frac": round(achieved / hbm_peak, 4),
+            "traffic": traffic,
+            "peak_kind": peak_kind,
+            "alu_achieved_tflops": round(achieved_tf, 2),
+            "alu_peak_tflops": round(alu_peak, 1),
+            "alu_frac": round(achieved_tf / alu_peak, 4),
+        },
+        "clocks": clocks,
+        "wall_s": round(wall, 3),
+    }
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(I_np, phi_np, iters, budget_s=args.cpu_budget_s)
+    if rank == 0:
+        print(json.dumps(out))
+    gs.close()
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+    return 0
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
+    ap.add_argument("--grid", type=int, default=0, help="blocks of the iteration kernel (0 = automatic)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-budget-s", type=float, default=12.0)
+    ap.add_argument("--ref-sample-iters", type=int, default=2)
+    args = ap.parse_args(argv)
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,167 @@
+/*
+ * gs.h -- C ABI of the GB300 Gerchberg-Saxton phase-mask library.
+ *
+ * The library computes a phase-only mask for a spatial light modulator (SLM)
+ * whose Fourier-transform intensity reproduces a target optical stimulation
+ * pattern (OSP), by the method of alternating projections (Gerchberg-Saxton)
+ * of Kramer, Hagemann and Luke, "Real-Time Phase Masks for Interactive
+ * Stimulation of Optogenetic Neurons", Sec. II:
+ *
+ *   S = { u : |u_jk| = 1 }                 (Eq. slm-constraint, unit amplitude p = 1)
+ *   M = { u : |(F u)_jk| = m_jk }          (Eq. pattern-constraint)
+ *   u^{nu+1} = P_S P_M u^nu                (Eq. e:AP, projections Eqs. e:PS, e:PM, e:Mhat)
+ *
+ * Conventions shared by every entry point:
+ *   - A grid is nx x ny pixels stored row-major as [ny][nx] (pixel (j, k) of
+ *     the paper, j < nx along a row, at index k*nx + j: the paper's
+ *     lexicographic pixel index, Sec. III).
+ *   - F is the 2D DFT with kernel exp(-2 pi i (j k1/nx + k k2/ny)). The target
+ *     intensity I is given in DFT order (zero frequency at [0][0]).
+ *   - The OSP amplitude is m = sqrt(I) scaled so that sum m^2 = N = nx*ny
+ *     (m is an amplitude, Eq. pattern-constraint; the scale, which the paper
+ *     leaves open, does not change the iterates).
+ *   - A pixel whose value is exactly zero gets phase 0 in either projection
+ *     (the paper allows any phase there, Eqs. e:PS and e:Mhat).
+ *   - Residuals are the normalised gaps of Eq. (gap-error):
+ *       r^nu = || |F u^nu|/sqrt(N) - m ||_2 / sqrt(N)   (distance of u^nu to M)
+ *       g^nu = || P_M u^nu - P_S P_M u^nu ||_2 / sqrt(N) (distance of P_M u^nu to S)
+ *     reduced in FP64. The field itself is computed in FP32.
+ *   - nx and ny must be powers of two in [32, 4096].
+ *
+ * Memory and ordering:
+ *   - Pointers named "device" are CUDA device pointers owned by the caller;
+ *     the library never frees them. Pointers named "host" are host memory
+ *     owned by the caller (pinned memory gives asynchronous copies).
+ *   - All work is enqueued on the context's CUDA stream and is asynchronous
+ *     unless stated otherwise. Results are valid once that stream has
+ *     synchronised (e.g. through gs_status).
+ *   - A context is not thread-safe; use one context per host thread.
+ *
+ * Errors: every call returns an int status, GS_OK on success. No exception
+ * crosses the ABI. Arguments are validated before anything is enqueued.
+ * Errors detected on the device (a non-finite or all-zero target, a barrier
+ * that timed out) are recorded in the context and returned by gs_status.
+ */
+#ifndef GS_GB300_H
+#define GS_GB300_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  GS_OK = 0,
+  GS_EINVAL = -1,   /* invalid argument: null pointer, unsupported size, iters < 0 */
+  GS_ENOMEM = -2,   /* device or host allocation failed */
+  GS_ECUDA = -3,    /* a CUDA runtime call failed (no device, launch failure) */
+  GS_ETIMEOUT = -4, /* a device-side wait gave up (grid barrier did not complete) */
+  GS_ENUMERIC = -5  /* target intensity is non-finite, negative or sums to zero */
+};
+
+/* Flags for gs_create. */
+enum {
+  /* After the last iteration also compute r^K (one forward column pass). */
+  GS_FINAL_RESIDUAL = 1u
+};
+
+typedef struct gs_ctx gs_ctx;
+
+/*
+ * gs_create -- allocate a context for nx x ny grids.
+ *
+ * Operation: none yet; sizes the workspace for Eq. (e:AP) on an nx x ny SLM
+ * (Sec. II: "n_x, n_y the respective number of pixels").
+ *   out     host pointer that receives the context (set to NULL on failure).
+ *   nx, ny  powers of two in [32, 4096].
+ *   flags   GS_* flags (GS_FINAL_RESIDUAL).
+ *   stream  a cudaStream_t, or NULL for the legacy default stream. All later
+ *           work of this context is enqueued on it.
+ * The context owns its device workspace (gs_workspace_bytes bytes): the field,
+ * the scaled amplitude, per-block FP64 partial sums, twiddle tables, a
+ * barrier counter and a status word. Synchronous (allocates and uploads).
+ * Returns GS_EINVAL for bad sizes or a NULL out, GS_ENOMEM, GS_ECUDA.
+ */
+int gs_create(gs_ctx** out, int nx, int ny, unsigned flags, void* stream);
+
+/*
+ * gs_run -- run K iterations of the method of alternating projections.
+ *
+ * Operation: Eq. (e:AP) from u^0 = exp(i phase_in), with P_S (Eq. e:PS, p = 1)
+ * and P_M (Eqs. e:PM, e:Mhat, m from target_intensity); outputs the phase of
+ * u^K and the gaps of Eq. (gap-error).
+ *   target_intensity  device, float [ny][nx], DFT order, >= 0, finite, not all 0.
+ *   phase_in          device, float [ny][nx], radians. May alias phase_out
+ *                     (warm start from a previous mask).
+ *   iters             K >= 0. K == 0 computes r^0 only (with GS_FINAL_RESIDUAL)
+ *                     and writes phase_out = arg exp(i phase_in).
+ *   phase_out         device, float [ny][nx], arg u^K in (-pi, pi].
+ *   residual_out      device, double[K+1] (r^0..r^K) with GS_FINAL_RESIDUAL,
+ *                     else double[K] (r^0..r^{K-1}); or NULL.
+ *   object_gap_out    device, double[K] (g^0..g^{K-1}), or NULL.
+ * Asynchronous on the context stream. Returns GS_EINVAL on NULL context or
+ * arrays, iters < 0; GS_ECUDA if a launch fails. Device-side errors are
+ * reported by gs_status; on GS_ENUMERIC the phase output is left untouched and
+ * residuals are set to NaN.
+ */
+int gs_run(gs_ctx* c, const float* target_intensity, const float* phase_in, int iters,
+           float* phase_out, double* residual_out, double* object_gap_out);
+
+/*
+ * gs_run_host -- gs_run on HOST buffers: end-to-end call including transfers.
+ *
+ * Same operation and argument meaning as gs_run, but every array is host
+ * memory (pinned memory gives asynchronous copies): the target and the
+ * initial phase are copied to context-owned device buffers, the iteration
+ * runs, and the phase and residuals are copied back. Synchronous: returns
+ * after the results are in host memory, with the device status folded into
+ * the return value (GS_ENUMERIC, GS_ETIMEOUT as for gs_status).
+ */
+int gs_run_host(gs_ctx* c, const float* target_intensity, const float* phase_in, int iters,
+                float* phase_out, double* residual_out, double* object_gap_out);
+
+/*
+ * gs_status -- wait for the context stream and return the device status.
+ *
+ * Synchronises the context stream, then returns GS_OK, GS_ENUMERIC or
+ * GS_ETIMEOUT for the runs enqueued since the previous gs_status (the first
+ * error wins), or GS_ECUDA if the stream reports an error. Clears the status.
+ */
+int gs_status(gs_ctx* c);
+
+/*
+ * gs_set_grid -- tuning knob: number of thread blocks of the iteration kernel.
+ *
+ * ctas = 0 restores the automatic choice. A value above what the device can
+ * keep resident at once is clamped. Host-only; takes effect at the next run.
+ * Returns GS_EINVAL for a NULL context or ctas < 0.
+ */
+int gs_set_grid(gs_ctx* c, int ctas);
+
+/*
+ * gs_get_grid -- the number of thread blocks the next run will launch.
+ * Writes it to *ctas (host). Returns GS_EINVAL for NULL arguments.
+ */
+int gs_get_grid(gs_ctx* c, int* ctas);
+
+/*
+ * gs_destroy -- free the context and its workspace. Synchronises the
+ * context stream first. NULL is accepted (no-op). Returns GS_OK or GS_ECUDA.
+ */
+int gs_destroy(gs_ctx* c);
+
+/* gs_strerror -- static English text for a status code (never NULL). */
+const char* gs_strerror(int code);
+
+/*
+ * gs_workspace_bytes -- device bytes a context for nx x ny allocates
+ * (for admission by memory). Pure host computation; 0 for invalid sizes.
+ */
+size_t gs_workspace_bytes(int nx, int ny, unsigned flags);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GS_GB300_H */

@@ -1,0 +1,27 @@
+"""GB300 (sm_103a) Gerchberg-Saxton phase masks.
+
+The method of alternating projections of Kramer, Hagemann and Luke,
+"Real-Time Phase Masks for Interactive Stimulation of Optogenetic Neurons",
+as a C-ABI CUDA library (include/gs.h) with a thin Python binding.
+"""
+
+from ._binding import (  # noqa: F401
+    GS_ECUDA,
+    GS_EINVAL,
+    GS_ENOMEM,
+    GS_ENUMERIC,
+    GS_ETIMEOUT,
+    GS_FINAL_RESIDUAL,
+    GS_OK,
+    GSError,
+    gs_create,
+    gs_destroy,
+    gs_get_grid,
+    gs_run,
+    gs_run_host,
+    gs_set_grid,
+    gs_status,
+    gs_strerror,
+    gs_workspace_bytes,
+)
+from .solver import GerchbergSaxton  # noqa: F401

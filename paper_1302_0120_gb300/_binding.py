@@ -1,0 +1,116 @@
+"""ctypes binding of the C ABI declared in include/gs.h.
+
+Argument marshalling only: every function here forwards to the CUDA library
+of the same name. The library must have been built (build_lib.build()); if it
+is missing the import of the symbols fails loudly. There is no CPU fallback.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+
+from .build_lib import LIB_PATH
+
+GS_OK = 0
+GS_EINVAL = -1
+GS_ENOMEM = -2
+GS_ECUDA = -3
+GS_ETIMEOUT = -4
+GS_ENUMERIC = -5
+
+GS_FINAL_RESIDUAL = 1
+
+_c_int = ctypes.c_int
+_c_uint = ctypes.c_uint
+_vp = ctypes.c_void_p
+
+# name -> (restype, argtypes), mirroring include/gs.h
+SIGNATURES = {
+    "gs_create": (_c_int, [ctypes.POINTER(_vp), _c_int, _c_int, _c_uint, _vp]),
+    "gs_run": (_c_int, [_vp, _vp, _vp, _c_int, _vp, _vp, _vp]),
+    "gs_run_host": (_c_int, [_vp, _vp, _vp, _c_int, _vp, _vp, _vp]),
+    "gs_status": (_c_int, [_vp]),
+    "gs_set_grid": (_c_int, [_vp, _c_int]),
+    "gs_get_grid": (_c_int, [_vp, ctypes.POINTER(_c_int)]),
+    "gs_destroy": (_c_int, [_vp]),
+    "gs_strerror": (ctypes.c_char_p, [_c_int]),
+    "gs_workspace_bytes": (ctypes.c_size_t, [_c_int, _c_int, _c_uint]),
+}
+
+_lib = None
+
+
+class GSError(RuntimeError):
+    def __init__(self, code: int, what: str = ""):
+        self.code = code
+        super().__init__(f"{what}: {gs_strerror(code)} ({code})" if what else f"{gs_strerror(code)} ({code})")
+
+
+def lib() -> ctypes.CDLL:
+    """The loaded CUDA library. Raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(
+                f"{LIB_PATH} is missing: build it with paper_1302_0120_gb300.build_lib.build() "
+                "(requires nvcc); there is no CPU fallback"
+            )
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def gs_strerror(code: int) -> str:
+    return lib().gs_strerror(int(code)).decode()
+
+
+def gs_workspace_bytes(nx: int, ny: int, flags: int = GS_FINAL_RESIDUAL) -> int:
+    return int(lib().gs_workspace_bytes(int(nx), int(ny), int(flags)))
+
+
+def gs_create(nx: int, ny: int, flags: int = GS_FINAL_RESIDUAL, stream: int | None = None) -> int:
+    """Create a context; returns its handle (an int). Raises GSError."""
+    h = _vp()
+    rc = lib().gs_create(ctypes.byref(h), int(nx), int(ny), int(flags), _vp(stream or 0))
+    if rc != GS_OK:
+        raise GSError(rc, "gs_create")
+    return h.value
+
+
+def gs_run(ctx: int, target_intensity: int, phase_in: int, iters: int, phase_out: int,
+           residual_out: int = 0, object_gap_out: int = 0) -> int:
+    """Enqueue a run on device pointers; returns the status code."""
+    return lib().gs_run(_vp(ctx), _vp(target_intensity), _vp(phase_in), int(iters), _vp(phase_out),
+                        _vp(residual_out or 0), _vp(object_gap_out or 0))
+
+
+def gs_run_host(ctx: int, target_intensity: int, phase_in: int, iters: int, phase_out: int,
+                residual_out: int = 0, object_gap_out: int = 0) -> int:
+    """Run on host pointers (synchronous); returns the status code."""
+    return lib().gs_run_host(_vp(ctx), _vp(target_intensity), _vp(phase_in), int(iters), _vp(phase_out),
+                             _vp(residual_out or 0), _vp(object_gap_out or 0))
+
+
+def gs_status(ctx: int) -> int:
+    return lib().gs_status(_vp(ctx))
+
+
+def gs_set_grid(ctx: int, ctas: int) -> int:
+    return lib().gs_set_grid(_vp(ctx), int(ctas))
+
+
+def gs_get_grid(ctx: int) -> int:
+    out = _c_int(0)
+    rc = lib().gs_get_grid(_vp(ctx), ctypes.byref(out))
+    if rc != GS_OK:
+        raise GSError(rc, "gs_get_grid")
+    return out.value
+
+
+def gs_destroy(ctx: int) -> int:
+    return lib().gs_destroy(_vp(ctx))

@@ -1,0 +1,314 @@
+// gs_api.cu -- the C ABI: context, workspace, validation and launches.
+//
+// Host code only. Every entry point validates its arguments before touching
+// CUDA, returns a GS_* status and lets no exception escape.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "gs.h"
+#include "gs_internal.h"
+
+namespace {
+
+constexpr size_t kAlign = 256;
+
+size_t align_up(size_t x) { return (x + kAlign - 1) & ~(kAlign - 1); }
+
+bool valid_dim(int n) { return n >= 32 && n <= 4096 && (n & (n - 1)) == 0; }
+
+int ilog2i(int n) {
+  int l = 0;
+  while ((1 << l) < n) ++l;
+  return l;
+}
+
+// Offsets of the sub-buffers of one workspace allocation.
+struct Layout {
+  size_t B, mT, partials, twx, twy, bar, status, abort_flag, dI, dphi, total;
+};
+
+Layout make_layout(int nx, int ny) {
+  const size_t n = static_cast<size_t>(nx) * ny;
+  Layout L{};
+  size_t o = 0;
+  L.B = o;          o = align_up(o + n * sizeof(float2));
+  L.mT = o;         o = align_up(o + n * sizeof(float));
+  L.partials = o;   o = align_up(o + static_cast<size_t>(gsk::kSlots) * gsk::kMaxGrid * sizeof(double));
+  L.twx = o;        o = align_up(o + static_cast<size_t>(nx) * sizeof(float2));
+  L.twy = o;        o = align_up(o + static_cast<size_t>(ny) * sizeof(float2));
+  L.bar = o;        o = align_up(o + sizeof(unsigned));
+  L.status = o;     o = align_up(o + sizeof(int));
+  L.abort_flag = o; o = align_up(o + sizeof(int));
+  L.dI = o;         o = align_up(o + n * sizeof(float));
+  L.dphi = o;       o = align_up(o + n * sizeof(float));
+  L.total = o;
+  return L;
+}
+
+// W_n^k = exp(-2 pi i k / n) for k < n, computed in double and rounded once;
+// points on the eight octant directions are set exactly.
+std::vector<float2> twiddles(int n) {
+  std::vector<float2> w(n);
+  const double h = std::sqrt(0.5);
+  const double oc[8] = {1.0, h, 0.0, -h, -1.0, -h, 0.0, h};
+  const double os[8] = {0.0, h, 1.0, h, 0.0, -h, -1.0, -h};
+  for (int k = 0; k < n; ++k) {
+    double c, s;
+    if ((8LL * k) % n == 0) {
+      const int o = static_cast<int>((8LL * k) / n);
+      c = oc[o];
+      s = os[o];
+    } else {
+      const double a = 2.0 * M_PI * static_cast<double>(k) / n;
+      c = std::cos(a);
+      s = std::sin(a);
+    }
+    w[k] = make_float2(static_cast<float>(c), static_cast<float>(-s));
+  }
+  return w;
+}
+
+}  // namespace
+
+struct gs_ctx {
+  int nx = 0, ny = 0;
+  unsigned flags = 0;
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  int num_sms = 0;
+  int blocks_per_sm = 0;
+  int grid_override = 0;
+  unsigned extra_arrivals = 0;
+  Layout L{};
+  unsigned char* ws = nullptr;
+  double* dres = nullptr;  // device residual staging for gs_run_host
+  size_t dres_cap = 0;     // doubles
+};
+
+namespace {
+
+template <typename T>
+T* at(gs_ctx* c, size_t off) {
+  return reinterpret_cast<T*>(c->ws + off);
+}
+
+int max_grid(const gs_ctx* c) {
+  int m = c->num_sms * c->blocks_per_sm;
+  if (m > gsk::kMaxGrid) m = gsk::kMaxGrid;
+  return m < 1 ? 1 : m;
+}
+
+int choose_grid(const gs_ctx* c) {
+  const int cap = max_grid(c);
+  int g;
+  if (c->grid_override > 0) {
+    g = c->grid_override;
+  } else {
+    const long long n = static_cast<long long>(c->nx) * c->ny;
+    g = static_cast<int>(n / 4096);
+  }
+  if (g > cap) g = cap;
+  if (g < 1) g = 1;
+  return g;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* gs_strerror(int code) {
+  switch (code) {
+    case GS_OK: return "success";
+    case GS_EINVAL: return "invalid argument";
+    case GS_ENOMEM: return "out of memory";
+    case GS_ECUDA: return "CUDA runtime error";
+    case GS_ETIMEOUT: return "device-side wait timed out";
+    case GS_ENUMERIC: return "target intensity is non-finite, negative or zero";
+    default: return "unknown status";
+  }
+}
+
+size_t gs_workspace_bytes(int nx, int ny, unsigned flags) {
+  (void)flags;
+  if (!valid_dim(nx) || !valid_dim(ny)) return 0;
+  return make_layout(nx, ny).total;
+}
+
+int gs_create(gs_ctx** out, int nx, int ny, unsigned flags, void* stream) {
+  if (out == nullptr) return GS_EINVAL;
+  *out = nullptr;
+  if (!valid_dim(nx) || !valid_dim(ny)) return GS_EINVAL;
+  if ((flags & ~static_cast<unsigned>(GS_FINAL_RESIDUAL)) != 0) return GS_EINVAL;
+  gs_ctx* c = new (std::nothrow) gs_ctx();
+  if (c == nullptr) return GS_ENOMEM;
+  c->nx = nx;
+  c->ny = ny;
+  c->flags = flags;
+  c->stream = static_cast<cudaStream_t>(stream);
+  c->L = make_layout(nx, ny);
+  if (cudaGetDevice(&c->device) != cudaSuccess ||
+      cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess ||
+      gsk::iteration_occupancy(nx, ny, &c->blocks_per_sm) != cudaSuccess || c->blocks_per_sm < 1) {
+    cudaGetLastError();
+    delete c;
+    return GS_ECUDA;
+  }
+  if (cudaMalloc(&c->ws, c->L.total) != cudaSuccess) {
+    cudaGetLastError();
+    delete c;
+    return GS_ENOMEM;
+  }
+  const std::vector<float2> wx = twiddles(nx);
+  const std::vector<float2> wy = twiddles(ny);
+  bool ok = cudaMemcpy(c->ws + c->L.twx, wx.data(), nx * sizeof(float2), cudaMemcpyHostToDevice) == cudaSuccess &&
+            cudaMemcpy(c->ws + c->L.twy, wy.data(), ny * sizeof(float2), cudaMemcpyHostToDevice) == cudaSuccess &&
+            cudaMemset(c->ws + c->L.bar, 0, c->L.dI - c->L.bar) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    cudaFree(c->ws);
+    delete c;
+    return GS_ECUDA;
+  }
+  *out = c;
+  return GS_OK;
+}
+
+int gs_run(gs_ctx* c, const float* target_intensity, const float* phase_in, int iters, float* phase_out,
+           double* residual_out, double* object_gap_out) {
+  if (c == nullptr || target_intensity == nullptr || phase_in == nullptr || phase_out == nullptr || iters < 0)
+    return GS_EINVAL;
+  const int grid = choose_grid(c);
+  gsk::Params p{};
+  p.nx = c->nx;
+  p.ny = c->ny;
+  p.lognx = ilog2i(c->nx);
+  p.logny = ilog2i(c->ny);
+  p.B = at<float2>(c, c->L.B);
+  p.mT = at<float>(c, c->L.mT);
+  p.I = target_intensity;
+  p.phi_in = phase_in;
+  p.phi_out = phase_out;
+  p.partials = at<double>(c, c->L.partials);
+  p.r_out = residual_out;
+  p.g_out = object_gap_out;
+  p.twx = at<float2>(c, c->L.twx);
+  p.twy = at<float2>(c, c->L.twy);
+  p.bar = at<unsigned>(c, c->L.bar);
+  p.status = at<int>(c, c->L.status);
+  p.abort_flag = at<int>(c, c->L.abort_flag);
+  p.iters = iters;
+  p.final_resid = (c->flags & GS_FINAL_RESIDUAL) ? 1 : 0;
+  p.extra_arrivals = c->extra_arrivals;
+  const double n = static_cast<double>(c->nx) * c->ny;
+  p.inv_sqrt_n = static_cast<float>(1.0 / std::sqrt(n));
+  p.inv_n = 1.0 / n;
+  if (cudaMemsetAsync(p.abort_flag, 0, sizeof(int), c->stream) != cudaSuccess) {
+    cudaGetLastError();
+    return GS_ECUDA;
+  }
+  int it0 = 0;
+  do {
+    int it1 = it0 + gsk::kMaxIterPerLaunch;
+    if (it1 > iters) it1 = iters;
+    p.it0 = it0;
+    p.it1 = it1;
+    p.do_init = (it0 == 0) ? 1 : 0;
+    p.do_final = (it1 == iters) ? 1 : 0;
+    if (cudaMemsetAsync(p.bar, 0, sizeof(unsigned), c->stream) != cudaSuccess ||
+        gsk::launch_iterations(p, grid, c->stream) != cudaSuccess) {
+      cudaGetLastError();
+      return GS_ECUDA;
+    }
+    it0 = it1;
+  } while (it0 < iters);
+  return GS_OK;
+}
+
+int gs_status(gs_ctx* c) {
+  if (c == nullptr) return GS_EINVAL;
+  if (cudaStreamSynchronize(c->stream) != cudaSuccess) {
+    cudaGetLastError();
+    return GS_ECUDA;
+  }
+  int st = 0;
+  int* dst = at<int>(c, c->L.status);
+  if (cudaMemcpyAsync(&st, dst, sizeof(int), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
+      cudaMemsetAsync(dst, 0, sizeof(int), c->stream) != cudaSuccess ||
+      cudaStreamSynchronize(c->stream) != cudaSuccess) {
+    cudaGetLastError();
+    return GS_ECUDA;
+  }
+  return st;
+}
+
+int gs_run_host(gs_ctx* c, const float* target_intensity, const float* phase_in, int iters, float* phase_out,
+                double* residual_out, double* object_gap_out) {
+  if (c == nullptr || target_intensity == nullptr || phase_in == nullptr || phase_out == nullptr || iters < 0)
+    return GS_EINVAL;
+  const size_t n = static_cast<size_t>(c->nx) * c->ny;
+  const size_t nres = static_cast<size_t>(iters) + 1;
+  const size_t need = nres + static_cast<size_t>(iters);
+  if (c->dres_cap < need) {
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) {
+      cudaGetLastError();
+      return GS_ECUDA;
+    }
+    cudaFree(c->dres);
+    c->dres = nullptr;
+    c->dres_cap = 0;
+    if (cudaMalloc(&c->dres, need * sizeof(double)) != cudaSuccess) {
+      cudaGetLastError();
+      return GS_ENOMEM;
+    }
+    c->dres_cap = need;
+  }
+  float* dI = at<float>(c, c->L.dI);
+  float* dphi = at<float>(c, c->L.dphi);
+  double* dr = residual_out ? c->dres : nullptr;
+  double* dg = object_gap_out ? c->dres + nres : nullptr;
+  if (cudaMemcpyAsync(dI, target_intensity, n * sizeof(float), cudaMemcpyHostToDevice, c->stream) != cudaSuccess ||
+      cudaMemcpyAsync(dphi, phase_in, n * sizeof(float), cudaMemcpyHostToDevice, c->stream) != cudaSuccess) {
+    cudaGetLastError();
+    return GS_ECUDA;
+  }
+  int rc = gs_run(c, dI, dphi, iters, dphi, dr, dg);
+  if (rc != GS_OK) return rc;
+  const size_t nr = static_cast<size_t>(iters) + ((c->flags & GS_FINAL_RESIDUAL) ? 1 : 0);
+  if (cudaMemcpyAsync(phase_out, dphi, n * sizeof(float), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
+      (dr && nr && cudaMemcpyAsync(residual_out, dr, nr * sizeof(double), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess) ||
+      (dg && iters && cudaMemcpyAsync(object_gap_out, dg, iters * sizeof(double), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess)) {
+    cudaGetLastError();
+    return GS_ECUDA;
+  }
+  return gs_status(c);
+}
+
+int gs_set_grid(gs_ctx* c, int ctas) {
+  if (c == nullptr || ctas < 0) return GS_EINVAL;
+  c->grid_override = ctas;
+  return GS_OK;
+}
+
+int gs_get_grid(gs_ctx* c, int* ctas) {
+  if (c == nullptr || ctas == nullptr) return GS_EINVAL;
+  *ctas = choose_grid(c);
+  return GS_OK;
+}
+
+int gs_destroy(gs_ctx* c) {
+  if (c == nullptr) return GS_OK;
+  int rc = GS_OK;
+  if (cudaStreamSynchronize(c->stream) != cudaSuccess) rc = GS_ECUDA;
+  if (c->ws && cudaFree(c->ws) != cudaSuccess) rc = GS_ECUDA;
+  if (c->dres && cudaFree(c->dres) != cudaSuccess) rc = GS_ECUDA;
+  cudaGetLastError();
+  delete c;
+  return rc;
+}
+
+}  // extern "C"

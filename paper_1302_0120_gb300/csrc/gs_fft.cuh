@@ -1,0 +1,230 @@
+// gs_fft.cuh -- register/shared-memory FFT building blocks for sm_103a.
+//
+// A length-n transform (n = 2^logn, 32 <= n <= 4096) is computed by a group
+// of T = n/32 threads; thread t holds the 32 elements x[t + T*i], i = 0..31,
+// in registers. The transform is a Stockham auto-sort FFT: a first radix-32
+// stage entirely in registers, then further stages of radix 32 (and one final
+// stage of radix 2..16 when log2(n) is not a multiple of 5), each preceded by
+// one exchange through the group's padded shared-memory buffer. The output is
+// left in registers in the same layout, in natural order.
+//
+// Only the forward transform (kernel exp(-2 pi i jk/n), unnormalised) is
+// implemented. The inverse is obtained from it by exchanging real and
+// imaginary parts before and after: swap(DFT(swap(x))) = n * IDFT(x). The
+// kernels fold those swaps into the neighbouring projection code, so they cost
+// nothing.
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace gsk {
+
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+// a * w for a twiddle w = (c, s) meaning c + i s.
+__device__ __forceinline__ float2 cmul(float2 a, float2 w) {
+  return make_float2(a.x * w.x - a.y * w.y, a.x * w.y + a.y * w.x);
+}
+
+// cos(2 pi e / 32) for e = 0..8, rounded to float.
+struct Cos32 {
+  static constexpr float v[9] = {1.0f,
+                                 9.807852507e-01f,
+                                 9.238795042e-01f,
+                                 8.314695954e-01f,
+                                 7.071067691e-01f,
+                                 5.555702448e-01f,
+                                 3.826834261e-01f,
+                                 1.950903237e-01f,
+                                 0.0f};
+};
+
+// W_32^E = exp(-2 pi i E/32) = C - i S for 0 <= E < 16.
+template <int E>
+struct W32 {
+  static constexpr float C = (E <= 8) ? Cos32::v[E] : -Cos32::v[16 - E];
+  static constexpr float S = (E <= 8) ? Cos32::v[8 - E] : Cos32::v[E - 8];
+};
+
+// d * W_32^E with the trivial factors (1, -i, (1-i)/sqrt2, (-1-i)/sqrt2)
+// written out so that no multiplication by 0 or 1 is issued.
+template <int E>
+__device__ __forceinline__ float2 tw32(float2 d) {
+  if constexpr (E == 0) {
+    return d;
+  } else if constexpr (E == 8) {
+    return make_float2(d.y, -d.x);
+  } else if constexpr (E == 4) {
+    constexpr float c = Cos32::v[4];
+    return make_float2(c * (d.x + d.y), c * (d.y - d.x));
+  } else if constexpr (E == 12) {
+    constexpr float c = Cos32::v[4];
+    return make_float2(c * (d.y - d.x), -c * (d.x + d.y));
+  } else {
+    constexpr float c = W32<E>::C;
+    constexpr float s = W32<E>::S;
+    // (x + i y)(c - i s) = (x c + y s) + i (y c - x s)
+    return make_float2(d.x * c + d.y * s, d.y * c - d.x * s);
+  }
+}
+
+// One radix-2 decimation-in-frequency stage of length LEN on an R-array:
+// for every block and k < LEN/2: (a, b) -> (a + b, (a - b) W_LEN^k).
+template <int R, int LEN>
+struct DifStage {
+  template <int BASE, int K>
+  static __device__ __forceinline__ void k_loop(float2 (&a)[R]) {
+    if constexpr (K < LEN / 2) {
+      constexpr int H = LEN / 2;
+      const float2 x = a[BASE + K];
+      const float2 y = a[BASE + K + H];
+      a[BASE + K] = cadd(x, y);
+      a[BASE + K + H] = tw32<K * (32 / LEN)>(csub(x, y));
+      k_loop<BASE, K + 1>(a);
+    }
+  }
+  template <int BASE>
+  static __device__ __forceinline__ void b_loop(float2 (&a)[R]) {
+    if constexpr (BASE < R) {
+      k_loop<BASE, 0>(a);
+      b_loop<BASE + LEN>(a);
+    }
+  }
+  static __device__ __forceinline__ void run(float2 (&a)[R]) { b_loop<0>(a); }
+};
+
+template <int R, int LEN>
+__device__ __forceinline__ void dif_all(float2 (&a)[R]) {
+  if constexpr (LEN >= 2) {
+    DifStage<R, LEN>::run(a);
+    dif_all<R, LEN / 2>(a);
+  }
+}
+
+__host__ __device__ constexpr int bitrev(int i, int bits) {
+  int r = 0;
+  for (int b = 0; b < bits; ++b) r |= ((i >> b) & 1) << (bits - 1 - b);
+  return r;
+}
+
+__host__ __device__ constexpr int ilog2(int n) { return n <= 1 ? 0 : 1 + ilog2(n >> 1); }
+
+template <int R, int I>
+__device__ __forceinline__ void bitrev_copy(float2 (&dst)[R], const float2 (&src)[R]) {
+  if constexpr (I < R) {
+    dst[I] = src[bitrev(I, ilog2(R))];
+    bitrev_copy<R, I + 1>(dst, src);
+  }
+}
+
+// In-register forward DFT of size R (power of two, 2 <= R <= 32), natural
+// order in and out.
+template <int R>
+__device__ __forceinline__ void dft(float2 (&a)[R]) {
+  dif_all<R, R>(a);
+  float2 t[R];
+  bitrev_copy<R, 0>(t, a);
+#pragma unroll
+  for (int i = 0; i < R; ++i) a[i] = t[i];
+}
+
+// Per-group state of a distributed transform of length N = 2^LOGN by
+// T = N/32 threads. The geometry is a compile-time constant so that every
+// register and shared-memory index folds to an immediate offset.
+template <int LOGN>
+struct GroupT {
+  static constexpr int N = 1 << LOGN;
+  static constexpr int T = N >> 5;
+  static constexpr int SMEM = N + N / 32;  // padded exchange buffer (complex)
+  int t;                                   // thread index in the group, 0..T-1
+  int bar_id;                              // named barrier id (T > 32)
+  float2* sm;                              // this group's exchange buffer
+  const float2* __restrict__ tw;           // W_N^k = exp(-2 pi i k/N), k < N
+
+  __device__ __forceinline__ void sync() const {
+    if constexpr (T <= 32) {
+      __syncwarp();
+    } else {
+      asm volatile("bar.sync %0, %1;" ::"r"(bar_id), "n"(T) : "memory");
+    }
+  }
+};
+
+// Stockham stage of radix R with Ns = 2^NSL: butterflies j = t + T*b,
+// b < 32/R. Butterfly j reads x[j + m N/R] = v[b + (32/R) m], multiplies by
+// W_{Ns R}^{(j mod Ns) m} and transforms over m; for the last stage the
+// outputs land at the same register positions.
+template <int LOGN, int NSL, int R>
+__device__ __forceinline__ void stage_c(float2 (&v)[32], const GroupT<LOGN>& g) {
+  constexpr int Q = 32 / R;
+  constexpr int RLOG = ilog2(R);
+  constexpr int SHIFT = LOGN - NSL - RLOG;  // log2(N / (Ns R))
+  constexpr int T = GroupT<LOGN>::T;
+#pragma unroll
+  for (int b = 0; b < Q; ++b) {
+    float2 a[R];
+#pragma unroll
+    for (int m = 0; m < R; ++m) a[m] = v[b + Q * m];
+    if constexpr (NSL > 0) {
+      const int j = g.t + T * b;
+      const int step = (j & ((1 << NSL) - 1)) << SHIFT;
+      const float2* __restrict__ w = g.tw + step;
+#pragma unroll
+      for (int m = 1; m < R; ++m) a[m] = cmul(a[m], __ldg(w + (m - 1) * step));
+    }
+    dft<R>(a);
+#pragma unroll
+    for (int m = 0; m < R; ++m) v[b + Q * m] = a[m];
+  }
+}
+
+// Exchange after a radix-32 stage with Ns = 2^NSL (butterfly j = t): output
+// m goes to (t / Ns) 32 Ns + (t mod Ns) + m Ns; then every thread reads back
+// x[t + T i]. Index i of the padded buffer lives at i + i/32.
+template <int LOGN, int NSL>
+__device__ __forceinline__ void exchange(float2 (&v)[32], const GroupT<LOGN>& g) {
+  constexpr int T = GroupT<LOGN>::T;
+  static_assert(NSL == 0 || NSL >= 5, "exchanges follow radix-32 stages");
+  if constexpr (NSL == 0) {
+    float2* w = g.sm + 33 * g.t;
+#pragma unroll
+    for (int m = 0; m < 32; ++m) w[m] = v[m];
+  } else {
+    const int base = ((g.t >> NSL) << (NSL + 5)) + (g.t & ((1 << NSL) - 1));
+    float2* w = g.sm + base + (base >> 5);
+    constexpr int STR = (1 << NSL) + (1 << (NSL - 5));
+#pragma unroll
+    for (int m = 0; m < 32; ++m) w[m * STR] = v[m];
+  }
+  g.sync();
+  if constexpr (T >= 32) {
+    const float2* r = g.sm + g.t + (g.t >> 5);
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = r[i * (T + T / 32)];
+  } else {
+    const float2* r = g.sm + g.t;
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = r[i * T + ((i * T) >> 5)];
+  }
+  g.sync();
+}
+
+template <int LOGN, int DONE>
+__device__ __forceinline__ void fft_from(float2 (&v)[32], const GroupT<LOGN>& g) {
+  if constexpr (DONE < LOGN) {
+    if constexpr (DONE > 0) exchange<LOGN, DONE - 5>(v, g);
+    constexpr int REM = LOGN - DONE;
+    constexpr int RL = REM >= 5 ? 5 : REM;
+    stage_c<LOGN, DONE, (1 << RL)>(v, g);
+    fft_from<LOGN, DONE + RL>(v, g);
+  }
+}
+
+// Forward unnormalised DFT of length N over the group: v holds x[t + T i] on
+// entry and X[t + T i] on exit. Every thread of the group must call it.
+template <int LOGN>
+__device__ __forceinline__ void group_fft(float2 (&v)[32], const GroupT<LOGN>& g) {
+  fft_from<LOGN, 0>(v, g);
+}
+
+}  // namespace gsk

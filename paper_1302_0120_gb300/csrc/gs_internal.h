@@ -1,0 +1,50 @@
+// gs_internal.h -- parameters shared by the host API and the iteration kernel.
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace gsk {
+
+constexpr int kThreads = 256;                   // threads per block of the iteration kernel
+constexpr int kMaxIterPerLaunch = 128;          // iterations per persistent launch
+constexpr int kSlots = 2 * kMaxIterPerLaunch + 2;  // FP64 partial-sum slots per launch
+constexpr int kMaxGrid = 1024;                  // upper bound on blocks per launch
+// Group exchange buffers: (256 / T) groups of (n + n/32) complex, T = n/32,
+// which is 256 * 33 complex whatever n is.
+constexpr int kGroupSmemBytes = kThreads * 33 * 8;
+
+struct Params {
+  int nx, ny;          // grid, powers of two in [32, 4096]
+  int lognx, logny;
+  float2* B;           // [ny][nx] field between passes (row-transformed)
+  float* mT;           // scaled OSP amplitude, transposed: [nx][ny]
+  const float* I;      // target intensity [ny][nx]
+  const float* phi_in; // initial phase [ny][nx]
+  float* phi_out;      // final phase [ny][nx]
+  double* partials;    // [kSlots][grid] per-block FP64 sums
+  double* r_out;       // r^nu, or null
+  double* g_out;       // g^nu, or null
+  const float2* twx;   // W_nx^k, k < nx
+  const float2* twy;   // W_ny^k, k < ny
+  unsigned* bar;       // grid barrier arrival counter (zeroed before each launch)
+  int* status;         // device status word (first error wins)
+  int* abort_flag;     // set when a launch failed; later launches of the run return at once
+  int it0, it1;        // iterations [it0, it1) of this launch
+  int iters;           // total K of the run
+  int do_init;         // this launch computes m and u^0
+  int do_final;        // this launch ends the run (phase out, final residual)
+  int final_resid;     // compute r^K
+  unsigned extra_arrivals;  // test hook: arrivals a barrier waits for beyond the grid (0 in use)
+  float inv_sqrt_n;    // 1/sqrt(N)
+  double inv_n;        // 1/N
+};
+
+// Kernel for log2(nx) = LX and the given log2(ny); defined per LX in gs_inst.cu.
+template <int LX>
+const void* iterate_kernel_lx(int ly);
+
+size_t iteration_smem_bytes(int nx, int ny);
+cudaError_t launch_iterations(const Params& p, int grid, cudaStream_t s);
+cudaError_t iteration_occupancy(int nx, int ny, int* blocks_per_sm);
+
+}  // namespace gsk

@@ -1,0 +1,110 @@
+"""Torch-facing wrapper of the C ABI: device memory and streams come from torch.
+
+Every step of the method runs in the CUDA library; this module only checks
+tensor shapes and dtypes, allocates outputs and passes pointers.
+"""
+
+from __future__ import annotations
+
+import numpy as np
+
+from . import _binding as B
+
+
+class GerchbergSaxton:
+    """A Gerchberg-Saxton context for nx x ny grids (C: gs_create).
+
+    Runs are enqueued on ``stream`` (default: torch's current stream at
+    construction). Arrays are [ny, nx] float32, target intensity in DFT order.
+    """
+
+    def __init__(self, nx: int, ny: int, final_residual: bool = True, stream=None):
+        import torch
+
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.nx, self.ny = int(nx), int(ny)
+        self.final_residual = bool(final_residual)
+        self.stream = stream
+        flags = B.GS_FINAL_RESIDUAL if final_residual else 0
+        self.handle = B.gs_create(self.nx, self.ny, flags, stream.cuda_stream)
+
+    # -- helpers
+    def _check(self, x, name):
+        import torch
+
+        if not (isinstance(x, torch.Tensor) and x.is_cuda and x.dtype == torch.float32 and x.is_contiguous()):
+            raise TypeError(f"{name} must be a contiguous float32 CUDA tensor")
+        if tuple(x.shape) != (self.ny, self.nx):
+            raise ValueError(f"{name} has shape {tuple(x.shape)}, expected {(self.ny, self.nx)}")
+
+    def run(self, target, phase_in, iters: int, phase_out=None, residuals: bool = True, object_gap: bool = True):
+        """Enqueue ``iters`` iterations (C: gs_run). Returns (phase_out, r, g);
+        r and g are float64 CUDA tensors or None. Call ``status()`` (or sync the
+        stream) before reading them."""
+        import torch
+
+        self._check(target, "target")
+        self._check(phase_in, "phase_in")
+        with torch.cuda.stream(self.stream):
+            if phase_out is None:
+                phase_out = torch.empty_like(phase_in)
+            else:
+                self._check(phase_out, "phase_out")
+            nr = iters + (1 if self.final_residual else 0)
+            r = torch.empty(max(nr, 1), dtype=torch.float64, device=target.device) if residuals else None
+            g = torch.empty(max(iters, 1), dtype=torch.float64, device=target.device) if object_gap else None
+        rc = B.gs_run(self.handle, target.data_ptr(), phase_in.data_ptr(), int(iters), phase_out.data_ptr(),
+                      r.data_ptr() if r is not None else 0, g.data_ptr() if g is not None else 0)
+        if rc != B.GS_OK:
+            raise B.GSError(rc, "gs_run")
+        if r is not None:
+            r = r[:nr]
+        if g is not None:
+            g = g[:iters]
+        return phase_out, r, g
+
+    def run_host(self, target: np.ndarray, phase_in: np.ndarray, iters: int):
+        """End-to-end run on host arrays (C: gs_run_host). Returns numpy
+        (phase, r, g); raises GSError on a device-side error."""
+        target = np.ascontiguousarray(target, dtype=np.float32)
+        phase_in = np.ascontiguousarray(phase_in, dtype=np.float32)
+        out = np.empty_like(phase_in)
+        nr = iters + (1 if self.final_residual else 0)
+        r = np.empty(max(nr, 1), np.float64)
+        g = np.empty(max(iters, 1), np.float64)
+        rc = B.gs_run_host(self.handle, target.ctypes.data, phase_in.ctypes.data, int(iters), out.ctypes.data,
+                           r.ctypes.data, g.ctypes.data)
+        if rc != B.GS_OK:
+            raise B.GSError(rc, "gs_run_host")
+        return out, r[:nr], g[:iters]
+
+    def status(self) -> int:
+        """Synchronise the stream and return (and clear) the device status (C: gs_status)."""
+        return B.gs_status(self.handle)
+
+    def set_grid(self, ctas: int) -> None:
+        rc = B.gs_set_grid(self.handle, int(ctas))
+        if rc != B.GS_OK:
+            raise B.GSError(rc, "gs_set_grid")
+
+    @property
+    def grid(self) -> int:
+        return B.gs_get_grid(self.handle)
+
+    def close(self) -> None:
+        if getattr(self, "handle", None):
+            B.gs_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

@@ -1,0 +1,91 @@
+"""The C-ABI library loads and exports every symbol include/*.h declares, and
+its host-side validation answers without touching the GPU."""
+
+import ctypes
+import glob
+import os
+import re
+
+import pytest
+
+from paper_1302_0120_gb300 import _binding as B
+from paper_1302_0120_gb300 import build_lib
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build_lib.build()
+    return B.lib()
+
+
+def declared_functions():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"^\s*[A-Za-z_][\w\s\*]*?\b(gs_\w+)\s*\(", text, flags=re.M):
+            names.add(m.group(1))
+    return sorted(names)
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for must in ("gs_create", "gs_run", "gs_run_host", "gs_status", "gs_destroy", "gs_strerror",
+                 "gs_workspace_bytes"):
+        assert must in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+        assert ctypes.cast(getattr(lib, name), ctypes.c_void_p).value
+
+
+def test_binding_covers_every_declared_symbol():
+    assert set(declared_functions()) <= set(B.SIGNATURES)
+
+
+def test_strerror(lib):
+    assert B.gs_strerror(B.GS_OK) == "success"
+    for code in (B.GS_EINVAL, B.GS_ENOMEM, B.GS_ECUDA, B.GS_ETIMEOUT, B.GS_ENUMERIC, 12345):
+        assert len(B.gs_strerror(code)) > 0
+
+
+def test_workspace_bytes(lib):
+    for n in (32, 64, 512, 1024, 4096):
+        w = B.gs_workspace_bytes(n, n)
+        # field (8 B/px) + amplitude (4) + host staging (2 x 4), plus FP64 partials
+        assert w >= 20 * n * n
+        assert w < 20 * n * n + (4 << 20)
+    assert B.gs_workspace_bytes(1024, 512) > 0
+    for bad in ((16, 64), (64, 16), (33, 64), (8192, 64), (0, 0), (-64, 64), (100, 128)):
+        assert B.gs_workspace_bytes(*bad) == 0
+
+
+def test_create_validates_before_cuda(lib):
+    h = ctypes.c_void_p(123)
+    for nx, ny in ((33, 64), (64, 8192), (16, 16), (0, 64)):
+        rc = lib.gs_create(ctypes.byref(h), nx, ny, 1, None)
+        assert rc == B.GS_EINVAL
+        assert h.value is None
+    assert lib.gs_create(None, 64, 64, 1, None) == B.GS_EINVAL
+    assert lib.gs_create(ctypes.byref(h), 64, 64, 0x80, None) == B.GS_EINVAL
+
+
+def test_null_context_calls(lib):
+    assert lib.gs_run(None, None, None, 1, None, None, None) == B.GS_EINVAL
+    assert lib.gs_run_host(None, None, None, 1, None, None, None) == B.GS_EINVAL
+    assert lib.gs_status(None) == B.GS_EINVAL
+    assert lib.gs_set_grid(None, 4) == B.GS_EINVAL
+    out = ctypes.c_int(0)
+    assert lib.gs_get_grid(None, ctypes.byref(out)) == B.GS_EINVAL
+    assert lib.gs_destroy(None) == B.GS_OK
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    monkeypatch.setattr(B, "_lib", None)
+    monkeypatch.setattr(B, "LIB_PATH", str(tmp_path / "nope.so"))
+    with pytest.raises(RuntimeError, match="no CPU fallback"):
+        B.lib()
