@@ -27,6 +27,9 @@ int ilog2i(int n) {
   return l;
 }
 
+// Entries of one stage-twiddle table (stages after 32 and after 1024 points).
+constexpr int kTwiddleEntries = 31 * 32 + 31 * 1024;
+
 // Offsets of the sub-buffers of one workspace allocation.
 struct Layout {
   size_t B, mT, partials, twx, twy, bar, status, abort_flag, dI, dphi, total;
@@ -39,8 +42,8 @@ Layout make_layout(int nx, int ny) {
   L.B = o;          o = align_up(o + n * sizeof(float2));
   L.mT = o;         o = align_up(o + n * sizeof(float));
   L.partials = o;   o = align_up(o + static_cast<size_t>(gsk::kSlots) * gsk::kMaxGrid * sizeof(double));
-  L.twx = o;        o = align_up(o + static_cast<size_t>(nx) * sizeof(float2));
-  L.twy = o;        o = align_up(o + static_cast<size_t>(ny) * sizeof(float2));
+  L.twx = o;        o = align_up(o + static_cast<size_t>(kTwiddleEntries) * sizeof(float2));
+  L.twy = o;        o = align_up(o + static_cast<size_t>(kTwiddleEntries) * sizeof(float2));
   L.bar = o;        o = align_up(o + sizeof(unsigned));
   L.status = o;     o = align_up(o + sizeof(int));
   L.abort_flag = o; o = align_up(o + sizeof(int));
@@ -50,25 +53,34 @@ Layout make_layout(int nx, int ny) {
   return L;
 }
 
-// W_n^k = exp(-2 pi i k / n) for k < n, computed in double and rounded once;
-// points on the eight octant directions are set exactly.
+// exp(-2 pi i k / M) computed in double and rounded once; points on the eight
+// octant directions are exact.
+float2 unit_root(long long k, long long M) {
+  k %= M;
+  if ((8 * k) % M == 0) {
+    const double h = std::sqrt(0.5);
+    const double oc[8] = {1.0, h, 0.0, -h, -1.0, -h, 0.0, h};
+    const double os[8] = {0.0, h, 1.0, h, 0.0, -h, -1.0, -h};
+    const int o = static_cast<int>((8 * k) / M);
+    return make_float2(static_cast<float>(oc[o]), static_cast<float>(-os[o]));
+  }
+  const double a = 2.0 * M_PI * static_cast<double>(k) / static_cast<double>(M);
+  return make_float2(static_cast<float>(std::cos(a)), static_cast<float>(-std::sin(a)));
+}
+
+// Stage twiddle tables of a length-n transform, in the layout stage_c reads:
+// for the stage after Ns = 2^nsl points (nsl = 5, 10) with radix R, entry
+// offset(nsl) + (m - 1) Ns + r holds W_{Ns R}^{r m}.
 std::vector<float2> twiddles(int n) {
-  std::vector<float2> w(n);
-  const double h = std::sqrt(0.5);
-  const double oc[8] = {1.0, h, 0.0, -h, -1.0, -h, 0.0, h};
-  const double os[8] = {0.0, h, 1.0, h, 0.0, -h, -1.0, -h};
-  for (int k = 0; k < n; ++k) {
-    double c, s;
-    if ((8LL * k) % n == 0) {
-      const int o = static_cast<int>((8LL * k) / n);
-      c = oc[o];
-      s = os[o];
-    } else {
-      const double a = 2.0 * M_PI * static_cast<double>(k) / n;
-      c = std::cos(a);
-      s = std::sin(a);
-    }
-    w[k] = make_float2(static_cast<float>(c), static_cast<float>(-s));
+  std::vector<float2> w(kTwiddleEntries, make_float2(0.f, 0.f));
+  for (int nsl = 5; nsl < 12; nsl += 5) {
+    const int ns = 1 << nsl;
+    if (n <= ns) break;
+    int R = n / ns;
+    if (R > 32) R = 32;
+    const int off = nsl == 5 ? 0 : 31 * 32;
+    for (int m = 1; m < R; ++m)
+      for (int r = 0; r < ns; ++r) w[off + (m - 1) * ns + r] = unit_root(static_cast<long long>(r) * m, static_cast<long long>(ns) * R);
   }
   return w;
 }
@@ -165,8 +177,8 @@ int gs_create(gs_ctx** out, int nx, int ny, unsigned flags, void* stream) {
   }
   const std::vector<float2> wx = twiddles(nx);
   const std::vector<float2> wy = twiddles(ny);
-  bool ok = cudaMemcpy(c->ws + c->L.twx, wx.data(), nx * sizeof(float2), cudaMemcpyHostToDevice) == cudaSuccess &&
-            cudaMemcpy(c->ws + c->L.twy, wy.data(), ny * sizeof(float2), cudaMemcpyHostToDevice) == cudaSuccess &&
+  bool ok = cudaMemcpy(c->ws + c->L.twx, wx.data(), wx.size() * sizeof(float2), cudaMemcpyHostToDevice) == cudaSuccess &&
+            cudaMemcpy(c->ws + c->L.twy, wy.data(), wy.size() * sizeof(float2), cudaMemcpyHostToDevice) == cudaSuccess &&
             cudaMemset(c->ws + c->L.bar, 0, c->L.dI - c->L.bar) == cudaSuccess;
   if (!ok) {
     cudaGetLastError();

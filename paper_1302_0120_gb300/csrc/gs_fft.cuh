@@ -46,40 +46,52 @@ struct W32 {
   static constexpr float S = (E <= 8) ? Cos32::v[8 - E] : Cos32::v[E - 8];
 };
 
-// d * W_32^E with the trivial factors (1, -i, (1-i)/sqrt2, (-1-i)/sqrt2)
-// written out so that no multiplication by 0 or 1 is issued.
+// Radix-2 decimation-in-time butterfly (a, b) -> (a + w b, a - w b) with
+// w = W_32^E (0 <= E < 16). Trivial factors (1, -i) cost only additions,
+// (+-1 - i)/sqrt2 one addition pair less than a general factor, and the
+// general case uses fused multiply-adds with a - w b = 2a - (a + w b).
 template <int E>
-__device__ __forceinline__ float2 tw32(float2 d) {
+__device__ __forceinline__ void bfly(float2& a, float2& b) {
   if constexpr (E == 0) {
-    return d;
-  } else if constexpr (E == 8) {
-    return make_float2(d.y, -d.x);
-  } else if constexpr (E == 4) {
+    const float2 s = make_float2(a.x + b.x, a.y + b.y);
+    b = make_float2(a.x - b.x, a.y - b.y);
+    a = s;
+  } else if constexpr (E == 8) {  // w = -i: w b = (b.y, -b.x)
+    const float2 s = make_float2(a.x + b.y, a.y - b.x);
+    b = make_float2(a.x - b.y, a.y + b.x);
+    a = s;
+  } else if constexpr (E == 4 || E == 12) {
     constexpr float c = Cos32::v[4];
-    return make_float2(c * (d.x + d.y), c * (d.y - d.x));
-  } else if constexpr (E == 12) {
-    constexpr float c = Cos32::v[4];
-    return make_float2(c * (d.y - d.x), -c * (d.x + d.y));
+    const float t1 = b.x + b.y;
+    const float t2 = b.y - b.x;
+    if constexpr (E == 4) {  // w b = c t1 + i c t2
+      const float2 s = make_float2(fmaf(c, t1, a.x), fmaf(c, t2, a.y));
+      b = make_float2(fmaf(-c, t1, a.x), fmaf(-c, t2, a.y));
+      a = s;
+    } else {  // w b = c t2 - i c t1
+      const float2 s = make_float2(fmaf(c, t2, a.x), fmaf(-c, t1, a.y));
+      b = make_float2(fmaf(-c, t2, a.x), fmaf(c, t1, a.y));
+      a = s;
+    }
   } else {
-    constexpr float c = W32<E>::C;
-    constexpr float s = W32<E>::S;
-    // (x + i y)(c - i s) = (x c + y s) + i (y c - x s)
-    return make_float2(d.x * c + d.y * s, d.y * c - d.x * s);
+    constexpr float C = W32<E>::C;
+    constexpr float S = W32<E>::S;
+    // w b = (C b.x + S b.y) + i (C b.y - S b.x)
+    const float2 s = make_float2(fmaf(C, b.x, fmaf(S, b.y, a.x)), fmaf(C, b.y, fmaf(-S, b.x, a.y)));
+    b = make_float2(fmaf(2.f, a.x, -s.x), fmaf(2.f, a.y, -s.y));
+    a = s;
   }
 }
 
-// One radix-2 decimation-in-frequency stage of length LEN on an R-array:
-// for every block and k < LEN/2: (a, b) -> (a + b, (a - b) W_LEN^k).
-template <int R, int LEN>
-struct DifStage {
+// One decimation-in-time stage with half-span H on an R-array (bit-reversed
+// input order): for every block of 2H and k < H,
+// (x[k], x[k + H]) -> (x[k] + W_{2H}^k x[k + H], x[k] - W_{2H}^k x[k + H]).
+template <int R, int H>
+struct DitStage {
   template <int BASE, int K>
   static __device__ __forceinline__ void k_loop(float2 (&a)[R]) {
-    if constexpr (K < LEN / 2) {
-      constexpr int H = LEN / 2;
-      const float2 x = a[BASE + K];
-      const float2 y = a[BASE + K + H];
-      a[BASE + K] = cadd(x, y);
-      a[BASE + K + H] = tw32<K * (32 / LEN)>(csub(x, y));
+    if constexpr (K < H) {
+      bfly<K * (16 / H)>(a[BASE + K], a[BASE + K + H]);
       k_loop<BASE, K + 1>(a);
     }
   }
@@ -87,17 +99,17 @@ struct DifStage {
   static __device__ __forceinline__ void b_loop(float2 (&a)[R]) {
     if constexpr (BASE < R) {
       k_loop<BASE, 0>(a);
-      b_loop<BASE + LEN>(a);
+      b_loop<BASE + 2 * H>(a);
     }
   }
   static __device__ __forceinline__ void run(float2 (&a)[R]) { b_loop<0>(a); }
 };
 
-template <int R, int LEN>
-__device__ __forceinline__ void dif_all(float2 (&a)[R]) {
-  if constexpr (LEN >= 2) {
-    DifStage<R, LEN>::run(a);
-    dif_all<R, LEN / 2>(a);
+template <int R, int H>
+__device__ __forceinline__ void dit_all(float2 (&a)[R]) {
+  if constexpr (H < R) {
+    DitStage<R, H>::run(a);
+    dit_all<R, 2 * H>(a);
   }
 }
 
@@ -118,12 +130,13 @@ __device__ __forceinline__ void bitrev_copy(float2 (&dst)[R], const float2 (&src
 }
 
 // In-register forward DFT of size R (power of two, 2 <= R <= 32), natural
-// order in and out.
+// order in and out: bit-reversal permutation (register renaming only), then
+// log2(R) radix-2 decimation-in-time stages.
 template <int R>
 __device__ __forceinline__ void dft(float2 (&a)[R]) {
-  dif_all<R, R>(a);
   float2 t[R];
   bitrev_copy<R, 0>(t, a);
+  dit_all<R, 1>(t);
 #pragma unroll
   for (int i = 0; i < R; ++i) a[i] = t[i];
 }
@@ -139,7 +152,7 @@ struct GroupT {
   int t;                                   // thread index in the group, 0..T-1
   int bar_id;                              // named barrier id (T > 32)
   float2* sm;                              // this group's exchange buffer
-  const float2* __restrict__ tw;           // W_N^k = exp(-2 pi i k/N), k < N
+  const float2* __restrict__ tw;           // stage twiddle tables (twiddle_offset)
 
   __device__ __forceinline__ void sync() const {
     if constexpr (T <= 32) {
@@ -150,6 +163,13 @@ struct GroupT {
   }
 };
 
+// Twiddle tables. For the stage with Ns = 2^NSL and radix R the factors
+// W_{Ns R}^{r m} (1 <= m < R, r < Ns) are stored transposed, entry
+// (m - 1) * Ns + r, so that the threads of a warp (consecutive r) read
+// consecutive addresses. The stage with NSL = 5 starts at entry 0; the stage
+// with NSL = 10 (only for N > 1024, after a radix-32 stage) at entry 31 * 32.
+__host__ __device__ constexpr int twiddle_offset(int nsl) { return nsl == 5 ? 0 : 31 * 32; }
+
 // Stockham stage of radix R with Ns = 2^NSL: butterflies j = t + T*b,
 // b < 32/R. Butterfly j reads x[j + m N/R] = v[b + (32/R) m], multiplies by
 // W_{Ns R}^{(j mod Ns) m} and transforms over m; for the last stage the
@@ -157,20 +177,18 @@ struct GroupT {
 template <int LOGN, int NSL, int R>
 __device__ __forceinline__ void stage_c(float2 (&v)[32], const GroupT<LOGN>& g) {
   constexpr int Q = 32 / R;
-  constexpr int RLOG = ilog2(R);
-  constexpr int SHIFT = LOGN - NSL - RLOG;  // log2(N / (Ns R))
   constexpr int T = GroupT<LOGN>::T;
+  constexpr int NS = 1 << NSL;
 #pragma unroll
   for (int b = 0; b < Q; ++b) {
     float2 a[R];
 #pragma unroll
     for (int m = 0; m < R; ++m) a[m] = v[b + Q * m];
     if constexpr (NSL > 0) {
-      const int j = g.t + T * b;
-      const int step = (j & ((1 << NSL) - 1)) << SHIFT;
-      const float2* __restrict__ w = g.tw + step;
+      const int r = (g.t + T * b) & (NS - 1);
+      const float2* __restrict__ w = g.tw + twiddle_offset(NSL) + r;
 #pragma unroll
-      for (int m = 1; m < R; ++m) a[m] = cmul(a[m], __ldg(w + (m - 1) * step));
+      for (int m = 1; m < R; ++m) a[m] = cmul(a[m], __ldg(w + (m - 1) * NS));
     }
     dft<R>(a);
 #pragma unroll

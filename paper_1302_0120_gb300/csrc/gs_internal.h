@@ -24,8 +24,8 @@ struct Params {
   double* partials;    // [kSlots][grid] per-block FP64 sums
   double* r_out;       // r^nu, or null
   double* g_out;       // g^nu, or null
-  const float2* twx;   // W_nx^k, k < nx
-  const float2* twy;   // W_ny^k, k < ny
+  const float2* twx;   // stage twiddle tables of the row transforms (length nx)
+  const float2* twy;   // stage twiddle tables of the column transforms (length ny)
   unsigned* bar;       // grid barrier arrival counter (zeroed before each launch)
   int* status;         // device status word (first error wins)
   int* abort_flag;     // set when a launch failed; later launches of the run return at once

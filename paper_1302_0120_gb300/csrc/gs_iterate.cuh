@@ -36,6 +36,7 @@
 #include "gs.h"
 #include "gs_fft.cuh"
 #include "gs_internal.h"
+#include "gs_tma.cuh"
 
 namespace gsk {
 
@@ -46,9 +47,18 @@ constexpr unsigned long long kBarrierTimeoutNs = 1000000000ull;
 constexpr unsigned kMaxSpins = 1u << 26;
 
 struct Shared {
+  uint64_t mbar;  // completion of the amplitude bulk copy
   int flag;
+  int pending;    // a bulk copy into shared memory may still be in flight
+  unsigned pending_phase;  // the mbarrier phase that copy completes
   double red[kThreads / 32];
 };
+
+// Shared-memory layout of the iteration kernel (dynamic part): group exchange
+// buffers, the staged amplitude columns, then the staged field columns.
+constexpr int kAmpSmemBytes = 8192 * 4;  // W columns x N rows of m, W N = 8192
+constexpr int kAmpSmemOffset = kGroupSmemBytes;
+constexpr int kBlockSmemOffset = kGroupSmemBytes + kAmpSmemBytes;
 
 __device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
   unsigned v;
@@ -123,6 +133,7 @@ static __device__ bool grid_sync(const Params& p, unsigned& target, Shared& sh) 
       }
     }
     __threadfence();
+    if (ok && *reinterpret_cast<volatile int*>(p.abort_flag) != 0) ok = 0;  // another block failed
     sh.flag = ok;
   }
   __syncthreads();
@@ -130,19 +141,23 @@ static __device__ bool grid_sync(const Params& p, unsigned& target, Shared& sh) 
 }
 
 // One pass over this block's share of rows (kInit, kRow; LOGN = log2 nx) or
-// columns (kCol, kResid; LOGN = log2 ny). Returns this thread's FP64
-// contribution to the pass's gap sum.
-template <int LOGN>
-__device__ __forceinline__ double run_pass(const Params& p, int kind, bool last, unsigned char* smem) {
+// columns (kCol, kResid; LOGN = log2 ny); LX = log2 nx. Returns this thread's
+// FP64 contribution to the pass's gap sum.
+template <int LOGN, int LX>
+__device__ __forceinline__ double run_pass(const Params& p, int kind, bool last, unsigned char* smem, Shared& sh,
+                                           unsigned& mphase) {
   using G = GroupT<LOGN>;
   constexpr int N = G::N;
   constexpr int T = G::T;
+  constexpr int NX = 1 << LX;
   constexpr int LOGT = LOGN - 5;
   constexpr int LOGNG = 8 - LOGT;  // log2(kThreads / T)
   constexpr int NG = 1 << LOGNG;   // groups per block
   constexpr int W = NG;            // columns per staged block
   constexpr int WS = W + 1;        // padded row stride of the staged block
+  constexpr int RSTEP = kThreads / W;  // block rows one sweep of the threads covers
   static_assert(kThreads == 256, "geometry assumes 256 threads");
+  static_assert(N * W == 8192, "a staged block holds 8192 elements");
   const bool rows = (kind == kInit || kind == kRow);
   const int g = threadIdx.x >> LOGT;
   G grp;
@@ -151,27 +166,27 @@ __device__ __forceinline__ double run_pass(const Params& p, int kind, bool last,
   grp.sm = reinterpret_cast<float2*>(smem) + g * G::SMEM;
   grp.tw = rows ? p.twx : p.twy;
   const int t = grp.t;
-  float2* blk = reinterpret_cast<float2*>(smem + kGroupSmemBytes);
-  const int total = rows ? p.ny : p.nx;
+  float* ms = reinterpret_cast<float*>(smem + kAmpSmemOffset);
+  float2* blk = reinterpret_cast<float2*>(smem + kBlockSmemOffset);
+  const int total = rows ? p.ny : NX;
   const int lo = split(blockIdx.x, gridDim.x, total);
   const int hi = split(blockIdx.x + 1, gridDim.x, total);
   const int nfft = (kind == kCol || (kind == kRow && !(last && !p.final_resid))) ? 2 : 1;
   const float inv_sqrt_n = p.inv_sqrt_n;
-  const int nx = p.nx;
   double acc = 0.0;
 
   for (int base = lo; base < hi; base += NG) {
     const int idx = base + g;
     const bool valid = idx < hi;
+    const int ridx = valid ? idx : base;  // groups past the end work on a valid copy and store nothing
     const int wcur = min(NG, hi - base);
     float2 v[32];
     if (kind == kInit) {
-      const float* ph = p.phi_in + static_cast<size_t>(idx) * N + t;
+      const float* ph = p.phi_in + static_cast<size_t>(ridx) * N + t;
 #pragma unroll
       for (int i = 0; i < 32; ++i) {
-        const float a = valid ? ph[T * i] : 0.f;
         float s, c;
-        sincosf(a, &s, &c);
+        sincosf(ph[T * i], &s, &c);
         v[i] = make_float2(c, s);
       }
       if (last && valid) {  // zero iterations: the mask is arg exp(i phi^0)
@@ -183,16 +198,29 @@ __device__ __forceinline__ double run_pass(const Params& p, int kind, bool last,
         }
       }
     } else if (kind == kRow) {
-      const float2* src = p.B + static_cast<size_t>(idx) * N + t;
+      const float2* src = p.B + static_cast<size_t>(ridx) * N + t;
 #pragma unroll
-      for (int i = 0; i < 32; ++i) v[i] = valid ? src[T * i] : make_float2(0.f, 0.f);
+      for (int i = 0; i < 32; ++i) v[i] = src[T * i];
     } else {
+      __syncthreads();  // previous round's readers of the staging buffers are done
+      if (threadIdx.x == 0) {
+        // Columns [base, base + wcur) of m are contiguous in the transposed
+        // amplitude: one bulk copy, completed on the block's mbarrier.
+        const unsigned bytes = static_cast<unsigned>(wcur) * N * 4u;
+        fence_proxy_async_smem();
+        mbar_arrive_expect_tx(&sh.mbar, bytes);
+        bulk_g2s(ms, p.mT + static_cast<size_t>(base) * N, bytes, &sh.mbar);
+        sh.pending = 1;
+        sh.pending_phase = mphase;
+      }
       // Stage columns [base, base + wcur) of B (N rows) through shared memory.
-      __syncthreads();
-      for (int e = threadIdx.x; e < N * W; e += kThreads) {
-        const int k = e & (W - 1);
-        const int y = e >> LOGNG;
-        if (k < wcur) blk[y * WS + k] = p.B[static_cast<size_t>(y) * nx + base + k];
+      const int k = threadIdx.x & (W - 1);
+      const int y0 = threadIdx.x >> LOGNG;
+      if (k < wcur) {
+        const float2* src = p.B + static_cast<size_t>(y0) * NX + base + k;
+        float2* dst = blk + y0 * WS + k;
+#pragma unroll 8
+        for (int j = 0; j < N / RSTEP; ++j) dst[j * RSTEP * WS] = src[static_cast<size_t>(j) * RSTEP * NX];
       }
       __syncthreads();
       const float2* src = blk + t * WS + g;
@@ -207,10 +235,16 @@ __device__ __forceinline__ double run_pass(const Params& p, int kind, bool last,
       if (h != 0) continue;
       if (kind == kCol || kind == kResid) {
         // v = Y = F u^nu along this column. Residual and Eq. (e:Mhat).
-        const float* mcol = p.mT + static_cast<size_t>(idx) * N + t;
+        if (!mbar_wait_bounded(&sh.mbar, mphase)) {
+          fail(p, GS_ETIMEOUT);
+        } else if (threadIdx.x == 0) {
+          sh.pending = 0;
+        }
+        mphase ^= 1u;
+        const float* mcol = ms + g * N + t;
 #pragma unroll
         for (int i = 0; i < 32; ++i) {
-          const float m = valid ? mcol[T * i] : 0.f;
+          const float m = mcol[T * i];
           const float2 Y = v[i];
           const float a2 = Y.x * Y.x + Y.y * Y.y;
           const float rs = rsqrtf(a2);
@@ -225,7 +259,7 @@ __device__ __forceinline__ double run_pass(const Params& p, int kind, bool last,
         }
       } else if (kind == kRow) {
         // v = swap(IDFT_x(B)) = swap(sqrt(N) P_M u^nu). Gap to S and Eq. (e:PS).
-        float* po = p.phi_out + static_cast<size_t>(idx) * N + t;
+        float* po = p.phi_out + static_cast<size_t>(ridx) * N + t;
 #pragma unroll
         for (int i = 0; i < 32; ++i) {
           const float vx = v[i].y;
@@ -257,14 +291,24 @@ __device__ __forceinline__ double run_pass(const Params& p, int kind, bool last,
 #pragma unroll
       for (int i = 0; i < 32; ++i) dstb[i * T * WS] = v[i];
       __syncthreads();
-      for (int e = threadIdx.x; e < N * W; e += kThreads) {
-        const int k = e & (W - 1);
-        const int y = e >> LOGNG;
-        if (k < wcur) p.B[static_cast<size_t>(y) * nx + base + k] = blk[y * WS + k];
+      const int k = threadIdx.x & (W - 1);
+      const int y0 = threadIdx.x >> LOGNG;
+      if (k < wcur) {
+        float2* dst = p.B + static_cast<size_t>(y0) * NX + base + k;
+        const float2* srcb = blk + y0 * WS + k;
+#pragma unroll 8
+        for (int j = 0; j < N / RSTEP; ++j) dst[static_cast<size_t>(j) * RSTEP * NX] = srcb[j * RSTEP * WS];
       }
     }
   }
   return acc;
+}
+
+// Before leaving after a failure, give a bulk copy that may still target this
+// block's shared memory a bounded time to land.
+static __device__ void drain_copies(Shared& sh) {
+  if (threadIdx.x == 0 && sh.pending) mbar_wait_bounded(&sh.mbar, sh.pending_phase);
+  __syncthreads();
 }
 
 // m = s sqrt(I) for this block's columns, written transposed ([nx][ny]) so
@@ -272,7 +316,7 @@ __device__ __forceinline__ double run_pass(const Params& p, int kind, bool last,
 static __device__ void build_amplitude(const Params& p, float s, unsigned char* smem) {
   const int logNG = 8 - (p.logny - 5);
   const int W = 1 << logNG;
-  float* blk = reinterpret_cast<float*>(smem + kGroupSmemBytes);
+  float* blk = reinterpret_cast<float*>(smem + kBlockSmemOffset);
   const int lo = split(blockIdx.x, gridDim.x, p.nx);
   const int hi = split(blockIdx.x + 1, gridDim.x, p.nx);
   for (int base = lo; base < hi; base += W) {
@@ -301,6 +345,13 @@ __global__ void __launch_bounds__(kThreads, 1) gs_iterate(const Params p) {
   const int G = gridDim.x;
   const int b = blockIdx.x;
   unsigned target = 0;
+  unsigned mphase = 0;
+  if (threadIdx.x == 0) {
+    mbar_init(&sh.mbar, 1);
+    fence_barrier_init();
+    sh.pending = 0;
+  }
+  __syncthreads();
 
   if (p.do_init) {
     // A0: FP64 energy of the target over this block's rows. A non-finite or
@@ -365,15 +416,19 @@ __global__ void __launch_bounds__(kThreads, 1) gs_iterate(const Params p) {
     }
     double a;
     if constexpr (LX == LY) {
-      a = run_pass<LX>(p, kind, last, smem);
+      a = run_pass<LX, LX>(p, kind, last, smem, sh, mphase);
     } else {
-      a = (kind == kInit || kind == kRow) ? run_pass<LX>(p, kind, last, smem) : run_pass<LY>(p, kind, last, smem);
+      a = (kind == kInit || kind == kRow) ? run_pass<LX, LX>(p, kind, last, smem, sh, mphase)
+                                          : run_pass<LY, LX>(p, kind, last, smem, sh, mphase);
     }
     if (slot >= 0) {
       const double tot = block_sum(a, sh);
       if (threadIdx.x == 0) p.partials[static_cast<size_t>(slot) * G + b] = tot;
     }
-    if (!grid_sync(p, target, sh)) return;
+    if (!grid_sync(p, target, sh)) {
+      drain_copies(sh);
+      return;
+    }
   }
 
   // Gaps: r from column passes, g from row passes, in FP64.

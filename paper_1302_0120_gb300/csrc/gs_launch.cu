@@ -38,7 +38,7 @@ size_t iteration_smem_bytes(int nx, int ny) {
   (void)nx;
   const int groups = kThreads / (ny / 32);  // columns staged per block
   const size_t blk = static_cast<size_t>(ny) * (groups + 1) * sizeof(float2);
-  return kGroupSmemBytes + blk;
+  return kGroupSmemBytes + 8192 * 4 + blk;  // exchange buffers, staged m, staged field
 }
 
 cudaError_t iteration_occupancy(int nx, int ny, int* blocks_per_sm) {
