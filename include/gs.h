@@ -151,6 +151,42 @@ int gs_get_grid(gs_ctx* c, int* ctas);
  */
 int gs_destroy(gs_ctx* c);
 
+/*
+ * gs_run_noalloc -- gs_run without a context and without any allocation.
+ *
+ * The paper has no counterpart: this entry point exists for callers that may
+ * not allocate device memory. A closed-loop stimulation controller cannot
+ * afford cudaMalloc between spikes (it can synchronise the device and take
+ * milliseconds); a host application may own all device memory through its
+ * own pools and forbid libraries from calling the CUDA allocator; code
+ * certified to allocate nothing after start-up cannot create a context.
+ * This call performs the same operation as gs_run (same argument meaning,
+ * layout and results) with the library's own static scratch instead of a
+ * context workspace, and calls no cudaMalloc, cudaFree or allocating routine.
+ *   nx, ny          powers of two in [32, 4096] with nx * ny <= 262144
+ *                   (512 x 512): the static scratch holds one such grid.
+ *                   Larger grids return GS_EINVAL (use gs_create/gs_run).
+ *   flags, stream   as for gs_create (stream NULL = legacy default stream).
+ *   target_intensity, phase_in, iters, phase_out, residual_out,
+ *   object_gap_out  as for gs_run (device pointers owned by the caller).
+ *   device_status   device int, or NULL: receives the device-side status of
+ *                   this call (GS_OK, GS_ENUMERIC, GS_ETIMEOUT) once the
+ *                   stream reaches it.
+ * Scratch: about 4 MiB of device memory in a static array that every GPU which
+ * loads the library holds until the process exits. All calls on a device
+ * share it and it keeps the previous call's contents (each call clears what
+ * must start at zero); calls whose work overlaps on the GPU (different
+ * streams, or different host threads without ordering) race and corrupt each
+ * other's results: serialise them on one stream. The first call on a device
+ * looks up the array's device address (cudaGetSymbolAddress) with that device
+ * current; make that first call before any stream capture.
+ * Asynchronous on `stream`. Returns GS_EINVAL for unsupported sizes or flags,
+ * NULL arrays or iters < 0, GS_ECUDA if a CUDA call or launch fails.
+ */
+int gs_run_noalloc(int nx, int ny, unsigned flags, void* stream, const float* target_intensity,
+                   const float* phase_in, int iters, float* phase_out, double* residual_out,
+                   double* object_gap_out, int* device_status);
+
 /* gs_strerror -- static English text for a status code (never NULL). */
 const char* gs_strerror(int code);
 

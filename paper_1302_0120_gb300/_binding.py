@@ -36,6 +36,7 @@ SIGNATURES = {
     "gs_destroy": (_c_int, [_vp]),
     "gs_strerror": (ctypes.c_char_p, [_c_int]),
     "gs_workspace_bytes": (ctypes.c_size_t, [_c_int, _c_int, _c_uint]),
+    "gs_run_noalloc": (_c_int, [_c_int, _c_int, _c_uint, _vp, _vp, _vp, _c_int, _vp, _vp, _vp, _vp]),
 }
 
 _lib = None
@@ -110,6 +111,14 @@ def gs_get_grid(ctx: int) -> int:
     if rc != GS_OK:
         raise GSError(rc, "gs_get_grid")
     return out.value
+
+
+def gs_run_noalloc(nx: int, ny: int, flags: int, stream: int, target_intensity: int, phase_in: int, iters: int,
+                   phase_out: int, residual_out: int = 0, object_gap_out: int = 0, device_status: int = 0) -> int:
+    """gs_run on the library's static scratch (no allocation); returns the status code."""
+    return lib().gs_run_noalloc(int(nx), int(ny), int(flags), _vp(stream or 0), _vp(target_intensity),
+                                _vp(phase_in), int(iters), _vp(phase_out), _vp(residual_out or 0),
+                                _vp(object_gap_out or 0), _vp(device_status or 0))
 
 
 def gs_destroy(ctx: int) -> int:

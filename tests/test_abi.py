@@ -84,6 +84,17 @@ def test_null_context_calls(lib):
     assert lib.gs_destroy(None) == B.GS_OK
 
 
+def test_noalloc_validates_before_cuda(lib):
+    """Host-side rejection only (NULL arrays everywhere): sizes over the static
+    scratch (nx * ny > 512 * 512), sizes that are not powers of two in
+    [32, 4096], unknown flags, NULL arrays and negative iteration counts."""
+    for nx, ny in ((1024, 512), (1024, 1024), (4096, 128), (4096, 4096), (16, 64), (33, 64), (64, 8192)):
+        assert lib.gs_run_noalloc(nx, ny, 1, None, None, None, 1, None, None, None, None) == B.GS_EINVAL
+    assert lib.gs_run_noalloc(64, 64, 0x80, None, None, None, 1, None, None, None, None) == B.GS_EINVAL
+    assert lib.gs_run_noalloc(64, 64, 1, None, None, None, 1, None, None, None, None) == B.GS_EINVAL
+    assert lib.gs_run_noalloc(64, 64, 1, None, None, None, -1, None, None, None, None) == B.GS_EINVAL
+
+
 def test_missing_library_fails_loudly(monkeypatch, tmp_path):
     monkeypatch.setattr(B, "_lib", None)
     monkeypatch.setattr(B, "LIB_PATH", str(tmp_path / "nope.so"))
