@@ -170,12 +170,35 @@ struct GroupT {
 // with NSL = 10 (only for N > 1024, after a radix-32 stage) at entry 31 * 32.
 __host__ __device__ constexpr int twiddle_offset(int nsl) { return nsl == 5 ? 0 : 31 * 32; }
 
+// Twiddles of the stage that follows the first 32 points (NSL = 5), held in
+// registers: thread t needs W_{32 R}^{r m} for r = (t + T b) mod 32, b < 32/R,
+// 1 <= m < R. Loaded once and reused by every transform of the same length.
+template <int LOGN>
+struct StageTw {
+  static constexpr int R = (LOGN <= 5) ? 1 : ((LOGN - 5 >= 5) ? 32 : (1 << (LOGN - 5)));
+  static constexpr int Q = 32 / R;
+  static constexpr int COUNT = (R > 1) ? (R - 1) * Q : 1;
+  float2 w[COUNT];
+
+  __device__ __forceinline__ void load(const float2* __restrict__ tw, int t) {
+    if constexpr (R > 1) {
+      constexpr int T = (1 << LOGN) >> 5;
+#pragma unroll
+      for (int b = 0; b < Q; ++b) {
+        const int r = (t + T * b) & 31;
+#pragma unroll
+        for (int m = 1; m < R; ++m) w[b * (R - 1) + m - 1] = __ldg(tw + (m - 1) * 32 + r);
+      }
+    }
+  }
+};
+
 // Stockham stage of radix R with Ns = 2^NSL: butterflies j = t + T*b,
 // b < 32/R. Butterfly j reads x[j + m N/R] = v[b + (32/R) m], multiplies by
 // W_{Ns R}^{(j mod Ns) m} and transforms over m; for the last stage the
 // outputs land at the same register positions.
 template <int LOGN, int NSL, int R>
-__device__ __forceinline__ void stage_c(float2 (&v)[32], const GroupT<LOGN>& g) {
+__device__ __forceinline__ void stage_c(float2 (&v)[32], const GroupT<LOGN>& g, const StageTw<LOGN>& sw) {
   constexpr int Q = 32 / R;
   constexpr int T = GroupT<LOGN>::T;
   constexpr int NS = 1 << NSL;
@@ -184,7 +207,10 @@ __device__ __forceinline__ void stage_c(float2 (&v)[32], const GroupT<LOGN>& g) 
     float2 a[R];
 #pragma unroll
     for (int m = 0; m < R; ++m) a[m] = v[b + Q * m];
-    if constexpr (NSL > 0) {
+    if constexpr (NSL == 5) {
+#pragma unroll
+      for (int m = 1; m < R; ++m) a[m] = cmul(a[m], sw.w[b * (R - 1) + m - 1]);
+    } else if constexpr (NSL > 0) {
       const int r = (g.t + T * b) & (NS - 1);
       const float2* __restrict__ w = g.tw + twiddle_offset(NSL) + r;
 #pragma unroll
@@ -228,21 +254,21 @@ __device__ __forceinline__ void exchange(float2 (&v)[32], const GroupT<LOGN>& g)
 }
 
 template <int LOGN, int DONE>
-__device__ __forceinline__ void fft_from(float2 (&v)[32], const GroupT<LOGN>& g) {
+__device__ __forceinline__ void fft_from(float2 (&v)[32], const GroupT<LOGN>& g, const StageTw<LOGN>& sw) {
   if constexpr (DONE < LOGN) {
     if constexpr (DONE > 0) exchange<LOGN, DONE - 5>(v, g);
     constexpr int REM = LOGN - DONE;
     constexpr int RL = REM >= 5 ? 5 : REM;
-    stage_c<LOGN, DONE, (1 << RL)>(v, g);
-    fft_from<LOGN, DONE + RL>(v, g);
+    stage_c<LOGN, DONE, (1 << RL)>(v, g, sw);
+    fft_from<LOGN, DONE + RL>(v, g, sw);
   }
 }
 
 // Forward unnormalised DFT of length N over the group: v holds x[t + T i] on
 // entry and X[t + T i] on exit. Every thread of the group must call it.
 template <int LOGN>
-__device__ __forceinline__ void group_fft(float2 (&v)[32], const GroupT<LOGN>& g) {
-  fft_from<LOGN, 0>(v, g);
+__device__ __forceinline__ void group_fft(float2 (&v)[32], const GroupT<LOGN>& g, const StageTw<LOGN>& sw) {
+  fft_from<LOGN, 0>(v, g, sw);
 }
 
 }  // namespace gsk

@@ -50,15 +50,17 @@ struct Shared {
   uint64_t mbar;  // completion of the amplitude bulk copy
   int flag;
   int pending;    // a bulk copy into shared memory may still be in flight
+  int m_block;    // column block whose amplitude is in shared memory (-1: none)
   unsigned pending_phase;  // the mbarrier phase that copy completes
   double red[kThreads / 32];
 };
 
 // Shared-memory layout of the iteration kernel (dynamic part): group exchange
 // buffers, the staged amplitude columns, then the staged field columns.
-constexpr int kAmpSmemBytes = 8192 * 4;  // W columns x N rows of m, W N = 8192
+constexpr int kAmpSmemBytes = 8192 * 4;  // amplitude of one column block (<= 8192 values)
 constexpr int kAmpSmemOffset = kGroupSmemBytes;
 constexpr int kBlockSmemOffset = kGroupSmemBytes + kAmpSmemBytes;
+constexpr int kBlockSmemBytes = 8192 * 8;  // one column block of the field
 
 __device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
   unsigned v;
@@ -140,24 +142,48 @@ static __device__ bool grid_sync(const Params& p, unsigned& target, Shared& sh) 
   return sh.flag != 0;
 }
 
+// Storage of the field B between passes: column blocks of W adjacent columns,
+// each block one contiguous [ny][W] array, with the W elements of each of its
+// rows permuted by an XOR swizzle. A column pass moves a whole block with one
+// bulk copy each way and reads its columns from shared memory without bank
+// conflicts; a row pass reads and writes 8W-byte row segments.
+__host__ __device__ constexpr int cmin(int a, int b) { return a < b ? a : b; }
+
+template <int LX, int LY>
+struct FieldLayout {
+  static constexpr int NX = 1 << LX;
+  static constexpr int NY = 1 << LY;
+  static constexpr int TY = NY >> 5;          // threads per column transform
+  static constexpr int NGY = kThreads / TY;   // column groups per block
+  static constexpr int W = cmin(cmin(8, TY), cmin(NGY, NX));
+  static constexpr int LW = ilog2(W);
+  static constexpr int S = (W == 1) ? 0 : ilog2(16 / W);
+  static constexpr int NBLK = NX / W;
+  static constexpr int BLOCK = NY * W;        // elements of one column block
+  static_assert(BLOCK <= 8192, "a column block fits the staging buffer");
+  __device__ static constexpr int swz(int y) { return W > 1 ? ((y >> S) & (W - 1)) : 0; }
+  // element (row y, column x) of the field
+  __device__ static size_t off(int y, int x) {
+    return static_cast<size_t>(x >> LW) * BLOCK + y * W + ((x & (W - 1)) ^ swz(y));
+  }
+  // element (row y, column k) inside one block
+  __device__ static int boff(int y, int k) { return y * W + (k ^ swz(y)); }
+};
+
 // One pass over this block's share of rows (kInit, kRow; LOGN = log2 nx) or
-// columns (kCol, kResid; LOGN = log2 ny); LX = log2 nx. Returns this thread's
-// FP64 contribution to the pass's gap sum.
-template <int LOGN, int LX>
+// column blocks (kCol, kResid; LOGN = log2 ny). Returns this thread's FP64
+// contribution to the pass's gap sum.
+template <int LOGN, int LX, int LY, bool HOLD>
 __device__ __forceinline__ double run_pass(const Params& p, int kind, bool last, unsigned char* smem, Shared& sh,
-                                           unsigned& mphase) {
+                                           unsigned& mphase, const StageTw<LOGN>& tw_rows) {
   using G = GroupT<LOGN>;
+  using L = FieldLayout<LX, LY>;
   constexpr int N = G::N;
   constexpr int T = G::T;
-  constexpr int NX = 1 << LX;
   constexpr int LOGT = LOGN - 5;
   constexpr int LOGNG = 8 - LOGT;  // log2(kThreads / T)
   constexpr int NG = 1 << LOGNG;   // groups per block
-  constexpr int W = NG;            // columns per staged block
-  constexpr int WS = W + 1;        // padded row stride of the staged block
-  constexpr int RSTEP = kThreads / W;  // block rows one sweep of the threads covers
   static_assert(kThreads == 256, "geometry assumes 256 threads");
-  static_assert(N * W == 8192, "a staged block holds 8192 elements");
   const bool rows = (kind == kInit || kind == kRow);
   const int g = threadIdx.x >> LOGT;
   G grp;
@@ -166,82 +192,145 @@ __device__ __forceinline__ double run_pass(const Params& p, int kind, bool last,
   grp.sm = reinterpret_cast<float2*>(smem) + g * G::SMEM;
   grp.tw = rows ? p.twx : p.twy;
   const int t = grp.t;
+  // stage twiddles: the kernel's register copy for square grids, else
+  // loaded once for this pass
+  StageTw<LOGN> tw_own;
+  if constexpr (!HOLD) tw_own.load(grp.tw, t);
+  const StageTw<LOGN>& stw = [&]() -> const StageTw<LOGN>& {
+    if constexpr (HOLD) return tw_rows;
+    else return tw_own;
+  }();
   float* ms = reinterpret_cast<float*>(smem + kAmpSmemOffset);
   float2* blk = reinterpret_cast<float2*>(smem + kBlockSmemOffset);
-  const int total = rows ? p.ny : NX;
-  const int lo = split(blockIdx.x, gridDim.x, total);
-  const int hi = split(blockIdx.x + 1, gridDim.x, total);
   const int nfft = (kind == kCol || (kind == kRow && !(last && !p.final_resid))) ? 2 : 1;
   const float inv_sqrt_n = p.inv_sqrt_n;
   double acc = 0.0;
 
-  for (int base = lo; base < hi; base += NG) {
-    const int idx = base + g;
-    const bool valid = idx < hi;
-    const int ridx = valid ? idx : base;  // groups past the end work on a valid copy and store nothing
-    const int wcur = min(NG, hi - base);
-    float2 v[32];
-    if (kind == kInit) {
-      const float* ph = p.phi_in + static_cast<size_t>(ridx) * N + t;
+  if constexpr (LOGN == LX) {
+  if (rows) {
+    const int lo = split(blockIdx.x, gridDim.x, p.ny);
+    const int hi = split(blockIdx.x + 1, gridDim.x, p.ny);
+    for (int base = lo; base < hi; base += NG) {
+      const int idx = base + g;
+      const bool valid = idx < hi;
+      const int ridx = valid ? idx : base;  // groups past the end work on a valid copy and store nothing
+      float2 v[32];
+      if (kind == kInit) {
+        // exp(i phi) once per run: a rolled loop through the group's exchange
+        // buffer keeps a single copy of sincosf (and atan2f) in the kernel.
+        const float* ph = p.phi_in + static_cast<size_t>(ridx) * N + t;
+        float2* su = grp.sm + t;
+#pragma unroll 1
+        for (int i = 0; i < 32; ++i) {
+          float s, c;
+          sincosf(ph[T * i], &s, &c);
+          su[T * i] = make_float2(c, s);
+        }
+        if (last && valid) {  // zero iterations: the mask is arg exp(i phi^0)
+          float* po = p.phi_out + static_cast<size_t>(idx) * N + t;
+#pragma unroll 1
+          for (int i = 0; i < 32; ++i) {
+            const float2 u = su[T * i];
+            const float ph_out = atan2f(u.y, u.x);
+            po[T * i] = (ph_out <= -3.14159274f) ? 3.14159274f : ph_out;
+          }
+        }
 #pragma unroll
-      for (int i = 0; i < 32; ++i) {
-        float s, c;
-        sincosf(ph[T * i], &s, &c);
-        v[i] = make_float2(c, s);
+        for (int i = 0; i < 32; ++i) v[i] = su[T * i];
+        grp.sync();
+      } else {
+#pragma unroll
+        for (int i = 0; i < 32; ++i) v[i] = p.B[L::off(ridx, t + T * i)];
       }
-      if (last && valid) {  // zero iterations: the mask is arg exp(i phi^0)
-        float* po = p.phi_out + static_cast<size_t>(idx) * N + t;
+
+      float part = 0.f;
+#pragma unroll 1
+      for (int h = 0; h < nfft; ++h) {
+        group_fft<LOGN>(v, grp, stw);
+        if (h != 0 || kind != kRow) continue;
+        // v = swap(IDFT_x(B)) = swap(sqrt(N) P_M u^nu). Gap to S and Eq. (e:PS).
 #pragma unroll
         for (int i = 0; i < 32; ++i) {
-          const float ph_out = atan2f(v[i].y, v[i].x);
-          po[T * i] = (ph_out <= -3.14159274f) ? 3.14159274f : ph_out;
+          const float vx = v[i].y;
+          const float vy = v[i].x;
+          const float a2 = vx * vx + vy * vy;
+          const float rs = rsqrtf(a2);
+          const float mag = a2 > 0.f ? a2 * rs : 0.f;
+          const float d = mag * inv_sqrt_n - 1.f;
+          part += d * d;
+          v[i] = a2 > 0.f ? make_float2(vx * rs, vy * rs) : make_float2(1.f, 0.f);
         }
-      }
-    } else if (kind == kRow) {
-      const float2* src = p.B + static_cast<size_t>(ridx) * N + t;
+        if (last) {
+          // The mask, once per run: through the group's exchange buffer so
+          // that a rolled loop holds the only copy of atan2f.
+          float2* su = grp.sm + t;
 #pragma unroll
-      for (int i = 0; i < 32; ++i) v[i] = src[T * i];
-    } else {
-      __syncthreads();  // previous round's readers of the staging buffers are done
-      if (threadIdx.x == 0) {
-        // Columns [base, base + wcur) of m are contiguous in the transposed
-        // amplitude: one bulk copy, completed on the block's mbarrier.
-        const unsigned bytes = static_cast<unsigned>(wcur) * N * 4u;
-        fence_proxy_async_smem();
-        mbar_arrive_expect_tx(&sh.mbar, bytes);
-        bulk_g2s(ms, p.mT + static_cast<size_t>(base) * N, bytes, &sh.mbar);
-        sh.pending = 1;
-        sh.pending_phase = mphase;
-      }
-      // Stage columns [base, base + wcur) of B (N rows) through shared memory.
-      const int k = threadIdx.x & (W - 1);
-      const int y0 = threadIdx.x >> LOGNG;
-      if (k < wcur) {
-        const float2* src = p.B + static_cast<size_t>(y0) * NX + base + k;
-        float2* dst = blk + y0 * WS + k;
-#pragma unroll 8
-        for (int j = 0; j < N / RSTEP; ++j) dst[j * RSTEP * WS] = src[static_cast<size_t>(j) * RSTEP * NX];
-      }
-      __syncthreads();
-      const float2* src = blk + t * WS + g;
-#pragma unroll
-      for (int i = 0; i < 32; ++i) v[i] = src[i * T * WS];
-    }
-
-    float part = 0.f;
+          for (int i = 0; i < 32; ++i) su[T * i] = v[i];
+          if (valid) {
+            float* po = p.phi_out + static_cast<size_t>(idx) * N + t;
 #pragma unroll 1
-    for (int h = 0; h < nfft; ++h) {
-      group_fft<LOGN>(v, grp);
-      if (h != 0) continue;
-      if (kind == kCol || kind == kResid) {
-        // v = Y = F u^nu along this column. Residual and Eq. (e:Mhat).
-        if (!mbar_wait_bounded(&sh.mbar, mphase)) {
-          fail(p, GS_ETIMEOUT);
-        } else if (threadIdx.x == 0) {
-          sh.pending = 0;
+            for (int i = 0; i < 32; ++i) {
+              const float2 u = su[T * i];
+              const float ph_out = atan2f(u.y, u.x);
+              po[T * i] = (ph_out <= -3.14159274f) ? 3.14159274f : ph_out;
+            }
+          }
+          grp.sync();
         }
-        mphase ^= 1u;
-        const float* mcol = ms + g * N + t;
+      }
+      if (valid) acc += static_cast<double>(part);
+      if (valid && (kind == kInit || nfft == 2)) {
+#pragma unroll
+        for (int i = 0; i < 32; ++i) p.B[L::off(idx, t + T * i)] = v[i];
+      }
+    }
+    return acc;
+  }
+  }
+
+  // Column passes: one column block (W columns, N = ny rows) per round.
+  if constexpr (LOGN == LY) {
+  constexpr int W = L::W;
+  static_assert(N == L::NY, "column transforms have length ny");
+  const int lo = split(blockIdx.x, gridDim.x, L::NBLK);
+  const int hi = split(blockIdx.x + 1, gridDim.x, L::NBLK);
+  const bool gact = g < W;                                // this group owns a column
+  const bool wact = ((threadIdx.x & ~31) >> LOGT) < W;    // some group of this warp does
+  const int gq = gact ? g : 0;                            // idle groups read a valid column
+  for (int cb = lo; cb < hi; ++cb) {
+    __syncthreads();  // the previous round is done with the staging buffers
+    if (threadIdx.x == 0) {
+      if (kind == kCol) bulk_wait_read_all();  // the previous bulk store has read blk
+      fence_proxy_async_smem();
+      const bool need_m = (sh.m_block != cb);
+      const unsigned bytes_b = L::BLOCK * 8u;
+      const unsigned bytes_m = L::BLOCK * 4u;
+      mbar_arrive_expect_tx(&sh.mbar, bytes_b + (need_m ? bytes_m : 0u));
+      bulk_g2s(blk, p.B + static_cast<size_t>(cb) * L::BLOCK, bytes_b, &sh.mbar);
+      // columns cb W .. cb W + W - 1 of m are contiguous in the transposed amplitude
+      if (need_m) bulk_g2s(ms, p.mT + static_cast<size_t>(cb) * L::BLOCK, bytes_m, &sh.mbar);
+      sh.m_block = cb;
+      sh.pending = 1;
+      sh.pending_phase = mphase;
+    }
+    const bool landed = mbar_wait_bounded(&sh.mbar, mphase);
+    mphase ^= 1u;
+    if (!landed) {
+      fail(p, GS_ETIMEOUT);
+    } else if (threadIdx.x == 0) {
+      sh.pending = 0;
+    }
+    if (wact) {
+      float2 v[32];
+#pragma unroll
+      for (int i = 0; i < 32; ++i) v[i] = blk[L::boff(t + T * i, gq)];
+      float part = 0.f;
+#pragma unroll 1
+      for (int h = 0; h < nfft; ++h) {
+        group_fft<LOGN>(v, grp, stw);
+        if (h != 0) continue;
+        // v = Y = F u^nu along this column. Residual and Eq. (e:Mhat).
+        const float* mcol = ms + gq * N + t;
 #pragma unroll
         for (int i = 0; i < 32; ++i) {
           const float m = mcol[T * i];
@@ -257,49 +346,24 @@ __device__ __forceinline__ double run_pass(const Params& p, int kind, bool last,
             v[i] = make_float2(Yh.y, Yh.x);  // swapped: the next forward DFT acts as the inverse
           }
         }
-      } else if (kind == kRow) {
-        // v = swap(IDFT_x(B)) = swap(sqrt(N) P_M u^nu). Gap to S and Eq. (e:PS).
-        float* po = p.phi_out + static_cast<size_t>(ridx) * N + t;
+      }
+      if (gact) acc += static_cast<double>(part);
+      if (kind == kCol && gact) {
 #pragma unroll
-        for (int i = 0; i < 32; ++i) {
-          const float vx = v[i].y;
-          const float vy = v[i].x;
-          const float a2 = vx * vx + vy * vy;
-          const float rs = rsqrtf(a2);
-          const float mag = a2 > 0.f ? a2 * rs : 0.f;
-          const float d = mag * inv_sqrt_n - 1.f;
-          part += d * d;
-          const float2 u = a2 > 0.f ? make_float2(vx * rs, vy * rs) : make_float2(1.f, 0.f);
-          if (last && valid) {
-            const float ph_out = atan2f(u.y, u.x);
-            po[T * i] = (ph_out <= -3.14159274f) ? 3.14159274f : ph_out;
-          }
-          v[i] = u;
-        }
+        for (int i = 0; i < 32; ++i) blk[L::boff(t + T * i, g)] = v[i];
       }
     }
-    if (valid) acc += static_cast<double>(part);
-
-    if (kind == kInit || (kind == kRow && nfft == 2)) {
-      if (valid) {
-        float2* dst = p.B + static_cast<size_t>(idx) * N + t;
-#pragma unroll
-        for (int i = 0; i < 32; ++i) dst[T * i] = v[i];
-      }
-    } else if (kind == kCol) {
-      float2* dstb = blk + t * WS + g;
-#pragma unroll
-      for (int i = 0; i < 32; ++i) dstb[i * T * WS] = v[i];
+    if (kind == kCol) {
       __syncthreads();
-      const int k = threadIdx.x & (W - 1);
-      const int y0 = threadIdx.x >> LOGNG;
-      if (k < wcur) {
-        float2* dst = p.B + static_cast<size_t>(y0) * NX + base + k;
-        const float2* srcb = blk + y0 * WS + k;
-#pragma unroll 8
-        for (int j = 0; j < N / RSTEP; ++j) dst[static_cast<size_t>(j) * RSTEP * NX] = srcb[j * RSTEP * WS];
+      if (threadIdx.x == 0) {
+        fence_proxy_async_smem();
+        bulk_s2g(p.B + static_cast<size_t>(cb) * L::BLOCK, blk, L::BLOCK * 8u);
+        bulk_commit();
       }
     }
+  }
+  // the field must be in global memory before the grid barrier releases the next pass
+  if (kind == kCol && threadIdx.x == 0) bulk_wait_all();
   }
   return acc;
 }
@@ -346,10 +410,13 @@ __global__ void __launch_bounds__(kThreads, 1) gs_iterate(const Params p) {
   const int b = blockIdx.x;
   unsigned target = 0;
   unsigned mphase = 0;
+  StageTw<LX> tw_rows;  // square grids: stage twiddles held for the whole run
+  if constexpr (LX == LY) tw_rows.load(p.twx, threadIdx.x & ((1 << (LX - 5)) - 1));
   if (threadIdx.x == 0) {
     mbar_init(&sh.mbar, 1);
     fence_barrier_init();
     sh.pending = 0;
+    sh.m_block = -1;
   }
   __syncthreads();
 
@@ -416,10 +483,11 @@ __global__ void __launch_bounds__(kThreads, 1) gs_iterate(const Params p) {
     }
     double a;
     if constexpr (LX == LY) {
-      a = run_pass<LX, LX>(p, kind, last, smem, sh, mphase);
+      a = run_pass<LX, LX, LY, true>(p, kind, last, smem, sh, mphase, tw_rows);
     } else {
-      a = (kind == kInit || kind == kRow) ? run_pass<LX, LX>(p, kind, last, smem, sh, mphase)
-                                          : run_pass<LY, LX>(p, kind, last, smem, sh, mphase);
+      const StageTw<LY> none{};
+      a = (kind == kInit || kind == kRow) ? run_pass<LX, LX, LY, false>(p, kind, last, smem, sh, mphase, tw_rows)
+                                          : run_pass<LY, LX, LY, false>(p, kind, last, smem, sh, mphase, none);
     }
     if (slot >= 0) {
       const double tot = block_sum(a, sh);

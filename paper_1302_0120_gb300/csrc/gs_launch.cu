@@ -36,9 +36,9 @@ static const void* kernel_for(int nx, int ny) {
 
 size_t iteration_smem_bytes(int nx, int ny) {
   (void)nx;
-  const int groups = kThreads / (ny / 32);  // columns staged per block
-  const size_t blk = static_cast<size_t>(ny) * (groups + 1) * sizeof(float2);
-  return kGroupSmemBytes + 8192 * 4 + blk;  // exchange buffers, staged m, staged field
+  (void)ny;
+  // group exchange buffers, one column block of the amplitude, one of the field
+  return kGroupSmemBytes + 8192 * 4 + 8192 * 8;
 }
 
 cudaError_t iteration_occupancy(int nx, int ny, int* blocks_per_sm) {
