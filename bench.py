@@ -42,6 +42,34 @@ BYTES_PER_PX_ITER = 36
 FLOPS_PROJ_PER_PX = 20
 
 
+def kernel_sources_sha() -> str:
+    """Hash of the CUDA sources and the ABI header (identifies the kernel build)."""
+    import glob
+    import hashlib
+
+    h = hashlib.sha256()
+    for f in sorted(glob.glob(os.path.join(ROOT, "paper_1302_0120_gb300", "csrc", "*"))) + [
+            os.path.join(ROOT, "include", "gs.h")]:
+        h.update(os.path.basename(f).encode())
+        with open(f, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def measured_traffic():
+    """DRAM bytes per launch of the iteration kernel from the committed ncu
+    capture, or None when the kernel sources changed since that capture."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            rec = json.load(f)[WORKLOAD]
+    except Exception:
+        return None
+    if rec.get("csrc_sha256") != kernel_sources_sha():
+        return None
+    return rec.get("dram_bytes_per_launch")
+
+
 def peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -325,14 +353,7 @@ def run_gpu(args):
     flops_alg = iters * (2 * 5 * n * math.log2(n) + FLOPS_PROJ_PER_PX * n)
     alu_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12  # FP32 FMA lanes x 2 flops x max clock
     achieved_tf = flops_alg / (mean_ms * 1e-3) / 1e12
-    traffic = None
-    tpath = os.path.join(ROOT, "profiles", "traffic.json")
-    if os.path.exists(tpath):
-        try:
-            with open(tpath) as f:
-                traffic = json.load(f).get(WORKLOAD)
-        except Exception:
-            traffic = None
+    traffic = measured_traffic()
 
     out = {
         "metric": METRIC,
