@@ -315,6 +315,36 @@ def run_gpu(args):
     # final residual of the timed run, for the "matched residual" claim
     r_final = float(r[-1].item())
 
+    # throughput with several masks per launch (gs_run_batched): same workload
+    # recipe, seeds rank*64 + k; reported beside the single-mask latency
+    batched = None
+    if args.batch > 1:
+        nb = args.batch
+        Ib = torch.from_numpy(np.stack([S.workload(WORKLOAD, seed=rank * 64 + k)[0] for k in range(nb)])).to(dev)
+        Pb = torch.from_numpy(np.stack([S.workload(WORKLOAD, seed=rank * 64 + k)[1] for k in range(nb)])).to(dev)
+        gsb = GerchbergSaxton(nx, ny, final_residual=True, stream=stream, max_batch=nb)
+        outb = torch.empty_like(Pb)
+        for _ in range(args.warmup):
+            flush.zero_()
+            gsb.run_batched(Ib, Pb, iters, phase_out=outb)
+        if gsb.status() != 0:
+            raise RuntimeError("batched warm-up failed")
+        bsteps = max(3, args.steps // 4)
+        bs = [torch.cuda.Event(enable_timing=True) for _ in range(bsteps)]
+        be = [torch.cuda.Event(enable_timing=True) for _ in range(bsteps)]
+        for k in range(bsteps):
+            flush.zero_()
+            bs[k].record(stream)
+            gsb.run_batched(Ib, Pb, iters, phase_out=outb)
+            be[k].record(stream)
+        torch.cuda.synchronize(dev)
+        if gsb.status() != 0:
+            raise RuntimeError("batched run failed")
+        bper = statistics.mean(s_.elapsed_time(e_) for s_, e_ in zip(bs, be))
+        batched = {"batch": nb, "steps": bsteps, "ms_per_launch": round(bper, 4),
+                   "ms_per_mask": round(bper / nb, 4), "masks_per_s": round(1e3 * nb / bper, 1)}
+        gsb.close()
+
     # end to end through the public host-pointer call (gs_run_host)
     pin_I = torch.from_numpy(I_np).pin_memory()
     pin_phi = torch.from_numpy(phi_np).pin_memory()
@@ -394,6 +424,7 @@ def run_gpu(args):
             "alu_frac": round(achieved_tf / alu_peak, 4),
         },
         "clocks": clocks,
+        "batched_throughput": batched,
         "wall_s": round(wall, 3),
     }
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -415,6 +446,7 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
     ap.add_argument("--grid", type=int, default=0, help="blocks of the iteration kernel (0 = automatic)")
+    ap.add_argument("--batch", type=int, default=8, help="masks per launch for the batched-throughput field")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget-s", type=float, default=12.0)
     ap.add_argument("--ref-sample-iters", type=int, default=2)

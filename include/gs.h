@@ -86,6 +86,16 @@ typedef struct gs_ctx gs_ctx;
 int gs_create(gs_ctx** out, int nx, int ny, unsigned flags, void* stream);
 
 /*
+ * gs_create_batched -- gs_create for up to max_batch masks per run.
+ *
+ * Same as gs_create; the workspace holds max_batch fields (1 <= max_batch
+ * <= 64) so that gs_run_batched can iterate that many independent masks of
+ * the same grid in one launch (Eq. e:AP for each). Returns GS_EINVAL for a
+ * bad size or max_batch, GS_ENOMEM, GS_ECUDA.
+ */
+int gs_create_batched(gs_ctx** out, int nx, int ny, int max_batch, unsigned flags, void* stream);
+
+/*
  * gs_run -- run K iterations of the method of alternating projections.
  *
  * Operation: Eq. (e:AP) from u^0 = exp(i phase_in), with P_S (Eq. e:PS, p = 1)
@@ -107,6 +117,23 @@ int gs_create(gs_ctx** out, int nx, int ny, unsigned flags, void* stream);
  */
 int gs_run(gs_ctx* c, const float* target_intensity, const float* phase_in, int iters,
            float* phase_out, double* residual_out, double* object_gap_out);
+
+/*
+ * gs_run_batched -- gs_run for `batch` independent masks of the same grid.
+ *
+ * Operation: Eq. (e:AP) for each mask b < batch, exactly as gs_run (the
+ * masks share only the launch: results are identical to separate runs).
+ * Every array is strided by mask, mask b at offset b * (per-mask size):
+ *   target_intensity, phase_in, phase_out  device, float [batch][ny][nx]
+ *   residual_out   device, double [batch][K+1] (GS_FINAL_RESIDUAL) or
+ *                  [batch][K], or NULL
+ *   object_gap_out device, double [batch][K], or NULL
+ * 1 <= batch <= the context's max_batch. A mask whose target is invalid is
+ * skipped (its phase untouched, its gaps NaN) and gs_status reports
+ * GS_ENUMERIC; the other masks complete. Asynchronous; errors as gs_run.
+ */
+int gs_run_batched(gs_ctx* c, int batch, const float* target_intensity, const float* phase_in, int iters,
+                   float* phase_out, double* residual_out, double* object_gap_out);
 
 /*
  * gs_run_host -- gs_run on HOST buffers: end-to-end call including transfers.
@@ -195,6 +222,12 @@ const char* gs_strerror(int code);
  * (for admission by memory). Pure host computation; 0 for invalid sizes.
  */
 size_t gs_workspace_bytes(int nx, int ny, unsigned flags);
+
+/*
+ * gs_workspace_bytes_batched -- device bytes of a gs_create_batched context
+ * (for admission by memory). Pure host computation; 0 for invalid arguments.
+ */
+size_t gs_workspace_bytes_batched(int nx, int ny, int max_batch, unsigned flags);
 
 #ifdef __cplusplus
 }

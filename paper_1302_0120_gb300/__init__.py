@@ -15,13 +15,16 @@ from ._binding import (  # noqa: F401
     GS_OK,
     GSError,
     gs_create,
+    gs_create_batched,
     gs_destroy,
     gs_get_grid,
     gs_run,
+    gs_run_batched,
     gs_run_host,
     gs_set_grid,
     gs_status,
     gs_strerror,
     gs_workspace_bytes,
+    gs_workspace_bytes_batched,
 )
 from .solver import GerchbergSaxton  # noqa: F401

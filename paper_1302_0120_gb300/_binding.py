@@ -37,6 +37,9 @@ SIGNATURES = {
     "gs_strerror": (ctypes.c_char_p, [_c_int]),
     "gs_workspace_bytes": (ctypes.c_size_t, [_c_int, _c_int, _c_uint]),
     "gs_run_noalloc": (_c_int, [_c_int, _c_int, _c_uint, _vp, _vp, _vp, _c_int, _vp, _vp, _vp, _vp]),
+    "gs_create_batched": (_c_int, [ctypes.POINTER(_vp), _c_int, _c_int, _c_int, _c_uint, _vp]),
+    "gs_run_batched": (_c_int, [_vp, _c_int, _vp, _vp, _c_int, _vp, _vp, _vp]),
+    "gs_workspace_bytes_batched": (ctypes.c_size_t, [_c_int, _c_int, _c_int, _c_uint]),
 }
 
 _lib = None
@@ -72,6 +75,27 @@ def gs_strerror(code: int) -> str:
 
 def gs_workspace_bytes(nx: int, ny: int, flags: int = GS_FINAL_RESIDUAL) -> int:
     return int(lib().gs_workspace_bytes(int(nx), int(ny), int(flags)))
+
+
+def gs_workspace_bytes_batched(nx: int, ny: int, max_batch: int, flags: int = GS_FINAL_RESIDUAL) -> int:
+    return int(lib().gs_workspace_bytes_batched(int(nx), int(ny), int(max_batch), int(flags)))
+
+
+def gs_create_batched(nx: int, ny: int, max_batch: int, flags: int = GS_FINAL_RESIDUAL,
+                      stream: int | None = None) -> int:
+    """Create a context for up to max_batch masks per run; returns its handle. Raises GSError."""
+    h = _vp()
+    rc = lib().gs_create_batched(ctypes.byref(h), int(nx), int(ny), int(max_batch), int(flags), _vp(stream or 0))
+    if rc != GS_OK:
+        raise GSError(rc, "gs_create_batched")
+    return h.value
+
+
+def gs_run_batched(ctx: int, batch: int, target_intensity: int, phase_in: int, iters: int, phase_out: int,
+                   residual_out: int = 0, object_gap_out: int = 0) -> int:
+    """Enqueue a run of `batch` strided masks on device pointers; returns the status code."""
+    return lib().gs_run_batched(_vp(ctx), int(batch), _vp(target_intensity), _vp(phase_in), int(iters),
+                                _vp(phase_out), _vp(residual_out or 0), _vp(object_gap_out or 0))
 
 
 def gs_create(nx: int, ny: int, flags: int = GS_FINAL_RESIDUAL, stream: int | None = None) -> int:

@@ -32,21 +32,24 @@ constexpr int kTwiddleEntries = 31 * 32 + 31 * 1024;
 
 // Offsets of the sub-buffers of one workspace allocation.
 struct Layout {
-  size_t B, mT, partials, twx, twy, bar, status, abort_flag, dI, dphi, total;
+  size_t B, mT, partials, twx, twy, bar, status, abort_flag, mask_flags, dI, dphi, total;
 };
 
-Layout make_layout(int nx, int ny) {
+Layout make_layout(int nx, int ny, int max_batch) {
   const size_t n = static_cast<size_t>(nx) * ny;
+  const size_t nb = n * static_cast<size_t>(max_batch);
   Layout L{};
   size_t o = 0;
-  L.B = o;          o = align_up(o + n * sizeof(float2));
-  L.mT = o;         o = align_up(o + n * sizeof(float));
-  L.partials = o;   o = align_up(o + static_cast<size_t>(gsk::kSlots) * gsk::kMaxGrid * sizeof(double));
+  L.B = o;          o = align_up(o + nb * sizeof(float2));
+  L.mT = o;         o = align_up(o + nb * sizeof(float));
+  L.partials = o;
+  o = align_up(o + static_cast<size_t>(gsk::kSlots) * max_batch * gsk::kMaxGrid * sizeof(double));
   L.twx = o;        o = align_up(o + static_cast<size_t>(kTwiddleEntries) * sizeof(float2));
   L.twy = o;        o = align_up(o + static_cast<size_t>(kTwiddleEntries) * sizeof(float2));
   L.bar = o;        o = align_up(o + sizeof(unsigned));
   L.status = o;     o = align_up(o + sizeof(int));
   L.abort_flag = o; o = align_up(o + sizeof(int));
+  L.mask_flags = o; o = align_up(o + gsk::kMaxBatch * sizeof(int));
   L.dI = o;         o = align_up(o + n * sizeof(float));
   L.dphi = o;       o = align_up(o + n * sizeof(float));
   L.total = o;
@@ -89,6 +92,7 @@ std::vector<float2> twiddles(int n) {
 
 struct gs_ctx {
   int nx = 0, ny = 0;
+  int max_batch = 1;
   unsigned flags = 0;
   cudaStream_t stream = nullptr;
   int device = 0;
@@ -145,24 +149,31 @@ const char* gs_strerror(int code) {
   }
 }
 
-size_t gs_workspace_bytes(int nx, int ny, unsigned flags) {
+size_t gs_workspace_bytes_batched(int nx, int ny, int max_batch, unsigned flags) {
   (void)flags;
-  if (!valid_dim(nx) || !valid_dim(ny)) return 0;
-  return make_layout(nx, ny).total;
+  if (!valid_dim(nx) || !valid_dim(ny) || max_batch < 1 || max_batch > gsk::kMaxBatch) return 0;
+  return make_layout(nx, ny, max_batch).total;
 }
 
+size_t gs_workspace_bytes(int nx, int ny, unsigned flags) { return gs_workspace_bytes_batched(nx, ny, 1, flags); }
+
 int gs_create(gs_ctx** out, int nx, int ny, unsigned flags, void* stream) {
+  return gs_create_batched(out, nx, ny, 1, flags, stream);
+}
+
+int gs_create_batched(gs_ctx** out, int nx, int ny, int max_batch, unsigned flags, void* stream) {
   if (out == nullptr) return GS_EINVAL;
   *out = nullptr;
-  if (!valid_dim(nx) || !valid_dim(ny)) return GS_EINVAL;
+  if (!valid_dim(nx) || !valid_dim(ny) || max_batch < 1 || max_batch > gsk::kMaxBatch) return GS_EINVAL;
   if ((flags & ~static_cast<unsigned>(GS_FINAL_RESIDUAL)) != 0) return GS_EINVAL;
   gs_ctx* c = new (std::nothrow) gs_ctx();
   if (c == nullptr) return GS_ENOMEM;
   c->nx = nx;
   c->ny = ny;
+  c->max_batch = max_batch;
   c->flags = flags;
   c->stream = static_cast<cudaStream_t>(stream);
-  c->L = make_layout(nx, ny);
+  c->L = make_layout(nx, ny, max_batch);
   if (cudaGetDevice(&c->device) != cudaSuccess ||
       cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess ||
       gsk::iteration_occupancy(nx, ny, &c->blocks_per_sm) != cudaSuccess || c->blocks_per_sm < 1) {
@@ -192,10 +203,20 @@ int gs_create(gs_ctx** out, int nx, int ny, unsigned flags, void* stream) {
 
 int gs_run(gs_ctx* c, const float* target_intensity, const float* phase_in, int iters, float* phase_out,
            double* residual_out, double* object_gap_out) {
-  if (c == nullptr || target_intensity == nullptr || phase_in == nullptr || phase_out == nullptr || iters < 0)
+  return gs_run_batched(c, 1, target_intensity, phase_in, iters, phase_out, residual_out, object_gap_out);
+}
+
+int gs_run_batched(gs_ctx* c, int batch, const float* target_intensity, const float* phase_in, int iters,
+                   float* phase_out, double* residual_out, double* object_gap_out) {
+  if (c == nullptr || target_intensity == nullptr || phase_in == nullptr || phase_out == nullptr || iters < 0 ||
+      batch < 1 || batch > c->max_batch)
     return GS_EINVAL;
   const int grid = choose_grid(c);
   gsk::Params p{};
+  p.batch = batch;
+  p.mstride = static_cast<long long>(c->nx) * c->ny;
+  p.rstride = iters + ((c->flags & GS_FINAL_RESIDUAL) ? 1 : 0);
+  p.gstride = iters;
   p.nx = c->nx;
   p.ny = c->ny;
   p.lognx = ilog2i(c->nx);
@@ -213,6 +234,7 @@ int gs_run(gs_ctx* c, const float* target_intensity, const float* phase_in, int 
   p.bar = at<unsigned>(c, c->L.bar);
   p.status = at<int>(c, c->L.status);
   p.abort_flag = at<int>(c, c->L.abort_flag);
+  p.mask_flags = at<int>(c, c->L.mask_flags);
   p.iters = iters;
   p.final_resid = (c->flags & GS_FINAL_RESIDUAL) ? 1 : 0;
   p.extra_arrivals = c->extra_arrivals;

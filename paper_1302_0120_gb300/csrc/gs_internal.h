@@ -8,7 +8,8 @@ namespace gsk {
 constexpr int kThreads = 256;                   // threads per block of the iteration kernel
 constexpr int kMaxIterPerLaunch = 128;          // iterations per persistent launch
 constexpr int kSlots = 2 * kMaxIterPerLaunch + 2;  // FP64 partial-sum slots per launch
-constexpr int kMaxGrid = 1024;                  // upper bound on blocks per launch
+constexpr int kMaxGrid = 256;                   // upper bound on blocks per launch
+constexpr int kMaxBatch = 64;                   // masks per launch
 // Group exchange buffers: (256 / T) groups of (n + n/32) complex, T = n/32,
 // which is 256 * 33 complex whatever n is.
 constexpr int kGroupSmemBytes = kThreads * 33 * 8;
@@ -21,7 +22,7 @@ struct Params {
   const float* I;      // target intensity [ny][nx]
   const float* phi_in; // initial phase [ny][nx]
   float* phi_out;      // final phase [ny][nx]
-  double* partials;    // [kSlots][grid] per-block FP64 sums
+  double* partials;    // [kSlots][batch][grid] per-block FP64 sums
   double* r_out;       // r^nu, or null
   double* g_out;       // g^nu, or null
   const float2* twx;   // stage twiddle tables of the row transforms (length nx)
@@ -29,6 +30,11 @@ struct Params {
   unsigned* bar;       // grid barrier arrival counter (zeroed before each launch)
   int* status;         // device status word (first error wins)
   int* abort_flag;     // set when a launch failed; later launches of the run return at once
+  int* mask_flags;     // [kMaxBatch]: 1 for a mask whose target was rejected (written by the first launch)
+  int batch;           // masks in this launch, 1..kMaxBatch, strided in every array
+  long long mstride;   // elements of one mask in I, phi_in, phi_out, B and mT (nx*ny)
+  int rstride;         // entries of one mask in r_out
+  int gstride;         // entries of one mask in g_out
   int it0, it1;        // iterations [it0, it1) of this launch
   int iters;           // total K of the run
   int do_init;         // this launch computes m and u^0

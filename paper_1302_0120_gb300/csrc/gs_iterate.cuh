@@ -53,6 +53,8 @@ struct Shared {
   int m_block;    // column block whose amplitude is in shared memory (-1: none)
   unsigned pending_phase;  // the mbarrier phase that copy completes
   double red[kThreads / 32];
+  float scale[kMaxBatch];  // sqrt(N / sum I) per mask
+  int bad[kMaxBatch];      // mask with a non-finite, negative or zero target
 };
 
 // Shared-memory layout of the iteration kernel (dynamic part): group exchange
@@ -79,6 +81,9 @@ __device__ __forceinline__ void fail(const Params& p, int code) {
   atomicExch(p.abort_flag, 1);
 }
 
+// Record an error for the host without stopping the run (other masks go on).
+__device__ __forceinline__ void fail_status(const Params& p, int code) { atomicCAS(p.status, 0, code); }
+
 // Contiguous share [lo, hi) of `total` items for block b of G.
 __device__ __forceinline__ int split(int b, int G, int total) {
   return static_cast<int>((static_cast<long long>(b) * total) / G);
@@ -98,11 +103,11 @@ static __device__ double block_sum(double x, Shared& sh) {
   return s;
 }
 
-// Sum of partials[slot][0..G) in a fixed order, computed by one warp; the
-// result is returned to every lane of that warp.
-static __device__ double warp_slot_sum(const Params& p, int slot) {
+// Sum of partials[row][0..G) in a fixed order (row = slot * batch + mask),
+// computed by one warp; the result is returned to every lane of that warp.
+static __device__ double warp_slot_sum(const Params& p, int row) {
   const int G = gridDim.x;
-  const double* src = p.partials + static_cast<size_t>(slot) * G;
+  const double* src = p.partials + static_cast<size_t>(row) * G;
   double s = 0.0;
   for (int c = threadIdx.x & 31; c < G; c += 32) s += src[c];
 #pragma unroll
@@ -174,8 +179,12 @@ struct FieldLayout {
 // column blocks (kCol, kResid; LOGN = log2 ny). Returns this thread's FP64
 // contribution to the pass's gap sum.
 template <int LOGN, int LX, int LY, bool HOLD>
-__device__ __forceinline__ double run_pass(const Params& p, int kind, bool last, unsigned char* smem, Shared& sh,
-                                           unsigned& mphase, const StageTw<LOGN>& tw_rows) {
+__device__ __forceinline__ double run_pass(const Params& p, int mb, int kind, bool last, unsigned char* smem,
+                                           Shared& sh, unsigned& mphase, const StageTw<LOGN>& tw_rows) {
+  // this mask's arrays
+  const size_t moff = static_cast<size_t>(mb) * static_cast<size_t>(p.mstride);
+  float2* const Bm = p.B + moff;
+  const float* const mTm = p.mT + moff;
   using G = GroupT<LOGN>;
   using L = FieldLayout<LX, LY>;
   constexpr int N = G::N;
@@ -218,7 +227,7 @@ __device__ __forceinline__ double run_pass(const Params& p, int kind, bool last,
       if (kind == kInit) {
         // exp(i phi) once per run: a rolled loop through the group's exchange
         // buffer keeps a single copy of sincosf (and atan2f) in the kernel.
-        const float* ph = p.phi_in + static_cast<size_t>(ridx) * N + t;
+        const float* ph = p.phi_in + moff + static_cast<size_t>(ridx) * N + t;
         float2* su = grp.sm + t;
 #pragma unroll 1
         for (int i = 0; i < 32; ++i) {
@@ -227,7 +236,7 @@ __device__ __forceinline__ double run_pass(const Params& p, int kind, bool last,
           su[T * i] = make_float2(c, s);
         }
         if (last && valid) {  // zero iterations: the mask is arg exp(i phi^0)
-          float* po = p.phi_out + static_cast<size_t>(idx) * N + t;
+          float* po = p.phi_out + moff + static_cast<size_t>(idx) * N + t;
 #pragma unroll 1
           for (int i = 0; i < 32; ++i) {
             const float2 u = su[T * i];
@@ -240,7 +249,7 @@ __device__ __forceinline__ double run_pass(const Params& p, int kind, bool last,
         grp.sync();
       } else {
 #pragma unroll
-        for (int i = 0; i < 32; ++i) v[i] = p.B[L::off(ridx, t + T * i)];
+        for (int i = 0; i < 32; ++i) v[i] = Bm[L::off(ridx, t + T * i)];
       }
 
       float part = 0.f;
@@ -267,7 +276,7 @@ __device__ __forceinline__ double run_pass(const Params& p, int kind, bool last,
 #pragma unroll
           for (int i = 0; i < 32; ++i) su[T * i] = v[i];
           if (valid) {
-            float* po = p.phi_out + static_cast<size_t>(idx) * N + t;
+            float* po = p.phi_out + moff + static_cast<size_t>(idx) * N + t;
 #pragma unroll 1
             for (int i = 0; i < 32; ++i) {
               const float2 u = su[T * i];
@@ -281,7 +290,7 @@ __device__ __forceinline__ double run_pass(const Params& p, int kind, bool last,
       if (valid) acc += static_cast<double>(part);
       if (valid && (kind == kInit || nfft == 2)) {
 #pragma unroll
-        for (int i = 0; i < 32; ++i) p.B[L::off(idx, t + T * i)] = v[i];
+        for (int i = 0; i < 32; ++i) Bm[L::off(idx, t + T * i)] = v[i];
       }
     }
     return acc;
@@ -302,14 +311,15 @@ __device__ __forceinline__ double run_pass(const Params& p, int kind, bool last,
     if (threadIdx.x == 0) {
       if (kind == kCol) bulk_wait_read_all();  // the previous bulk store has read blk
       fence_proxy_async_smem();
-      const bool need_m = (sh.m_block != cb);
+      const int mkey = mb * L::NBLK + cb;  // which mask's amplitude block is resident
+      const bool need_m = (sh.m_block != mkey);
       const unsigned bytes_b = L::BLOCK * 8u;
       const unsigned bytes_m = L::BLOCK * 4u;
       mbar_arrive_expect_tx(&sh.mbar, bytes_b + (need_m ? bytes_m : 0u));
-      bulk_g2s(blk, p.B + static_cast<size_t>(cb) * L::BLOCK, bytes_b, &sh.mbar);
+      bulk_g2s(blk, Bm + static_cast<size_t>(cb) * L::BLOCK, bytes_b, &sh.mbar);
       // columns cb W .. cb W + W - 1 of m are contiguous in the transposed amplitude
-      if (need_m) bulk_g2s(ms, p.mT + static_cast<size_t>(cb) * L::BLOCK, bytes_m, &sh.mbar);
-      sh.m_block = cb;
+      if (need_m) bulk_g2s(ms, mTm + static_cast<size_t>(cb) * L::BLOCK, bytes_m, &sh.mbar);
+      sh.m_block = mkey;
       sh.pending = 1;
       sh.pending_phase = mphase;
     }
@@ -357,7 +367,7 @@ __device__ __forceinline__ double run_pass(const Params& p, int kind, bool last,
       __syncthreads();
       if (threadIdx.x == 0) {
         fence_proxy_async_smem();
-        bulk_s2g(p.B + static_cast<size_t>(cb) * L::BLOCK, blk, L::BLOCK * 8u);
+        bulk_s2g(Bm + static_cast<size_t>(cb) * L::BLOCK, blk, L::BLOCK * 8u);
         bulk_commit();
       }
     }
@@ -377,7 +387,10 @@ static __device__ void drain_copies(Shared& sh) {
 
 // m = s sqrt(I) for this block's columns, written transposed ([nx][ny]) so
 // that the column pass reads it contiguously.
-static __device__ void build_amplitude(const Params& p, float s, unsigned char* smem) {
+static __device__ void build_amplitude(const Params& p, int mb, float s, unsigned char* smem) {
+  const size_t moff = static_cast<size_t>(mb) * static_cast<size_t>(p.mstride);
+  const float* const Im = p.I + moff;
+  float* const mTm = p.mT + moff;
   const int logNG = 8 - (p.logny - 5);
   const int W = 1 << logNG;
   float* blk = reinterpret_cast<float*>(smem + kBlockSmemOffset);
@@ -389,13 +402,13 @@ static __device__ void build_amplitude(const Params& p, float s, unsigned char* 
     for (int e = threadIdx.x; e < p.ny * W; e += kThreads) {
       const int k = e & (W - 1);
       const int y = e >> logNG;
-      if (k < wcur) blk[y * (W + 1) + k] = p.I[static_cast<size_t>(y) * p.nx + base + k];
+      if (k < wcur) blk[y * (W + 1) + k] = Im[static_cast<size_t>(y) * p.nx + base + k];
     }
     __syncthreads();
     for (int e = threadIdx.x; e < wcur * p.ny; e += kThreads) {
       const int k = e >> p.logny;
       const int y = e & (p.ny - 1);
-      p.mT[static_cast<size_t>(base + k) * p.ny + y] = s * sqrtf(blk[y * (W + 1) + k]);
+      mTm[static_cast<size_t>(base + k) * p.ny + y] = s * sqrtf(blk[y * (W + 1) + k]);
     }
   }
   __syncthreads();
@@ -421,47 +434,69 @@ __global__ void __launch_bounds__(kThreads, 1) gs_iterate(const Params p) {
   __syncthreads();
 
   if (p.do_init) {
-    // A0: FP64 energy of the target over this block's rows. A non-finite or
-    // negative pixel poisons the sum with NaN.
+    // A0: FP64 energy of each mask's target over this block's rows. A
+    // non-finite or negative pixel poisons the sum with NaN.
     const int r0 = split(b, G, p.ny);
     const int r1 = split(b + 1, G, p.ny);
-    const float* I = p.I + static_cast<size_t>(r0) * p.nx;
     const int cnt = (r1 - r0) * p.nx;
-    double acc = 0.0;
-    bool bad = false;
-    for (int e = threadIdx.x; e < cnt; e += kThreads) {
-      const float x = I[e];
-      bad |= !(x >= 0.f && x <= FLT_MAX);
-      acc += static_cast<double>(x);
+    for (int mb = 0; mb < p.batch; ++mb) {
+      const float* I = p.I + static_cast<size_t>(mb) * static_cast<size_t>(p.mstride) + static_cast<size_t>(r0) * p.nx;
+      double acc = 0.0;
+      bool bad = false;
+      for (int e = threadIdx.x; e < cnt; e += kThreads) {
+        const float x = I[e];
+        bad |= !(x >= 0.f && x <= FLT_MAX);
+        acc += static_cast<double>(x);
+      }
+      if (__syncthreads_or(bad)) acc = __longlong_as_double(0x7ff8000000000000ll);
+      const double tot = block_sum(acc, sh);
+      if (threadIdx.x == 0) p.partials[static_cast<size_t>(mb) * G + b] = tot;
     }
-    if (bad) acc = __longlong_as_double(0x7ff8000000000000ll);
-    const double tot = block_sum(acc, sh);
-    if (threadIdx.x == 0) p.partials[b] = tot;
     if (!grid_sync(p, target, sh)) return;
+    // Every block reduces the same partials in the same order.
     if (threadIdx.x < 32) {
-      const double total = warp_slot_sum(p, 0);
-      if (threadIdx.x == 0) sh.red[0] = total;
+      for (int mb = 0; mb < p.batch; ++mb) {
+        const double total = warp_slot_sum(p, mb);
+        if (threadIdx.x == 0) {
+          const bool bad = !(total > 0.0) || !(total <= DBL_MAX);
+          sh.bad[mb] = bad ? 1 : 0;
+          if (b == 0) p.mask_flags[mb] = bad ? 1 : 0;  // for later launches of the run
+          sh.scale[mb] = bad ? 0.f : static_cast<float>(sqrt(static_cast<double>(p.nx) * p.ny / total));
+        }
+      }
     }
     __syncthreads();
-    const double total = sh.red[0];
-    if (!(total > 0.0) || !(total <= DBL_MAX)) {
+    int nbad = 0;
+    for (int mb = 0; mb < p.batch; ++mb) nbad += sh.bad[mb];
+    if (nbad > 0) {
+      // Masks with an invalid target are skipped: phase untouched, gaps NaN.
       if (b == 0) {
-        if (threadIdx.x == 0) fail(p, GS_ENUMERIC);
+        if (threadIdx.x == 0) fail_status(p, GS_ENUMERIC);
         const double nan = __longlong_as_double(0x7ff8000000000000ll);
         const int nr = p.iters + (p.final_resid ? 1 : 0);
-        if (p.r_out)
-          for (int e = threadIdx.x; e < nr; e += kThreads) p.r_out[e] = nan;
-        if (p.g_out)
-          for (int e = threadIdx.x; e < p.iters; e += kThreads) p.g_out[e] = nan;
+        for (int mb = 0; mb < p.batch; ++mb) {
+          if (!sh.bad[mb]) continue;
+          if (p.r_out)
+            for (int e = threadIdx.x; e < nr; e += kThreads) p.r_out[static_cast<size_t>(mb) * p.rstride + e] = nan;
+          if (p.g_out)
+            for (int e = threadIdx.x; e < p.iters; e += kThreads) p.g_out[static_cast<size_t>(mb) * p.gstride + e] = nan;
+        }
       }
-      return;
+      if (nbad == p.batch) {
+        if (b == 0 && threadIdx.x == 0) atomicExch(p.abort_flag, 1);  // later launches of the run
+        return;
+      }
     }
-    const float s = static_cast<float>(sqrt(static_cast<double>(p.nx) * p.ny / total));
-    build_amplitude(p, s, smem);
+    for (int mb = 0; mb < p.batch; ++mb)
+      if (!sh.bad[mb]) build_amplitude(p, mb, sh.scale[mb], smem);
+  } else if (threadIdx.x == 0) {
+    // later launches of a run: the invalid masks were flagged by the first
+    for (int mb = 0; mb < p.batch; ++mb) sh.bad[mb] = p.mask_flags[mb];
   }
+  __syncthreads();
 
-  // Pass schedule: [init] (col, row) x nit [resid]. Slot of pass q (after
-  // init) is 1 + q.
+  // Pass schedule: [init] (col, row) x nit [resid]. Pass q (after init) sums
+  // into partial rows (1 + q) * batch + mask.
   const int nit = p.it1 - p.it0;
   const int resid = (p.do_final && p.final_resid) ? 1 : 0;
   const int npass = p.do_init + 2 * nit + resid;
@@ -481,17 +516,20 @@ __global__ void __launch_bounds__(kThreads, 1) gs_iterate(const Params p) {
       kind = kResid;
       slot = 1 + q;
     }
-    double a;
-    if constexpr (LX == LY) {
-      a = run_pass<LX, LX, LY, true>(p, kind, last, smem, sh, mphase, tw_rows);
-    } else {
-      const StageTw<LY> none{};
-      a = (kind == kInit || kind == kRow) ? run_pass<LX, LX, LY, false>(p, kind, last, smem, sh, mphase, tw_rows)
-                                          : run_pass<LY, LX, LY, false>(p, kind, last, smem, sh, mphase, none);
-    }
-    if (slot >= 0) {
-      const double tot = block_sum(a, sh);
-      if (threadIdx.x == 0) p.partials[static_cast<size_t>(slot) * G + b] = tot;
+    for (int mb = 0; mb < p.batch; ++mb) {
+      if (sh.bad[mb]) continue;
+      double a;
+      if constexpr (LX == LY) {
+        a = run_pass<LX, LX, LY, true>(p, mb, kind, last, smem, sh, mphase, tw_rows);
+      } else {
+        const StageTw<LY> none{};
+        a = (kind == kInit || kind == kRow) ? run_pass<LX, LX, LY, false>(p, mb, kind, last, smem, sh, mphase, tw_rows)
+                                            : run_pass<LY, LX, LY, false>(p, mb, kind, last, smem, sh, mphase, none);
+      }
+      if (slot >= 0) {
+        const double tot = block_sum(a, sh);
+        if (threadIdx.x == 0) p.partials[(static_cast<size_t>(slot) * p.batch + mb) * G + b] = tot;
+      }
     }
     if (!grid_sync(p, target, sh)) {
       drain_copies(sh);
@@ -502,20 +540,23 @@ __global__ void __launch_bounds__(kThreads, 1) gs_iterate(const Params p) {
   // Gaps: r from column passes, g from row passes, in FP64.
   const int nslots = 2 * nit + resid;
   if (threadIdx.x < 32) {
-    for (int s = 1 + b; s <= nslots; s += G) {
-      const double sum = warp_slot_sum(p, s);
+    for (int s = b; s < nslots * p.batch; s += G) {
+      const int slot = 1 + s / p.batch;
+      const int mb = s % p.batch;
+      if (sh.bad[mb]) continue;
+      const double sum = warp_slot_sum(p, slot * p.batch + mb);
       if (threadIdx.x == 0) {
         const double val = sqrt(sum * p.inv_n);
-        const int q = s - 1;
+        const int q = slot - 1;
         if (q < 2 * nit) {
           const int nu = p.it0 + (q >> 1);
           if ((q & 1) == 0) {
-            if (p.r_out) p.r_out[nu] = val;
+            if (p.r_out) p.r_out[static_cast<size_t>(mb) * p.rstride + nu] = val;
           } else {
-            if (p.g_out) p.g_out[nu] = val;
+            if (p.g_out) p.g_out[static_cast<size_t>(mb) * p.gstride + nu] = val;
           }
         } else if (p.r_out) {
-          p.r_out[p.iters] = val;
+          p.r_out[static_cast<size_t>(mb) * p.rstride + p.iters] = val;
         }
       }
     }

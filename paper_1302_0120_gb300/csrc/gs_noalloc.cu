@@ -31,7 +31,7 @@ constexpr size_t kOffPartials = align_up(kOffM + static_cast<size_t>(kMaxPixels)
 constexpr size_t kOffTwx = align_up(kOffPartials + static_cast<size_t>(gsk::kSlots) * kMaxGrid * 8);
 constexpr size_t kOffTwy = align_up(kOffTwx + static_cast<size_t>(kTwEntries) * 8);
 constexpr size_t kOffWords = align_up(kOffTwy + static_cast<size_t>(kTwEntries) * 8);
-constexpr size_t kScratchBytes = align_up(kOffWords + 3 * sizeof(int));  // barrier, status, abort
+constexpr size_t kScratchBytes = align_up(kOffWords + (3 + gsk::kMaxBatch) * sizeof(int));  // barrier, status, abort, mask flags
 
 // The shared scratch of every gs_run_noalloc call on this device (about 4 MiB).
 static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
@@ -149,6 +149,11 @@ extern "C" int gs_run_noalloc(int nx, int ny, unsigned flags, void* stream, cons
   p.bar = reinterpret_cast<unsigned*>(base + kOffWords);
   p.status = reinterpret_cast<int*>(base + kOffWords) + 1;
   p.abort_flag = reinterpret_cast<int*>(base + kOffWords) + 2;
+  p.mask_flags = reinterpret_cast<int*>(base + kOffWords) + 3;
+  p.batch = 1;
+  p.mstride = static_cast<long long>(nx) * ny;
+  p.rstride = iters + ((flags & GS_FINAL_RESIDUAL) ? 1 : 0);
+  p.gstride = iters;
   p.iters = iters;
   p.final_resid = (flags & GS_FINAL_RESIDUAL) ? 1 : 0;
   p.extra_arrivals = 0;

@@ -18,7 +18,7 @@ class GerchbergSaxton:
     construction). Arrays are [ny, nx] float32, target intensity in DFT order.
     """
 
-    def __init__(self, nx: int, ny: int, final_residual: bool = True, stream=None):
+    def __init__(self, nx: int, ny: int, final_residual: bool = True, stream=None, max_batch: int = 1):
         import torch
 
         if stream is None:
@@ -26,8 +26,9 @@ class GerchbergSaxton:
         self.nx, self.ny = int(nx), int(ny)
         self.final_residual = bool(final_residual)
         self.stream = stream
+        self.max_batch = int(max_batch)
         flags = B.GS_FINAL_RESIDUAL if final_residual else 0
-        self.handle = B.gs_create(self.nx, self.ny, flags, stream.cuda_stream)
+        self.handle = B.gs_create_batched(self.nx, self.ny, self.max_batch, flags, stream.cuda_stream)
 
     # -- helpers
     def _check(self, x, name):
@@ -63,6 +64,34 @@ class GerchbergSaxton:
         if g is not None:
             g = g[:iters]
         return phase_out, r, g
+
+    def run_batched(self, target, phase_in, iters: int, phase_out=None, residuals: bool = True,
+                    object_gap: bool = True):
+        """Enqueue ``iters`` iterations for a batch of masks (C: gs_run_batched).
+        Arrays are [batch, ny, nx]; returns (phase_out, r [batch, K(+1)], g [batch, K])."""
+        import torch
+
+        for x, name in ((target, "target"), (phase_in, "phase_in")):
+            if not (isinstance(x, torch.Tensor) and x.is_cuda and x.dtype == torch.float32 and x.is_contiguous()):
+                raise TypeError(f"{name} must be a contiguous float32 CUDA tensor")
+            if x.dim() != 3 or tuple(x.shape[1:]) != (self.ny, self.nx):
+                raise ValueError(f"{name} has shape {tuple(x.shape)}, expected (batch, {self.ny}, {self.nx})")
+        nb = target.shape[0]
+        if phase_in.shape[0] != nb or not 1 <= nb <= self.max_batch:
+            raise ValueError(f"batch {nb} outside 1..{self.max_batch} or mismatched")
+        nr = iters + (1 if self.final_residual else 0)
+        with torch.cuda.stream(self.stream):
+            if phase_out is None:
+                phase_out = torch.empty_like(phase_in)
+            r = torch.empty((nb, max(nr, 1)), dtype=torch.float64, device=target.device) if residuals else None
+            g = torch.empty((nb, max(iters, 1)), dtype=torch.float64, device=target.device) if object_gap else None
+        if residuals and nr == 0:
+            r = r[:, :0]
+        rc = B.gs_run_batched(self.handle, nb, target.data_ptr(), phase_in.data_ptr(), int(iters), phase_out.data_ptr(),
+                              r.data_ptr() if r is not None else 0, g.data_ptr() if g is not None else 0)
+        if rc != B.GS_OK:
+            raise B.GSError(rc, "gs_run_batched")
+        return phase_out, r, (g[:, :iters] if g is not None else None)
 
     def run_host(self, target: np.ndarray, phase_in: np.ndarray, iters: int):
         """End-to-end run on host arrays (C: gs_run_host). Returns numpy
