@@ -345,6 +345,18 @@ def run_gpu(args):
                    "ms_per_mask": round(bper / nb, 4), "masks_per_s": round(1e3 * nb / bper, 1)}
         gsb.close()
 
+    # serving: a Poisson stream of 512^2 / 1024^2 requests (30 warm-started
+    # iterations each) through the continuous-batching loop
+    serving = None
+    if args.serve_seconds > 0 and ws == 1:
+        from paper_1302_0120_gb300 import serving as SV
+
+        summ, _, ex = SV.run_service(rate_hz=args.serve_rate, seconds=args.serve_seconds, sizes=(512, 1024),
+                                     lanes=(1, 2), iters=30, warmup_s=0.3)
+        ex.close()
+        serving = {k: (round(v, 4) if isinstance(v, float) else v) for k, v in summ.items() if k != "lanes"}
+        serving["lanes"] = [f"{p['name']} batch<={p['max_batch']} grid={p['grid']}" for p in summ["lanes"]]
+
     # end to end through the public host-pointer call (gs_run_host)
     pin_I = torch.from_numpy(I_np).pin_memory()
     pin_phi = torch.from_numpy(phi_np).pin_memory()
@@ -425,6 +437,7 @@ def run_gpu(args):
         },
         "clocks": clocks,
         "batched_throughput": batched,
+        "serving": serving,
         "wall_s": round(wall, 3),
     }
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -447,6 +460,8 @@ def main(argv=None):
     ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
     ap.add_argument("--grid", type=int, default=0, help="blocks of the iteration kernel (0 = automatic)")
     ap.add_argument("--batch", type=int, default=8, help="masks per launch for the batched-throughput field")
+    ap.add_argument("--serve-seconds", type=float, default=2.0, help="length of the serving stream (0: skip)")
+    ap.add_argument("--serve-rate", type=float, default=1000.0, help="request rate of the serving stream (Hz)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget-s", type=float, default=12.0)
     ap.add_argument("--ref-sample-iters", type=int, default=2)
