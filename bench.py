@@ -357,6 +357,31 @@ def run_gpu(args):
         serving = {k: (round(v, 4) if isinstance(v, float) else v) for k, v in summ.items() if k != "lanes"}
         serving["lanes"] = [f"{p['name']} batch<={p['max_batch']} grid={p['grid']}" for p in summ["lanes"]]
 
+    # differentiable form: 1024^2 phase, 100-spot target with sum I = N,
+    # 200 Adam steps (loss + hand-written adjoint + torch Adam per step)
+    differentiable = None
+    if args.adam_steps > 0 and ws == 1:
+        from paper_1302_0120_gb300.differentiable import LossContext, optimize_phase
+
+        It = S.spot_target(1000 + rank, ny, nx, 100, (0.5, 1.0)).astype(np.float64)
+        It *= It.size / It.sum()
+        It = torch.from_numpy(It.astype(np.float32)).to(dev)
+        ph0 = torch.from_numpy(S.random_phase(1001 + rank, ny, nx)).to(dev)
+        lc = LossContext(nx, stream=stream)
+        optimize_phase(It, ph0, steps=5, lctx=lc)  # warm-up
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        _, losses = optimize_phase(It, ph0, steps=args.adam_steps, lr=0.05, lctx=lc)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        if lc.status() != 0:
+            raise RuntimeError("loss kernel failed")
+        differentiable = {"n": nx, "spots": 100, "adam_steps": args.adam_steps, "lr": 0.05,
+                          "ms_per_step": round(e0.elapsed_time(e1) / args.adam_steps, 4),
+                          "loss_first": float(losses[0]), "loss_last": float(losses[-1])}
+        lc.close()
+
     # end to end through the public host-pointer call (gs_run_host)
     pin_I = torch.from_numpy(I_np).pin_memory()
     pin_phi = torch.from_numpy(phi_np).pin_memory()
@@ -438,6 +463,7 @@ def run_gpu(args):
         "clocks": clocks,
         "batched_throughput": batched,
         "serving": serving,
+        "differentiable": differentiable,
         "wall_s": round(wall, 3),
     }
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -462,6 +488,7 @@ def main(argv=None):
     ap.add_argument("--batch", type=int, default=8, help="masks per launch for the batched-throughput field")
     ap.add_argument("--serve-seconds", type=float, default=2.0, help="length of the serving stream (0: skip)")
     ap.add_argument("--serve-rate", type=float, default=1000.0, help="request rate of the serving stream (Hz)")
+    ap.add_argument("--adam-steps", type=int, default=200, help="Adam steps of the differentiable-form field (0: skip)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget-s", type=float, default=12.0)
     ap.add_argument("--ref-sample-iters", type=int, default=2)

@@ -179,6 +179,26 @@ int gs_get_grid(gs_ctx* c, int* ctas);
 int gs_destroy(gs_ctx* c);
 
 /*
+ * gs_loss_grad -- intensity loss of a phase mask and its gradient.
+ *
+ * Operation: the differentiable form of the inverse problem of Sec. II (fit
+ * the Fourier intensity of a phase-only field to the target):
+ *   L(phi) = sum_k (|y_k|^2 / N - I_k)^2,   y = F exp(i phi)  (F unnormalised)
+ *   dL/dphi = 4 Im(conj(x) * F^{-1}(r * y)),  x = exp(i phi), r = |y|^2/N - I,
+ * F^{-1} the normalised inverse (the adjoint is computed by hand-written
+ * passes, not by differentiating the forward code). Square grids only
+ * (nx == ny), batch 1, on the context's workspace and stream.
+ *   target_intensity  device, float [n][n], finite (any sign).
+ *   phase             device, float [n][n], radians.
+ *   loss_out          device, double[1].
+ *   grad_out          device, float [n][n] (dL/dphi), or NULL for the loss only.
+ * Asynchronous. Returns GS_EINVAL for NULL arguments or a non-square context,
+ * GS_ECUDA if the launch fails; a non-finite target sets loss_out to NaN and
+ * gs_status reports GS_ENUMERIC.
+ */
+int gs_loss_grad(gs_ctx* c, const float* target_intensity, const float* phase, double* loss_out, float* grad_out);
+
+/*
  * gs_run_noalloc -- gs_run without a context and without any allocation.
  *
  * The paper has no counterpart: this entry point exists for callers that may

@@ -40,6 +40,7 @@ SIGNATURES = {
     "gs_create_batched": (_c_int, [ctypes.POINTER(_vp), _c_int, _c_int, _c_int, _c_uint, _vp]),
     "gs_run_batched": (_c_int, [_vp, _c_int, _vp, _vp, _c_int, _vp, _vp, _vp]),
     "gs_workspace_bytes_batched": (ctypes.c_size_t, [_c_int, _c_int, _c_int, _c_uint]),
+    "gs_loss_grad": (_c_int, [_vp, _vp, _vp, _vp, _vp]),
 }
 
 _lib = None
@@ -119,6 +120,11 @@ def gs_run_host(ctx: int, target_intensity: int, phase_in: int, iters: int, phas
     """Run on host pointers (synchronous); returns the status code."""
     return lib().gs_run_host(_vp(ctx), _vp(target_intensity), _vp(phase_in), int(iters), _vp(phase_out),
                              _vp(residual_out or 0), _vp(object_gap_out or 0))
+
+
+def gs_loss_grad(ctx: int, target_intensity: int, phase: int, loss_out: int, grad_out: int = 0) -> int:
+    """Enqueue the intensity loss (and its gradient when grad_out != 0); returns the status code."""
+    return lib().gs_loss_grad(_vp(ctx), _vp(target_intensity), _vp(phase), _vp(loss_out), _vp(grad_out or 0))
 
 
 def gs_status(ctx: int) -> int:

@@ -322,6 +322,33 @@ int gs_run_host(gs_ctx* c, const float* target_intensity, const float* phase_in,
   return gs_status(c);
 }
 
+int gs_loss_grad(gs_ctx* c, const float* target_intensity, const float* phase, double* loss_out, float* grad_out) {
+  if (c == nullptr || target_intensity == nullptr || phase == nullptr || loss_out == nullptr || c->nx != c->ny)
+    return GS_EINVAL;
+  gsk::LossParams p{};
+  p.n = c->nx;
+  p.logn = ilog2i(c->nx);
+  p.B = at<float2>(c, c->L.B);
+  p.IT = at<float>(c, c->L.mT);
+  p.I = target_intensity;
+  p.phi = phase;
+  p.grad = grad_out;
+  p.loss = loss_out;
+  p.partials = at<double>(c, c->L.partials);
+  p.tw = at<float2>(c, c->L.twx);
+  p.bar = at<unsigned>(c, c->L.bar);
+  p.status = at<int>(c, c->L.status);
+  p.abort_flag = at<int>(c, c->L.abort_flag);
+  p.inv_n = 1.0f / static_cast<float>(static_cast<double>(c->nx) * c->ny);
+  if (cudaMemsetAsync(p.bar, 0, sizeof(unsigned), c->stream) != cudaSuccess ||
+      cudaMemsetAsync(p.abort_flag, 0, sizeof(int), c->stream) != cudaSuccess ||
+      gsk::launch_loss(p, choose_grid(c), c->stream) != cudaSuccess) {
+    cudaGetLastError();
+    return GS_ECUDA;
+  }
+  return GS_OK;
+}
+
 int gs_set_grid(gs_ctx* c, int ctas) {
   if (c == nullptr || ctas < 0) return GS_EINVAL;
   c->grid_override = ctas;

@@ -50,6 +50,25 @@ template <int LX>
 const void* iterate_kernel_lx(int ly);
 
 size_t iteration_smem_bytes(int nx, int ny);
+
+// Intensity loss and gradient (square grids), see gs_loss.cuh.
+struct LossParams {
+  int n, logn;             // square grid n x n
+  float2* B;               // workspace field (column-blocked layout)
+  float* IT;               // workspace: target transposed [n][n]
+  const float* I;          // target intensity [n][n]
+  const float* phi;        // phase [n][n]
+  float* grad;             // dL/dphi [n][n], or null (loss only)
+  double* loss;            // [1]
+  double* partials;        // [2][grid]
+  const float2* tw;        // stage twiddle tables (length n)
+  unsigned* bar;
+  int* status;
+  int* abort_flag;
+  float inv_n;             // 1/N
+};
+
+cudaError_t launch_loss(const LossParams& p, int grid, cudaStream_t s);
 cudaError_t launch_iterations(const Params& p, int grid, cudaStream_t s);
 cudaError_t iteration_occupancy(int nx, int ny, int* blocks_per_sm);
 
