@@ -15,12 +15,15 @@ Conventions (the paper fixes none of them; these are the readings used):
     ``exp(-2*pi*i*(j*k1/nx + k*k2/ny))``; ``F_u = F / sqrt(N)`` is unitary.
     The projections are computed with ``F_u`` so that the object and Fourier
     domains carry the same Euclidean norm.
-  * The OSP amplitude is ``m = sqrt(I)`` rescaled so that ``sum m^2 = N``,
-    the energy of a unit-modulus SLM field (Eq. pattern-constraint gives m as
-    an amplitude; the scale is unstated and does not change the iterates).
+  * The OSP amplitude is ``m = sqrt(I)`` rescaled so that ``sum m^2`` equals
+    the energy ``sum p^2`` of an SLM field (``N`` for unit amplitude p = 1;
+    Eq. pattern-constraint gives m as an amplitude; the scale is unstated and
+    does not change the iterates).
   * Where the paper allows an arbitrary phase for a zero pixel (Eqs. e:PS and
     e:Mhat), theta = 0 is chosen, with an exact-zero test.
-  * Both gaps are divided by ``sqrt(N) = ||u||``.
+  * Both gaps are divided by ``||p||_2 = ||u||`` (``sqrt(N)`` for p = 1).
+  * The initial condition ``P_M uhat^0`` of Sec. IV (garbled) is read as
+    ``u0 = P_S(F^{-1} m)``; the default start is ``u0 = p exp(i phi0)``.
 
 Parity status:
   fft2u / ifft2u, target_amplitude, proj_S, proj_M, gap_to_M, gap_to_S,
@@ -69,12 +72,13 @@ def ifft2u(X: np.ndarray) -> np.ndarray:
     return _sfft.ifft2(X, norm="ortho", workers=WORKERS)
 
 
-def target_amplitude(I: np.ndarray, dtype=np.float64) -> np.ndarray:
+def target_amplitude(I: np.ndarray, dtype=np.float64, energy: float | None = None) -> np.ndarray:
     """OSP amplitude m from a target intensity I (Eq. pattern-constraint).
 
     m is an amplitude, so ``m = sqrt(I)``; it is rescaled so that
-    ``sum m^2 = N``, the squared norm of any field in the SLM set S with unit
-    amplitude. Raises ValueError for a non-finite, negative or all-zero I.
+    ``sum m^2`` equals the squared norm of every field in the SLM set S:
+    ``energy = sum p^2`` (``N`` for unit amplitude, the default). Raises
+    ValueError for a non-finite, negative or all-zero I.
     """
     I = np.asarray(I, dtype=np.float64)
     if not np.all(np.isfinite(I)):
@@ -84,8 +88,8 @@ def target_amplitude(I: np.ndarray, dtype=np.float64) -> np.ndarray:
     total = float(np.sum(I))
     if not total > 0.0:
         raise ValueError("target intensity sums to zero")
-    n = I.size
-    m = np.sqrt(I) * np.sqrt(n / total)
+    e = float(I.size) if energy is None else float(energy)
+    m = np.sqrt(I) * np.sqrt(e / total)
     return m.astype(dtype)
 
 
@@ -120,43 +124,55 @@ def proj_M(u: np.ndarray, m: np.ndarray) -> np.ndarray:
     return ifft2u(_mhat(fft2u(u), m))
 
 
-def gap_to_M(u: np.ndarray, m: np.ndarray) -> float:
-    """Normalised distance of u to M, ``||u - P_M u||_2 / sqrt(N)``.
+def _norm_S(shape, p):
+    """||u|| for u in S: sqrt(sum p^2) (sqrt(N) for unit amplitude)."""
+    return np.sqrt(float(np.prod(shape))) if p is None else float(np.sqrt(np.sum(np.asarray(p, np.float64) ** 2)))
+
+
+def gap_to_M(u: np.ndarray, m: np.ndarray, p: np.ndarray | None = None) -> float:
+    """Normalised distance of u to M, ``||u - P_M u||_2 / ||p||_2``.
 
     Computed in the Fourier domain, where (Parseval) it equals
-    ``|| |F_u u| - m ||_2 / sqrt(N)``. This is the normalised OSP residual r.
+    ``|| |F_u u| - m ||_2 / ||p||_2``; ``||p||_2 = sqrt(N)`` for unit
+    amplitude. This is the normalised OSP residual r.
     """
     Fu = fft2u(u)
-    return float(np.linalg.norm((np.abs(Fu) - m).ravel().astype(np.float64)) / np.sqrt(u.size))
+    return float(np.linalg.norm((np.abs(Fu) - m).ravel().astype(np.float64)) / _norm_S(u.shape, p))
 
 
 def gap_to_S(v: np.ndarray, p: np.ndarray | None = None) -> float:
-    """Normalised distance of v to S, ``||v - P_S v||_2 / sqrt(N) = || |v| - p ||_2 / sqrt(N)``."""
-    if p is None:
-        p = 1.0
-    return float(np.linalg.norm((np.abs(v) - p).ravel().astype(np.float64)) / np.sqrt(v.size))
+    """Normalised distance of v to S, ``||v - P_S v||_2 / ||p||_2 = || |v| - p ||_2 / ||p||_2``."""
+    pp = 1.0 if p is None else p
+    return float(np.linalg.norm((np.abs(v) - pp).ravel().astype(np.float64)) / _norm_S(v.shape, p))
 
 
-def gs_step(u: np.ndarray, m: np.ndarray):
+def gs_step(u: np.ndarray, m: np.ndarray, p: np.ndarray | None = None):
     """One step of Eq. (e:AP), ``u' = P_S P_M u``, with both gaps of Eq. (gap-error).
 
-    Returns ``(u_next, r, g)`` where ``r = ||u - P_M u|| / sqrt(N)`` (the
+    Returns ``(u_next, r, g)`` where ``r = ||u - P_M u|| / ||p||`` (the
     distance of the current iterate to M, the normalised OSP residual) and
-    ``g = ||P_M u - P_S P_M u|| / sqrt(N)`` (the distance of the M-iterate to
+    ``g = ||P_M u - P_S P_M u|| / ||p||`` (the distance of the M-iterate to
     S). Eq. (gap-error) writes the gap as ``||P_S u - P_M u||``; since the
     iterate alternates between the sets, both readings are reported.
+    ``p`` is the SLM amplitude of Eq. (slm-constraint) (None: 1).
     """
     Fu = fft2u(u)
-    n = u.size
-    r = float(np.linalg.norm((np.abs(Fu) - m).ravel().astype(np.float64)) / np.sqrt(n))
+    r = float(np.linalg.norm((np.abs(Fu) - m).ravel().astype(np.float64)) / _norm_S(u.shape, p))
     v = ifft2u(_mhat(Fu, m))  # P_M u, Eq. (e:PM)
-    g = gap_to_S(v)
-    u_next = proj_S(v)  # Eq. (e:PS)
+    g = gap_to_S(v, p)
+    u_next = proj_S(v, p)  # Eq. (e:PS)
     return u_next, r, g
 
 
-def gs_run(I, phi0, iters: int, final_residual: bool = True, dtype=np.float64):
-    """The method of alternating projections, Eq. (e:AP), from ``u0 = exp(i phi0)``.
+def gs_run(I, phi0, iters: int, final_residual: bool = True, dtype=np.float64, p=None, init: str = "phase"):
+    """The method of alternating projections, Eq. (e:AP).
+
+    Start ``init="phase"``: ``u0 = p exp(i phi0)``. Start ``init="target"``:
+    the initial condition of Sec. IV, read as ``u0 = P_S(F^{-1} m)`` (the
+    target amplitude brought to the SLM plane and adapted to the SLM
+    constraint); ``phi0`` is then unused. ``p`` is the SLM amplitude of Eq.
+    (slm-constraint), float32 [ny, nx] >= 0 (None: 1); the target amplitude
+    carries the same energy, ``sum m^2 = sum p^2``.
 
     Inputs are the arrays the GPU receives; they are widened exactly to
     ``dtype`` (FP64 by default; FP32 reproduces the paper's single-precision
@@ -170,16 +186,26 @@ def gs_run(I, phi0, iters: int, final_residual: bool = True, dtype=np.float64):
         raise ValueError("iters must be >= 0")
     rdt = np.dtype(dtype)
     cdt = _complex_dtype(rdt)
-    m = target_amplitude(I, dtype=rdt)
-    phi = np.asarray(phi0, dtype=np.float32).astype(rdt)
-    u = np.exp(1j * phi).astype(cdt)
+    I = np.asarray(I)
+    pw = None if p is None else np.asarray(p, dtype=np.float32).astype(rdt)
+    energy = None if pw is None else float(np.sum(pw.astype(np.float64) ** 2))
+    m = target_amplitude(I, dtype=rdt, energy=energy)
+    if init == "phase":
+        phi = np.asarray(phi0, dtype=np.float32).astype(rdt)
+        u = np.exp(1j * phi).astype(cdt)
+        if pw is not None:
+            u = (pw * u).astype(cdt)
+    elif init == "target":
+        u = proj_S(ifft2u(m.astype(cdt)), pw).astype(cdt)
+    else:
+        raise ValueError("init must be 'phase' or 'target'")
     r_hist, g_hist = [], []
     for _ in range(iters):
-        u, r, g = gs_step(u, m)
+        u, r, g = gs_step(u, m, pw)
         r_hist.append(r)
         g_hist.append(g)
     if final_residual:
-        r_hist.append(gap_to_M(u, m))
+        r_hist.append(gap_to_M(u, m, pw))
     phase = np.angle(u)
     phase = np.where(phase <= -np.pi, np.pi, phase)
     return {

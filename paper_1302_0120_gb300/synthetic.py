@@ -83,6 +83,28 @@ def random_phase(seed: int, ny: int, nx: int) -> np.ndarray:
     return (rng.random((ny, nx)) * (2.0 * np.pi)).astype(np.float32)
 
 
+def siemens_star(ny: int, nx: int, spokes: int = 36, radius_frac: float = 0.4) -> np.ndarray:
+    """The resolution target of Sec. IV: a Siemens star with ``spokes`` dark
+    and ``spokes`` lit sectors inside a disc of radius ``radius_frac * min(ny, nx)``,
+    centred on the grid centre and then moved to DFT order (centre at [0, 0]).
+    Intensity 1 (lit) or 0, float32."""
+    y = (np.arange(ny) - ny // 2)[:, None].astype(np.float64)
+    x = (np.arange(nx) - nx // 2)[None, :].astype(np.float64)
+    r = np.hypot(x, y)
+    th = np.arctan2(y, x)
+    star = (np.sin(spokes * th) > 0) & (r < radius_frac * min(ny, nx))
+    return np.fft.ifftshift(star.astype(np.float32))
+
+
+def laser_amplitude(ny: int, nx: int, waist_frac: float = 0.45, floor: float = 0.01) -> np.ndarray:
+    """A Gaussian beam profile on the SLM (the amplitude p of the SLM set S),
+    exp(-(r / w)^2) with w = waist_frac * size along each axis, plus a floor;
+    float32 [ny, nx]."""
+    y = (np.arange(ny) - ny / 2)[:, None] / (waist_frac * ny)
+    x = (np.arange(nx) - nx / 2)[None, :] / (waist_frac * nx)
+    return (np.exp(-(x * x + y * y)) + floor).astype(np.float32)
+
+
 def neuron_positions(seed: int, count: int, ny: int, nx: int) -> np.ndarray:
     """A fixed set of ``count`` neuron positions for request streams."""
     rng = np.random.default_rng([seed, 0xCE11])

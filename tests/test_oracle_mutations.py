@@ -66,6 +66,15 @@ def _grad_dropped_factor(phi, I):
     return 2.0 * np.imag(np.conj(x) * sfft.ifft2(r * y))
 
 
+def _norm_S_ignores_p(shape, p):
+    return np.sqrt(float(np.prod(shape)))
+
+
+def _amp_unit_energy(I, dtype=np.float64, energy=None):
+    I = np.asarray(I, dtype=np.float64)
+    return (np.sqrt(I) * np.sqrt(I.size / I.sum())).astype(dtype)
+
+
 MUTATIONS = [
     ("fft2u", _wrong_sign_fft, lambda: P.check_fft_direct((8, 32))),
     ("fft2u", _unnormalised_fft, P.check_fft_identities),
@@ -77,6 +86,8 @@ MUTATIONS = [
     ("gs_step", _gs_step_late_residual, P.check_gap_definitions),
     ("intensity_loss_grad", _grad_wrong_sign, P.check_gradient_fd),
     ("intensity_loss_grad", _grad_dropped_factor, P.check_gradient_fd),
+    ("_norm_S", _norm_S_ignores_p, P.check_slm_amplitude_chain),
+    ("target_amplitude", _amp_unit_energy, P.check_slm_amplitude_chain),
 ]
 
 

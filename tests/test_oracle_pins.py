@@ -277,6 +277,78 @@ def test_phase_range():
     assert np.all(ph > -np.pi) and np.all(ph <= np.pi)
 
 
+# ---------------------------------------------------------------- SLM amplitude p and the target start
+
+
+def laser_profile(ny, nx, seed=0):
+    """A Gaussian beam on the SLM with a little seeded ripple, float32, > 0."""
+    y = (np.arange(ny) - ny / 2)[:, None] / (0.45 * ny)
+    x = (np.arange(nx) - nx / 2)[None, :] / (0.45 * nx)
+    rng = np.random.default_rng(seed)
+    p = np.exp(-(x * x + y * y)) * (1 + 0.05 * rng.standard_normal((ny, nx)))
+    return np.abs(p).astype(np.float32) + 0.01
+
+
+def check_slm_amplitude_chain(ny=32, nx=64, iters=25):
+    p = laser_profile(ny, nx)
+    I = S.spot_target(12, ny, nx, 6, (0.5, 1.0))
+    phi0 = S.random_phase(12, ny, nx)
+    res = O.gs_run(I, phi0, iters, p=p)
+    r, g = res["r"], res["g"]
+    assert np.all(r[:-1] - g >= -1e-12) and np.all(g - r[1:] >= -1e-12)
+    assert np.allclose(np.abs(res["u"]), p.astype(np.float64), rtol=0, atol=1e-12)  # u^K in S
+    m = O.target_amplitude(I, energy=float(np.sum(p.astype(np.float64) ** 2)))
+    assert abs(np.sum(m * m) - np.sum(p.astype(np.float64) ** 2)) <= 1e-9 * np.sum(m * m)
+    # the residual is the object-domain distance to M divided by ||p||
+    u = res["u"]
+    direct = np.linalg.norm(u - O.proj_M(u, m)) / np.linalg.norm(p.astype(np.float64))
+    assert abs(res["r"][-1] - direct) <= 1e-12
+
+
+def test_slm_amplitude_chain():
+    check_slm_amplitude_chain()
+
+
+def test_slm_amplitude_consistent_fixed_point():
+    n = 32
+    p = laser_profile(n, n, 3)
+    rng = np.random.default_rng(8)
+    phi_t = (rng.random((n, n)) * 2 * np.pi).astype(np.float32)
+    I = np.abs(O.fft2u(p.astype(np.float64) * np.exp(1j * phi_t.astype(np.float64)))) ** 2
+    res = O.gs_run(I, phi_t, 1, p=p)
+    assert res["r"][0] <= 1e-12 and res["g"][0] <= 1e-12 and res["r"][1] <= 1e-12
+
+
+def test_slm_amplitude_scale_invariance():
+    """Only phases survive the projections: scaling p leaves the phases."""
+    p = laser_profile(32, 32, 5)
+    I, phi0, _ = S.workload("spots64")
+    I, phi0 = I[:32, :32].copy(), phi0[:32, :32].copy()
+    I[3, 3] = 1.0
+    a = O.gs_run(I, phi0, 5, p=p)
+    b = O.gs_run(I, phi0, 5, p=(4.0 * p).astype(np.float32))  # exact in float32
+    assert np.max(np.abs(np.exp(1j * a["phase"]) - np.exp(1j * b["phase"]))) <= 1e-9
+    assert np.allclose(a["r"], b["r"], rtol=1e-12, atol=0)
+
+
+def test_target_start_is_hermitian():
+    """u0 = P_S(F^{-1} m) with real m is conjugate-symmetric, u0(-x) = conj(u0(x)),
+    so F u stays real along the iteration (the binary-phase Fourier plane of
+    this start, a consequence of the reading)."""
+    I, phi0, _ = S.workload("spots64")
+    res0 = O.gs_run(I, phi0, 0, init="target")
+    u0 = res0["u"]
+    flip = np.roll(np.flip(u0, axis=(0, 1)), (1, 1), axis=(0, 1))  # u0[-y, -x]
+    assert np.max(np.abs(flip - np.conj(u0))) <= 1e-9  # v/|v| amplifies rounding where |v| is tiny
+    res1 = O.gs_run(I, phi0, 1, init="target")
+    Fu = O.fft2u(res1["u"])
+    # real up to rounding (amplified where |v| is tiny, so checked after one step)
+    assert np.max(np.abs(Fu.imag)) <= 1e-7 * np.max(np.abs(Fu))
+    res = O.gs_run(I, phi0, 4, init="target")
+    r, g = res["r"], res["g"]
+    assert np.all(r[:-1] - g >= -1e-12) and np.all(g - r[1:] >= -1e-12)
+
+
 # ---------------------------------------------------------------- gradient (differentiable form)
 
 
