@@ -63,7 +63,12 @@ enum {
 /* Flags for gs_create. */
 enum {
   /* After the last iteration also compute r^K (one forward column pass). */
-  GS_FINAL_RESIDUAL = 1u
+  GS_FINAL_RESIDUAL = 1u,
+  /* Start from the target instead of an initial phase: u^0 = P_S(F^{-1} m),
+   * the initial condition of Sec. IV (P_M uhat^0 of the paper, garbled in
+   * the text, read this way). phase_in is ignored and may be NULL. With a
+   * real target this start is conjugate-symmetric, so F u stays real. */
+  GS_INIT_FROM_TARGET = 2u
 };
 
 typedef struct gs_ctx gs_ctx;
@@ -75,7 +80,7 @@ typedef struct gs_ctx gs_ctx;
  * (Sec. II: "n_x, n_y the respective number of pixels").
  *   out     host pointer that receives the context (set to NULL on failure).
  *   nx, ny  powers of two in [32, 4096].
- *   flags   GS_* flags (GS_FINAL_RESIDUAL).
+ *   flags   GS_* flags (GS_FINAL_RESIDUAL, GS_INIT_FROM_TARGET).
  *   stream  a cudaStream_t, or NULL for the legacy default stream. All later
  *           work of this context is enqueued on it.
  * The context owns its device workspace (gs_workspace_bytes bytes): the field,
@@ -103,7 +108,8 @@ int gs_create_batched(gs_ctx** out, int nx, int ny, int max_batch, unsigned flag
  * u^K and the gaps of Eq. (gap-error).
  *   target_intensity  device, float [ny][nx], DFT order, >= 0, finite, not all 0.
  *   phase_in          device, float [ny][nx], radians. May alias phase_out
- *                     (warm start from a previous mask).
+ *                     (warm start from a previous mask). Ignored (may be
+ *                     NULL) with GS_INIT_FROM_TARGET.
  *   iters             K >= 0. K == 0 computes r^0 only (with GS_FINAL_RESIDUAL)
  *                     and writes phase_out = arg exp(i phase_in).
  *   phase_out         device, float [ny][nx], arg u^K in (-pi, pi].
@@ -156,6 +162,21 @@ int gs_run_host(gs_ctx* c, const float* target_intensity, const float* phase_in,
  * error wins), or GS_ECUDA if the stream reports an error. Clears the status.
  */
 int gs_status(gs_ctx* c);
+
+/*
+ * gs_set_slm_amplitude -- the laser amplitude p on the SLM for later runs.
+ *
+ * Operation: replaces the unit amplitude of the SLM set S by p, Eq.
+ * (slm-constraint): runs start from u^0 = p exp(i phase_in), P_S maps v to
+ * p v/|v| (Eq. e:PS), the target amplitude carries the energy sum p^2, and
+ * both gaps are divided by ||p||_2 instead of sqrt(N).
+ *   amplitude  device, float [ny][nx], >= 0 and finite, caller-owned: it must
+ *              stay valid while runs that use it execute. NULL restores p = 1.
+ * Enqueues an FP64 reduction of sum p^2 on the context stream (asynchronous).
+ * A negative or non-finite p makes later runs report GS_ENUMERIC.
+ * Returns GS_EINVAL for a NULL context, GS_ECUDA if the launch fails.
+ */
+int gs_set_slm_amplitude(gs_ctx* c, const float* amplitude);
 
 /*
  * gs_set_grid -- tuning knob: number of thread blocks of the iteration kernel.

@@ -12,6 +12,7 @@ from ._binding import (  # noqa: F401
     GS_ENUMERIC,
     GS_ETIMEOUT,
     GS_FINAL_RESIDUAL,
+    GS_INIT_FROM_TARGET,
     GS_OK,
     GSError,
     gs_create,
@@ -22,6 +23,7 @@ from ._binding import (  # noqa: F401
     gs_run_batched,
     gs_run_host,
     gs_set_grid,
+    gs_set_slm_amplitude,
     gs_status,
     gs_strerror,
     gs_workspace_bytes,

@@ -20,6 +20,7 @@ GS_ETIMEOUT = -4
 GS_ENUMERIC = -5
 
 GS_FINAL_RESIDUAL = 1
+GS_INIT_FROM_TARGET = 2
 
 _c_int = ctypes.c_int
 _c_uint = ctypes.c_uint
@@ -41,6 +42,7 @@ SIGNATURES = {
     "gs_run_batched": (_c_int, [_vp, _c_int, _vp, _vp, _c_int, _vp, _vp, _vp]),
     "gs_workspace_bytes_batched": (ctypes.c_size_t, [_c_int, _c_int, _c_int, _c_uint]),
     "gs_loss_grad": (_c_int, [_vp, _vp, _vp, _vp, _vp]),
+    "gs_set_slm_amplitude": (_c_int, [_vp, _vp]),
 }
 
 _lib = None
@@ -129,6 +131,11 @@ def gs_loss_grad(ctx: int, target_intensity: int, phase: int, loss_out: int, gra
 
 def gs_status(ctx: int) -> int:
     return lib().gs_status(_vp(ctx))
+
+
+def gs_set_slm_amplitude(ctx: int, amplitude: int) -> int:
+    """Set (device pointer) or clear (0) the SLM amplitude p; returns the status code."""
+    return lib().gs_set_slm_amplitude(_vp(ctx), _vp(amplitude or 0))
 
 
 def gs_set_grid(ctx: int, ctas: int) -> int:

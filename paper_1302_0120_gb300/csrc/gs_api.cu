@@ -32,7 +32,7 @@ constexpr int kTwiddleEntries = 31 * 32 + 31 * 1024;
 
 // Offsets of the sub-buffers of one workspace allocation.
 struct Layout {
-  size_t B, mT, partials, twx, twy, bar, status, abort_flag, mask_flags, dI, dphi, total;
+  size_t B, mT, partials, twx, twy, ones, bar, status, abort_flag, mask_flags, energy, dI, dphi, total;
 };
 
 Layout make_layout(int nx, int ny, int max_batch) {
@@ -46,10 +46,12 @@ Layout make_layout(int nx, int ny, int max_batch) {
   o = align_up(o + static_cast<size_t>(gsk::kSlots) * max_batch * gsk::kMaxGrid * sizeof(double));
   L.twx = o;        o = align_up(o + static_cast<size_t>(kTwiddleEntries) * sizeof(float2));
   L.twy = o;        o = align_up(o + static_cast<size_t>(kTwiddleEntries) * sizeof(float2));
+  L.ones = o;       o = align_up(o + 4096 * sizeof(float));
   L.bar = o;        o = align_up(o + sizeof(unsigned));
   L.status = o;     o = align_up(o + sizeof(int));
   L.abort_flag = o; o = align_up(o + sizeof(int));
   L.mask_flags = o; o = align_up(o + gsk::kMaxBatch * sizeof(int));
+  L.energy = o;     o = align_up(o + sizeof(double));
   L.dI = o;         o = align_up(o + n * sizeof(float));
   L.dphi = o;       o = align_up(o + n * sizeof(float));
   L.total = o;
@@ -99,6 +101,7 @@ struct gs_ctx {
   int num_sms = 0;
   int blocks_per_sm = 0;
   int grid_override = 0;
+  const float* p_slm = nullptr;  // caller-owned SLM amplitude, or null (p = 1)
   unsigned extra_arrivals = 0;
   Layout L{};
   unsigned char* ws = nullptr;
@@ -165,7 +168,7 @@ int gs_create_batched(gs_ctx** out, int nx, int ny, int max_batch, unsigned flag
   if (out == nullptr) return GS_EINVAL;
   *out = nullptr;
   if (!valid_dim(nx) || !valid_dim(ny) || max_batch < 1 || max_batch > gsk::kMaxBatch) return GS_EINVAL;
-  if ((flags & ~static_cast<unsigned>(GS_FINAL_RESIDUAL)) != 0) return GS_EINVAL;
+  if ((flags & ~static_cast<unsigned>(GS_FINAL_RESIDUAL | GS_INIT_FROM_TARGET)) != 0) return GS_EINVAL;
   gs_ctx* c = new (std::nothrow) gs_ctx();
   if (c == nullptr) return GS_ENOMEM;
   c->nx = nx;
@@ -188,7 +191,9 @@ int gs_create_batched(gs_ctx** out, int nx, int ny, int max_batch, unsigned flag
   }
   const std::vector<float2> wx = twiddles(nx);
   const std::vector<float2> wy = twiddles(ny);
+  const std::vector<float> ones(4096, 1.0f);
   bool ok = cudaMemcpy(c->ws + c->L.twx, wx.data(), wx.size() * sizeof(float2), cudaMemcpyHostToDevice) == cudaSuccess &&
+            cudaMemcpy(c->ws + c->L.ones, ones.data(), ones.size() * sizeof(float), cudaMemcpyHostToDevice) == cudaSuccess &&
             cudaMemcpy(c->ws + c->L.twy, wy.data(), wy.size() * sizeof(float2), cudaMemcpyHostToDevice) == cudaSuccess &&
             cudaMemset(c->ws + c->L.bar, 0, c->L.dI - c->L.bar) == cudaSuccess;
   if (!ok) {
@@ -208,8 +213,9 @@ int gs_run(gs_ctx* c, const float* target_intensity, const float* phase_in, int 
 
 int gs_run_batched(gs_ctx* c, int batch, const float* target_intensity, const float* phase_in, int iters,
                    float* phase_out, double* residual_out, double* object_gap_out) {
-  if (c == nullptr || target_intensity == nullptr || phase_in == nullptr || phase_out == nullptr || iters < 0 ||
-      batch < 1 || batch > c->max_batch)
+  const bool from_target = (c != nullptr) && (c->flags & GS_INIT_FROM_TARGET);
+  if (c == nullptr || target_intensity == nullptr || (phase_in == nullptr && !from_target) ||
+      phase_out == nullptr || iters < 0 || batch < 1 || batch > c->max_batch)
     return GS_EINVAL;
   const int grid = choose_grid(c);
   gsk::Params p{};
@@ -235,6 +241,10 @@ int gs_run_batched(gs_ctx* c, int batch, const float* target_intensity, const fl
   p.status = at<int>(c, c->L.status);
   p.abort_flag = at<int>(c, c->L.abort_flag);
   p.mask_flags = at<int>(c, c->L.mask_flags);
+  p.p_slm = c->p_slm;
+  p.energy = at<double>(c, c->L.energy);
+  p.ones = at<float>(c, c->L.ones);
+  p.init_target = from_target ? 1 : 0;
   p.iters = iters;
   p.final_resid = (c->flags & GS_FINAL_RESIDUAL) ? 1 : 0;
   p.extra_arrivals = c->extra_arrivals;
@@ -282,7 +292,9 @@ int gs_status(gs_ctx* c) {
 
 int gs_run_host(gs_ctx* c, const float* target_intensity, const float* phase_in, int iters, float* phase_out,
                 double* residual_out, double* object_gap_out) {
-  if (c == nullptr || target_intensity == nullptr || phase_in == nullptr || phase_out == nullptr || iters < 0)
+  const bool from_target = (c != nullptr) && (c->flags & GS_INIT_FROM_TARGET);
+  if (c == nullptr || target_intensity == nullptr || (phase_in == nullptr && !from_target) || phase_out == nullptr ||
+      iters < 0)
     return GS_EINVAL;
   const size_t n = static_cast<size_t>(c->nx) * c->ny;
   const size_t nres = static_cast<size_t>(iters) + 1;
@@ -306,7 +318,8 @@ int gs_run_host(gs_ctx* c, const float* target_intensity, const float* phase_in,
   double* dr = residual_out ? c->dres : nullptr;
   double* dg = object_gap_out ? c->dres + nres : nullptr;
   if (cudaMemcpyAsync(dI, target_intensity, n * sizeof(float), cudaMemcpyHostToDevice, c->stream) != cudaSuccess ||
-      cudaMemcpyAsync(dphi, phase_in, n * sizeof(float), cudaMemcpyHostToDevice, c->stream) != cudaSuccess) {
+      (phase_in != nullptr &&
+       cudaMemcpyAsync(dphi, phase_in, n * sizeof(float), cudaMemcpyHostToDevice, c->stream) != cudaSuccess)) {
     cudaGetLastError();
     return GS_ECUDA;
   }
@@ -344,6 +357,19 @@ int gs_loss_grad(gs_ctx* c, const float* target_intensity, const float* phase, d
       cudaMemsetAsync(p.abort_flag, 0, sizeof(int), c->stream) != cudaSuccess ||
       gsk::launch_loss(p, choose_grid(c), c->stream) != cudaSuccess) {
     cudaGetLastError();
+    return GS_ECUDA;
+  }
+  return GS_OK;
+}
+
+int gs_set_slm_amplitude(gs_ctx* c, const float* amplitude) {
+  if (c == nullptr) return GS_EINVAL;
+  c->p_slm = amplitude;
+  if (amplitude != nullptr &&
+      gsk::launch_energy(amplitude, static_cast<long long>(c->nx) * c->ny, at<double>(c, c->L.energy), c->stream) !=
+          cudaSuccess) {
+    cudaGetLastError();
+    c->p_slm = nullptr;
     return GS_ECUDA;
   }
   return GS_OK;

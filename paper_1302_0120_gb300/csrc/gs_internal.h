@@ -40,6 +40,10 @@ struct Params {
   int do_init;         // this launch computes m and u^0
   int do_final;        // this launch ends the run (phase out, final residual)
   int final_resid;     // compute r^K
+  const float* p_slm;  // SLM amplitude p [ny][nx] (Eq. slm-constraint), or null for p = 1
+  const double* energy;  // sum p^2 (FP64, workspace) when p_slm is set
+  const float* ones;   // a row of max(nx, ny) ones (workspace): p when p_slm is null
+  int init_target;     // start from P_S(F^{-1} m) instead of p exp(i phi_in)
   unsigned extra_arrivals;  // test hook: arrivals a barrier waits for beyond the grid (0 in use)
   float inv_sqrt_n;    // 1/sqrt(N)
   double inv_n;        // 1/N
@@ -70,6 +74,8 @@ struct LossParams {
 
 cudaError_t launch_loss(const LossParams& p, int grid, cudaStream_t s);
 cudaError_t launch_iterations(const Params& p, int grid, cudaStream_t s);
+// sum p^2 of an SLM amplitude into *energy (NaN if p has a negative or non-finite value)
+cudaError_t launch_energy(const float* p, long long n, double* energy, cudaStream_t s);
 cudaError_t iteration_occupancy(int nx, int ny, int* blocks_per_sm);
 
 }  // namespace gsk

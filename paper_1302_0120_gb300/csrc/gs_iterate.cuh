@@ -40,7 +40,7 @@
 
 namespace gsk {
 
-enum PassKind { kInit = 0, kCol = 1, kRow = 2, kResid = 3 };
+enum PassKind { kInit = 0, kCol = 1, kRow = 2, kResid = 3, kInitM = 4 };
 
 // A barrier wait gives up after this long and reports GS_ETIMEOUT.
 constexpr unsigned long long kBarrierTimeoutNs = 1000000000ull;
@@ -79,6 +79,11 @@ __device__ __forceinline__ unsigned long long global_ns() {
 __device__ __forceinline__ void fail(const Params& p, int code) {
   atomicCAS(p.status, 0, code);
   atomicExch(p.abort_flag, 1);
+}
+
+// sum p^2 of the SLM amplitude (N for p = 1): the energy of every field in S.
+__device__ __forceinline__ double energy_of(const Params& p) {
+  return p.p_slm ? *p.energy : static_cast<double>(p.nx) * p.ny;
 }
 
 // Record an error for the host without stopping the run (other masks go on).
@@ -229,11 +234,13 @@ __device__ __forceinline__ double run_pass(const Params& p, int mb, int kind, bo
         // buffer keeps a single copy of sincosf (and atan2f) in the kernel.
         const float* ph = p.phi_in + moff + static_cast<size_t>(ridx) * N + t;
         float2* su = grp.sm + t;
+        const float* pp = p.p_slm ? p.p_slm + static_cast<size_t>(ridx) * N + t : nullptr;
 #pragma unroll 1
         for (int i = 0; i < 32; ++i) {
           float s, c;
           sincosf(ph[T * i], &s, &c);
-          su[T * i] = make_float2(c, s);
+          const float a = pp ? pp[T * i] : 1.f;  // u0 = p exp(i phi0)
+          su[T * i] = make_float2(a * c, a * s);
         }
         if (last && valid) {  // zero iterations: the mask is arg exp(i phi^0)
           float* po = p.phi_out + moff + static_cast<size_t>(idx) * N + t;
@@ -258,16 +265,43 @@ __device__ __forceinline__ double run_pass(const Params& p, int mb, int kind, bo
         group_fft<LOGN>(v, grp, stw);
         if (h != 0 || kind != kRow) continue;
         // v = swap(IDFT_x(B)) = swap(sqrt(N) P_M u^nu). Gap to S and Eq. (e:PS).
+        if (p.p_slm == nullptr) {  // p = 1
 #pragma unroll
-        for (int i = 0; i < 32; ++i) {
-          const float vx = v[i].y;
-          const float vy = v[i].x;
-          const float a2 = vx * vx + vy * vy;
-          const float rs = rsqrtf(a2);
-          const float mag = a2 > 0.f ? a2 * rs : 0.f;
-          const float d = mag * inv_sqrt_n - 1.f;
-          part += d * d;
-          v[i] = a2 > 0.f ? make_float2(vx * rs, vy * rs) : make_float2(1.f, 0.f);
+          for (int i = 0; i < 32; ++i) {
+            const float vx = v[i].y;
+            const float vy = v[i].x;
+            const float a2 = vx * vx + vy * vy;
+            const float rs = rsqrtf(a2);
+            const float mag = a2 > 0.f ? a2 * rs : 0.f;
+            const float d = mag * inv_sqrt_n - 1.f;
+            part += d * d;
+            v[i] = a2 > 0.f ? make_float2(vx * rs, vy * rs) : make_float2(1.f, 0.f);
+          }
+        } else {
+          // SLM amplitude p: u = p v/|v|, gap |P_M u| - p. A rolled loop
+          // through the group's exchange buffer keeps this variant out of the
+          // unrolled hot code.
+          float2* su = grp.sm + t;
+          const float* pp = p.p_slm + static_cast<size_t>(ridx) * N + t;
+#pragma unroll
+          for (int i = 0; i < 32; ++i) su[T * i] = v[i];
+#pragma unroll 1
+          for (int i = 0; i < 32; ++i) {
+            const float a = pp[T * i];
+            const float2 w = su[T * i];
+            const float vx = w.y;
+            const float vy = w.x;
+            const float a2 = vx * vx + vy * vy;
+            const float rs = rsqrtf(a2);
+            const float mag = a2 > 0.f ? a2 * rs : 0.f;
+            const float d = mag * inv_sqrt_n - a;
+            part += d * d;
+            const float f = a * rs;
+            su[T * i] = a2 > 0.f ? make_float2(vx * f, vy * f) : make_float2(a, 0.f);
+          }
+#pragma unroll
+          for (int i = 0; i < 32; ++i) v[i] = su[T * i];
+          grp.sync();  // the buffer is reused by the next transform's exchange
         }
         if (last) {
           // The mask, once per run: through the group's exchange buffer so
@@ -308,15 +342,16 @@ __device__ __forceinline__ double run_pass(const Params& p, int mb, int kind, bo
   const int gq = gact ? g : 0;                            // idle groups read a valid column
   for (int cb = lo; cb < hi; ++cb) {
     __syncthreads();  // the previous round is done with the staging buffers
+    const bool from_m = (kind == kInitM);  // transform m itself (the target start)
     if (threadIdx.x == 0) {
-      if (kind == kCol) bulk_wait_read_all();  // the previous bulk store has read blk
+      bulk_wait_read_all();  // a previous bulk store has read blk
       fence_proxy_async_smem();
       const int mkey = mb * L::NBLK + cb;  // which mask's amplitude block is resident
       const bool need_m = (sh.m_block != mkey);
-      const unsigned bytes_b = L::BLOCK * 8u;
+      const unsigned bytes_b = from_m ? 0u : L::BLOCK * 8u;
       const unsigned bytes_m = L::BLOCK * 4u;
       mbar_arrive_expect_tx(&sh.mbar, bytes_b + (need_m ? bytes_m : 0u));
-      bulk_g2s(blk, Bm + static_cast<size_t>(cb) * L::BLOCK, bytes_b, &sh.mbar);
+      if (!from_m) bulk_g2s(blk, Bm + static_cast<size_t>(cb) * L::BLOCK, bytes_b, &sh.mbar);
       // columns cb W .. cb W + W - 1 of m are contiguous in the transposed amplitude
       if (need_m) bulk_g2s(ms, mTm + static_cast<size_t>(cb) * L::BLOCK, bytes_m, &sh.mbar);
       sh.m_block = mkey;
@@ -330,6 +365,16 @@ __device__ __forceinline__ double run_pass(const Params& p, int mb, int kind, bo
     } else if (threadIdx.x == 0) {
       sh.pending = 0;
     }
+    if (from_m) {
+      // The target start transforms m itself: stage swap((m, 0)) in the field
+      // layout, so the forward DFT below yields swap(IDFT_y(m)).
+      for (int e = threadIdx.x; e < L::BLOCK; e += kThreads) {
+        const int k = e % W;
+        const int y = e / W;
+        blk[L::boff(y, k)] = make_float2(0.f, ms[k * N + y]);
+      }
+      __syncthreads();
+    }
     if (wact) {
       float2 v[32];
 #pragma unroll
@@ -338,7 +383,7 @@ __device__ __forceinline__ double run_pass(const Params& p, int mb, int kind, bo
 #pragma unroll 1
       for (int h = 0; h < nfft; ++h) {
         group_fft<LOGN>(v, grp, stw);
-        if (h != 0) continue;
+        if (h != 0 || from_m) continue;
         // v = Y = F u^nu along this column. Residual and Eq. (e:Mhat).
         const float* mcol = ms + gq * N + t;
 #pragma unroll
@@ -358,12 +403,12 @@ __device__ __forceinline__ double run_pass(const Params& p, int mb, int kind, bo
         }
       }
       if (gact) acc += static_cast<double>(part);
-      if (kind == kCol && gact) {
+      if ((kind == kCol || from_m) && gact) {
 #pragma unroll
         for (int i = 0; i < 32; ++i) blk[L::boff(t + T * i, g)] = v[i];
       }
     }
-    if (kind == kCol) {
+    if (kind == kCol || from_m) {
       __syncthreads();
       if (threadIdx.x == 0) {
         fence_proxy_async_smem();
@@ -373,7 +418,7 @@ __device__ __forceinline__ double run_pass(const Params& p, int mb, int kind, bo
     }
   }
   // the field must be in global memory before the grid barrier releases the next pass
-  if (kind == kCol && threadIdx.x == 0) bulk_wait_all();
+  if ((kind == kCol || kind == kInitM) && threadIdx.x == 0) bulk_wait_all();
   }
   return acc;
 }
@@ -458,10 +503,11 @@ __global__ void __launch_bounds__(kThreads, 1) gs_iterate(const Params p) {
       for (int mb = 0; mb < p.batch; ++mb) {
         const double total = warp_slot_sum(p, mb);
         if (threadIdx.x == 0) {
-          const bool bad = !(total > 0.0) || !(total <= DBL_MAX);
+          const double ep = energy_of(p);
+          const bool bad = !(total > 0.0) || !(total <= DBL_MAX) || !(ep > 0.0) || !(ep <= DBL_MAX);
           sh.bad[mb] = bad ? 1 : 0;
           if (b == 0) p.mask_flags[mb] = bad ? 1 : 0;  // for later launches of the run
-          sh.scale[mb] = bad ? 0.f : static_cast<float>(sqrt(static_cast<double>(p.nx) * p.ny / total));
+          sh.scale[mb] = bad ? 0.f : static_cast<float>(sqrt(energy_of(p) / total));
         }
       }
     }
@@ -499,15 +545,16 @@ __global__ void __launch_bounds__(kThreads, 1) gs_iterate(const Params p) {
   // into partial rows (1 + q) * batch + mask.
   const int nit = p.it1 - p.it0;
   const int resid = (p.do_final && p.final_resid) ? 1 : 0;
-  const int npass = p.do_init + 2 * nit + resid;
+  const int ninit = p.do_init ? (p.init_target ? 2 : 1) : 0;  // target start: columns then rows
+  const int npass = ninit + 2 * nit + resid;
   for (int q0 = 0; q0 < npass; ++q0) {
     int kind;
     int slot = -1;
     bool last = false;
-    const int q = q0 - p.do_init;
+    const int q = q0 - ninit;
     if (q < 0) {
-      kind = kInit;
-      last = p.do_final && p.iters == 0;
+      kind = !p.init_target ? kInit : (q == -2 ? kInitM : kRow);
+      last = p.do_final && p.iters == 0 && q == -1;
     } else if (q < 2 * nit) {
       kind = (q & 1) ? kRow : kCol;
       slot = 1 + q;
@@ -546,7 +593,7 @@ __global__ void __launch_bounds__(kThreads, 1) gs_iterate(const Params p) {
       if (sh.bad[mb]) continue;
       const double sum = warp_slot_sum(p, slot * p.batch + mb);
       if (threadIdx.x == 0) {
-        const double val = sqrt(sum * p.inv_n);
+        const double val = sqrt(sum / energy_of(p));
         const int q = slot - 1;
         if (q < 2 * nit) {
           const int nu = p.it0 + (q >> 1);

@@ -1,7 +1,36 @@
 // gs_launch.cu -- host helpers that select, size and launch the iteration kernel.
+#include <cfloat>
+
 #include "gs_internal.h"
 
 namespace gsk {
+
+// sum p^2 in FP64 by one block in a fixed order; NaN if any p is negative or
+// not finite.
+__global__ void __launch_bounds__(1024) energy_kernel(const float* __restrict__ p, long long n, double* out) {
+  __shared__ double red[32];
+  double acc = 0.0;
+  bool bad = false;
+  for (long long e = threadIdx.x; e < n; e += blockDim.x) {
+    const float x = p[e];
+    bad |= !(x >= 0.f && x <= FLT_MAX);
+    acc += static_cast<double>(x) * static_cast<double>(x);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  const int any_bad = __syncthreads_or(bad);
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int w = 0; w < static_cast<int>(blockDim.x >> 5); ++w) s += red[w];
+    out[0] = any_bad ? __longlong_as_double(0x7ff8000000000000ll) : s;
+  }
+}
+
+cudaError_t launch_energy(const float* p, long long n, double* energy, cudaStream_t s) {
+  energy_kernel<<<1, 1024, 0, s>>>(p, n, energy);
+  return cudaGetLastError();
+}
 
 // Each is defined in the gs_inst.cu object compiled with GS_LX = LX.
 extern template const void* iterate_kernel_lx<5>(int);

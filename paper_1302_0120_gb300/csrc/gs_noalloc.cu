@@ -30,7 +30,8 @@ constexpr size_t kOffM = align_up(kOffB + static_cast<size_t>(kMaxPixels) * 8);
 constexpr size_t kOffPartials = align_up(kOffM + static_cast<size_t>(kMaxPixels) * 4);
 constexpr size_t kOffTwx = align_up(kOffPartials + static_cast<size_t>(gsk::kSlots) * kMaxGrid * 8);
 constexpr size_t kOffTwy = align_up(kOffTwx + static_cast<size_t>(kTwEntries) * 8);
-constexpr size_t kOffWords = align_up(kOffTwy + static_cast<size_t>(kTwEntries) * 8);
+constexpr size_t kOffOnes = align_up(kOffTwy + static_cast<size_t>(kTwEntries) * 8);
+constexpr size_t kOffWords = align_up(kOffOnes + 4096 * sizeof(float));
 constexpr size_t kScratchBytes = align_up(kOffWords + (3 + gsk::kMaxBatch) * sizeof(int));  // barrier, status, abort, mask flags
 
 // The shared scratch of every gs_run_noalloc call on this device (about 4 MiB).
@@ -84,6 +85,10 @@ __global__ void twiddle_tables(float2* tw, int n) {
   }
 }
 
+__global__ void fill_ones(float* x, int n) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) x[e] = 1.0f;
+}
+
 // Device address of the static scratch on the current device; looked up on
 // the first call for that device.
 int scratch_for_current_device(unsigned char** base, int* num_sms) {
@@ -114,8 +119,10 @@ extern "C" int gs_run_noalloc(int nx, int ny, unsigned flags, void* stream, cons
                               const float* phase_in, int iters, float* phase_out, double* residual_out,
                               double* object_gap_out, int* device_status) {
   if (!valid_dim(nx) || !valid_dim(ny) || static_cast<long long>(nx) * ny > kMaxPixels) return GS_EINVAL;
-  if ((flags & ~static_cast<unsigned>(GS_FINAL_RESIDUAL)) != 0) return GS_EINVAL;
-  if (target_intensity == nullptr || phase_in == nullptr || phase_out == nullptr || iters < 0) return GS_EINVAL;
+  if ((flags & ~static_cast<unsigned>(GS_FINAL_RESIDUAL | GS_INIT_FROM_TARGET)) != 0) return GS_EINVAL;
+  const bool from_target = (flags & GS_INIT_FROM_TARGET) != 0;
+  if (target_intensity == nullptr || (phase_in == nullptr && !from_target) || phase_out == nullptr || iters < 0)
+    return GS_EINVAL;
   unsigned char* base = nullptr;
   int num_sms = 0;
   int rc = scratch_for_current_device(&base, &num_sms);
@@ -150,7 +157,9 @@ extern "C" int gs_run_noalloc(int nx, int ny, unsigned flags, void* stream, cons
   p.status = reinterpret_cast<int*>(base + kOffWords) + 1;
   p.abort_flag = reinterpret_cast<int*>(base + kOffWords) + 2;
   p.mask_flags = reinterpret_cast<int*>(base + kOffWords) + 3;
+  p.ones = reinterpret_cast<const float*>(base + kOffOnes);
   p.batch = 1;
+  p.init_target = from_target ? 1 : 0;
   p.mstride = static_cast<long long>(nx) * ny;
   p.rstride = iters + ((flags & GS_FINAL_RESIDUAL) ? 1 : 0);
   p.gstride = iters;
@@ -167,6 +176,7 @@ extern "C" int gs_run_noalloc(int nx, int ny, unsigned flags, void* stream, cons
     cudaGetLastError();
     return GS_ECUDA;
   }
+  fill_ones<<<16, 256, 0, s>>>(reinterpret_cast<float*>(base + kOffOnes), 4096);
   twiddle_tables<<<64, 256, 0, s>>>(const_cast<float2*>(p.twx), nx);
   twiddle_tables<<<64, 256, 0, s>>>(const_cast<float2*>(p.twy), ny);
   if (cudaGetLastError() != cudaSuccess) return GS_ECUDA;

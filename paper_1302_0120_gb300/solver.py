@@ -18,7 +18,8 @@ class GerchbergSaxton:
     construction). Arrays are [ny, nx] float32, target intensity in DFT order.
     """
 
-    def __init__(self, nx: int, ny: int, final_residual: bool = True, stream=None, max_batch: int = 1):
+    def __init__(self, nx: int, ny: int, final_residual: bool = True, stream=None, max_batch: int = 1,
+                 init_from_target: bool = False):
         import torch
 
         if stream is None:
@@ -27,7 +28,9 @@ class GerchbergSaxton:
         self.final_residual = bool(final_residual)
         self.stream = stream
         self.max_batch = int(max_batch)
-        flags = B.GS_FINAL_RESIDUAL if final_residual else 0
+        flags = (B.GS_FINAL_RESIDUAL if final_residual else 0) | (B.GS_INIT_FROM_TARGET if init_from_target else 0)
+        self.init_from_target = bool(init_from_target)
+        self._p = None
         self.handle = B.gs_create_batched(self.nx, self.ny, self.max_batch, flags, stream.cuda_stream)
 
     # -- helpers
@@ -46,16 +49,18 @@ class GerchbergSaxton:
         import torch
 
         self._check(target, "target")
-        self._check(phase_in, "phase_in")
+        if phase_in is not None or not self.init_from_target:
+            self._check(phase_in, "phase_in")
         with torch.cuda.stream(self.stream):
             if phase_out is None:
-                phase_out = torch.empty_like(phase_in)
+                phase_out = torch.empty_like(target)
             else:
                 self._check(phase_out, "phase_out")
             nr = iters + (1 if self.final_residual else 0)
             r = torch.empty(max(nr, 1), dtype=torch.float64, device=target.device) if residuals else None
             g = torch.empty(max(iters, 1), dtype=torch.float64, device=target.device) if object_gap else None
-        rc = B.gs_run(self.handle, target.data_ptr(), phase_in.data_ptr(), int(iters), phase_out.data_ptr(),
+        rc = B.gs_run(self.handle, target.data_ptr(), phase_in.data_ptr() if phase_in is not None else 0, int(iters),
+                      phase_out.data_ptr(),
                       r.data_ptr() if r is not None else 0, g.data_ptr() if g is not None else 0)
         if rc != B.GS_OK:
             raise B.GSError(rc, "gs_run")
@@ -107,6 +112,16 @@ class GerchbergSaxton:
         if rc != B.GS_OK:
             raise B.GSError(rc, "gs_run_host")
         return out, r[:nr], g[:iters]
+
+    def set_slm_amplitude(self, p) -> None:
+        """Use the laser amplitude ``p`` (float32 CUDA tensor [ny, nx], kept
+        alive by this object) on the SLM, or ``None`` for p = 1 (C: gs_set_slm_amplitude)."""
+        if p is not None:
+            self._check(p, "p")
+        rc = B.gs_set_slm_amplitude(self.handle, p.data_ptr() if p is not None else 0)
+        if rc != B.GS_OK:
+            raise B.GSError(rc, "gs_set_slm_amplitude")
+        self._p = p
 
     def status(self) -> int:
         """Synchronise the stream and return (and clear) the device status (C: gs_status)."""

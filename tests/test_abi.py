@@ -82,6 +82,8 @@ def test_null_context_calls(lib):
     out = ctypes.c_int(0)
     assert lib.gs_get_grid(None, ctypes.byref(out)) == B.GS_EINVAL
     assert lib.gs_destroy(None) == B.GS_OK
+    assert lib.gs_set_slm_amplitude(None, None) == B.GS_EINVAL
+    assert lib.gs_loss_grad(None, None, None, None, None) == B.GS_EINVAL
 
 
 def test_noalloc_validates_before_cuda(lib):
