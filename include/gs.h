@@ -188,6 +188,19 @@ int gs_set_slm_amplitude(gs_ctx* c, const float* amplitude);
 int gs_set_grid(gs_ctx* c, int ctas);
 
 /*
+ * gs_test_barrier_timeout -- test hook for the bounded device-side waits.
+ *
+ * The paper has no counterpart (failure detection of this library). With
+ * enable != 0, every grid barrier of the context's later runs waits for one
+ * arrival more than the grid provides, so the first barrier gives up after
+ * its bounded wait (about 1 s), the run ends early with its outputs
+ * unspecified, and gs_status reports GS_ETIMEOUT; the context stays usable.
+ * enable = 0 restores normal runs. Host-only. Returns GS_EINVAL for a NULL
+ * context or a negative enable.
+ */
+int gs_test_barrier_timeout(gs_ctx* c, int enable);
+
+/*
  * gs_get_grid -- the number of thread blocks the next run will launch.
  * Writes it to *ctas (host). Returns GS_EINVAL for NULL arguments.
  */

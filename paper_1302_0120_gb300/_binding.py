@@ -43,6 +43,7 @@ SIGNATURES = {
     "gs_workspace_bytes_batched": (ctypes.c_size_t, [_c_int, _c_int, _c_int, _c_uint]),
     "gs_loss_grad": (_c_int, [_vp, _vp, _vp, _vp, _vp]),
     "gs_set_slm_amplitude": (_c_int, [_vp, _vp]),
+    "gs_test_barrier_timeout": (_c_int, [_vp, _c_int]),
 }
 
 _lib = None
@@ -136,6 +137,11 @@ def gs_status(ctx: int) -> int:
 def gs_set_slm_amplitude(ctx: int, amplitude: int) -> int:
     """Set (device pointer) or clear (0) the SLM amplitude p; returns the status code."""
     return lib().gs_set_slm_amplitude(_vp(ctx), _vp(amplitude or 0))
+
+
+def gs_test_barrier_timeout(ctx: int, enable: bool) -> int:
+    """Test hook: make the grid barriers of later runs time out (enable) or not."""
+    return lib().gs_test_barrier_timeout(_vp(ctx), 1 if enable else 0)
 
 
 def gs_set_grid(ctx: int, ctas: int) -> int:

@@ -375,6 +375,12 @@ int gs_set_slm_amplitude(gs_ctx* c, const float* amplitude) {
   return GS_OK;
 }
 
+int gs_test_barrier_timeout(gs_ctx* c, int enable) {
+  if (c == nullptr || enable < 0) return GS_EINVAL;
+  c->extra_arrivals = enable ? 1u : 0u;
+  return GS_OK;
+}
+
 int gs_set_grid(gs_ctx* c, int ctas) {
   if (c == nullptr || ctas < 0) return GS_EINVAL;
   c->grid_override = ctas;
