@@ -221,7 +221,8 @@ int gs_destroy(gs_ctx* c);
  *   dL/dphi = 4 Im(conj(x) * F^{-1}(r * y)),  x = exp(i phi), r = |y|^2/N - I,
  * F^{-1} the normalised inverse (the adjoint is computed by hand-written
  * passes, not by differentiating the forward code). Square grids only
- * (nx == ny), batch 1, on the context's workspace and stream.
+ * (nx == ny), batch 1, on the context's workspace and stream. With an SLM
+ * amplitude set (gs_set_slm_amplitude) the field is x = p exp(i phi).
  *   target_intensity  device, float [n][n], finite (any sign).
  *   phase             device, float [n][n], radians.
  *   loss_out          device, double[1].
@@ -231,6 +232,27 @@ int gs_destroy(gs_ctx* c);
  * gs_status reports GS_ENUMERIC.
  */
 int gs_loss_grad(gs_ctx* c, const float* target_intensity, const float* phase, double* loss_out, float* grad_out);
+
+/*
+ * gs_physical_error -- the physical error of a phase mask, Eq. (phys-error).
+ *
+ * Operation: for the field u = p exp(i phase) on the SLM (p from
+ * gs_set_slm_amplitude, else 1) and the target intensity I, with
+ * It = I / max I and the reconstructed intensity
+ * Ir = |F_u u|^2 (sum I / sum p^2) / max I (F_u the unitary DFT):
+ *   E_l = sum over I > 0 of (t_d |It - Ir| / (t_l It) - t_d) Theta(|It - Ir|/It - t_l)
+ *   E_d = sum over I = 0 of (Ir - t_d) Theta(Ir - t_d),   t_l = 0.1, t_d = 3e-4
+ * (Sec. II: violations of the relative tolerance on lit pixels and the
+ * absolute tolerance on dark pixels, summed in multiples of t_l and t_d; the
+ * normalisation of Ir is this library's reading of a garbled passage).
+ * Square grids only, on the context's workspace and stream.
+ *   target_intensity  device, float [n][n], finite, >= 0, not all zero.
+ *   phase             device, float [n][n], radians (e.g. a gs_run result).
+ *   error_out         device, double[2] = (E_l, E_d).
+ * Asynchronous. Returns GS_EINVAL for NULL arguments or a non-square context,
+ * GS_ECUDA if the launch fails; a non-finite target gives NaN and GS_ENUMERIC.
+ */
+int gs_physical_error(gs_ctx* c, const float* target_intensity, const float* phase, double* error_out);
 
 /*
  * gs_run_noalloc -- gs_run without a context and without any allocation.

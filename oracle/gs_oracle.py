@@ -233,18 +233,20 @@ def physical_error(I, u, t_l: float = TL_LIT, t_d: float = TD_DARK):
     Reading of the garbled passage: both the target and the reconstruction are
     compared as intensities normalised to the target's peak,
       ``It = I / max I`` and
-      ``Ir = |F_u u|^2 * (sum I / N) / max I``
-    (the reconstruction carries the target's total energy). A pixel is lit if
+      ``Ir = |F_u u|^2 * (sum I / ||u||^2) / max I``
+    (the reconstruction carries the target's total energy; ``||u||^2 = N``
+    for a unit-amplitude field, ``sum p^2`` with a laser amplitude p). A pixel is lit if
     ``It > 0``. The formula is evaluated as printed:
       ``E_l = sum_lit (t_d |It - Ir| / (t_l It) - t_d) * Theta(|It - Ir|/It - t_l)``
       ``E_d = sum_dark (Ir - t_d) * Theta(Ir - t_d)``,  Theta(0) = 0.
     Returns ``(E_l, E_d)``.
     """
     I = np.asarray(I, dtype=np.float64)
-    n = I.size
+    u = np.asarray(u, dtype=np.complex128)
+    energy = float(np.sum(np.abs(u) ** 2))
     imax = float(I.max())
     It = I / imax
-    Ir = np.abs(fft2u(np.asarray(u, dtype=np.complex128))) ** 2 * (float(I.sum()) / n) / imax
+    Ir = np.abs(fft2u(u)) ** 2 * (float(I.sum()) / energy) / imax
     lit = It > 0
     rel = np.zeros_like(It)
     rel[lit] = np.abs(It[lit] - Ir[lit]) / It[lit]
@@ -256,29 +258,32 @@ def physical_error(I, u, t_l: float = TL_LIT, t_d: float = TD_DARK):
     return e_l, e_d
 
 
-def intensity_loss(phi, I) -> float:
-    """Intensity loss ``L = sum (|F exp(i phi)|^2 / N - I)^2`` with the unnormalised F.
+def intensity_loss(phi, I, p=None) -> float:
+    """Intensity loss ``L = sum (|F x|^2 / N - I)^2``, ``x = p exp(i phi)``,
+    with the unnormalised F (p = 1 by default).
 
     The differentiable form of the same inverse problem (fit |F u|^2 to the
-    target intensity over phase-only u in S, Sec. II).
+    target intensity over u in S, Sec. II).
     """
     phi = np.asarray(phi, dtype=np.float64)
     I = np.asarray(I, dtype=np.float64)
-    y = _sfft.fft2(np.exp(1j * phi), workers=WORKERS)
+    pw = 1.0 if p is None else np.asarray(p, dtype=np.float64)
+    y = _sfft.fft2(pw * np.exp(1j * phi), workers=WORKERS)
     r = np.abs(y) ** 2 / phi.size - I
     return float(np.sum(r * r))
 
 
-def intensity_loss_grad(phi, I) -> np.ndarray:
+def intensity_loss_grad(phi, I, p=None) -> np.ndarray:
     """Analytic gradient of ``intensity_loss`` with respect to phi.
 
-    With ``x = exp(i phi)``, ``y = F x``, ``r = |y|^2/N - I``:
+    With ``x = p exp(i phi)``, ``y = F x``, ``r = |y|^2/N - I``:
     ``dL/dphi = 4 Im(conj(x) * F^{-1}(r * y))`` (F^{-1} the normalised inverse),
     from ``d y_k / d phi_j = F_kj i x_j`` and the symmetry of F.
     """
     phi = np.asarray(phi, dtype=np.float64)
     I = np.asarray(I, dtype=np.float64)
-    x = np.exp(1j * phi)
+    pw = 1.0 if p is None else np.asarray(p, dtype=np.float64)
+    x = pw * np.exp(1j * phi)
     y = _sfft.fft2(x, workers=WORKERS)
     r = np.abs(y) ** 2 / phi.size - I
     z = _sfft.ifft2(r * y, workers=WORKERS)

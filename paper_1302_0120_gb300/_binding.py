@@ -44,6 +44,7 @@ SIGNATURES = {
     "gs_loss_grad": (_c_int, [_vp, _vp, _vp, _vp, _vp]),
     "gs_set_slm_amplitude": (_c_int, [_vp, _vp]),
     "gs_test_barrier_timeout": (_c_int, [_vp, _c_int]),
+    "gs_physical_error": (_c_int, [_vp, _vp, _vp, _vp]),
 }
 
 _lib = None
@@ -128,6 +129,11 @@ def gs_run_host(ctx: int, target_intensity: int, phase_in: int, iters: int, phas
 def gs_loss_grad(ctx: int, target_intensity: int, phase: int, loss_out: int, grad_out: int = 0) -> int:
     """Enqueue the intensity loss (and its gradient when grad_out != 0); returns the status code."""
     return lib().gs_loss_grad(_vp(ctx), _vp(target_intensity), _vp(phase), _vp(loss_out), _vp(grad_out or 0))
+
+
+def gs_physical_error(ctx: int, target_intensity: int, phase: int, error_out: int) -> int:
+    """Enqueue the physical error (E_l, E_d) into a device double[2]; returns the status code."""
+    return lib().gs_physical_error(_vp(ctx), _vp(target_intensity), _vp(phase), _vp(error_out))
 
 
 def gs_status(ctx: int) -> int:

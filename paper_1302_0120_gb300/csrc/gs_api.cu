@@ -32,7 +32,7 @@ constexpr int kTwiddleEntries = 31 * 32 + 31 * 1024;
 
 // Offsets of the sub-buffers of one workspace allocation.
 struct Layout {
-  size_t B, mT, partials, twx, twy, ones, bar, status, abort_flag, mask_flags, energy, dI, dphi, total;
+  size_t B, mT, partials, twx, twy, ones, bar, status, abort_flag, mask_flags, energy, lossbuf, dI, dphi, total;
 };
 
 Layout make_layout(int nx, int ny, int max_batch) {
@@ -52,6 +52,7 @@ Layout make_layout(int nx, int ny, int max_batch) {
   L.abort_flag = o; o = align_up(o + sizeof(int));
   L.mask_flags = o; o = align_up(o + gsk::kMaxBatch * sizeof(int));
   L.energy = o;     o = align_up(o + sizeof(double));
+  L.lossbuf = o;    o = align_up(o + sizeof(double));
   L.dI = o;         o = align_up(o + n * sizeof(float));
   L.dphi = o;       o = align_up(o + n * sizeof(float));
   L.total = o;
@@ -335,9 +336,10 @@ int gs_run_host(gs_ctx* c, const float* target_intensity, const float* phase_in,
   return gs_status(c);
 }
 
-int gs_loss_grad(gs_ctx* c, const float* target_intensity, const float* phase, double* loss_out, float* grad_out) {
-  if (c == nullptr || target_intensity == nullptr || phase == nullptr || loss_out == nullptr || c->nx != c->ny)
-    return GS_EINVAL;
+namespace {
+
+int enqueue_loss(gs_ctx* c, const float* target_intensity, const float* phase, double* loss_out, float* grad_out,
+                 double* phys_out) {
   gsk::LossParams p{};
   p.n = c->nx;
   p.logn = ilog2i(c->nx);
@@ -347,6 +349,9 @@ int gs_loss_grad(gs_ctx* c, const float* target_intensity, const float* phase, d
   p.phi = phase;
   p.grad = grad_out;
   p.loss = loss_out;
+  p.phys = phys_out;
+  p.p_slm = c->p_slm;
+  p.energy = at<double>(c, c->L.energy);
   p.partials = at<double>(c, c->L.partials);
   p.tw = at<float2>(c, c->L.twx);
   p.bar = at<unsigned>(c, c->L.bar);
@@ -360,6 +365,20 @@ int gs_loss_grad(gs_ctx* c, const float* target_intensity, const float* phase, d
     return GS_ECUDA;
   }
   return GS_OK;
+}
+
+}  // namespace
+
+int gs_loss_grad(gs_ctx* c, const float* target_intensity, const float* phase, double* loss_out, float* grad_out) {
+  if (c == nullptr || target_intensity == nullptr || phase == nullptr || loss_out == nullptr || c->nx != c->ny)
+    return GS_EINVAL;
+  return enqueue_loss(c, target_intensity, phase, loss_out, grad_out, nullptr);
+}
+
+int gs_physical_error(gs_ctx* c, const float* target_intensity, const float* phase, double* error_out) {
+  if (c == nullptr || target_intensity == nullptr || phase == nullptr || error_out == nullptr || c->nx != c->ny)
+    return GS_EINVAL;
+  return enqueue_loss(c, target_intensity, phase, at<double>(c, c->L.lossbuf), nullptr, error_out);
 }
 
 int gs_set_slm_amplitude(gs_ctx* c, const float* amplitude) {

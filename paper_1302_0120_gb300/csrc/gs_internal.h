@@ -64,7 +64,10 @@ struct LossParams {
   const float* phi;        // phase [n][n]
   float* grad;             // dL/dphi [n][n], or null (loss only)
   double* loss;            // [1]
-  double* partials;        // [2][grid]
+  double* phys;            // [2]: physical error (E_l, E_d), or null
+  const float* p_slm;      // SLM amplitude [n][n], or null (p = 1)
+  const double* energy;    // sum p^2 when p_slm is set
+  double* partials;        // [6][grid]
   const float2* tw;        // stage twiddle tables (length n)
   unsigned* bar;
   int* status;

@@ -11,12 +11,26 @@
 //   columns  y = DFT_y(B); r; loss partial; B = IDFT_y(r * y)   (adjoint, swapped)
 //   rows     N z = IDFT_x(B); grad = 4 Im(conj(x) z)            (adjoint)
 // The target is staged like the amplitude of the iteration kernel
-// (transposed [nx][ny], read per column block). FP64 only for the loss sum.
+// (transposed [nx][ny], read per column block). FP64 only for the sums.
+// With a laser amplitude p on the SLM the field is x = p exp(i phi); the
+// gradient formula is unchanged (dy_k/dphi_j = F_kj i x_j still holds).
+//
+// The same column pass can also evaluate the physical error of Eq.
+// (phys-error) for u = x (Sec. II): with It = I / max I and the reconstructed
+// intensity Ir = |F_u u|^2 (sum I / sum p^2) / max I,
+//   E_l = sum_{I > 0} (t_d |It - Ir| / (t_l It) - t_d) Theta(|It - Ir|/It - t_l)
+//   E_d = sum_{I = 0} (Ir - t_d) Theta(Ir - t_d),   t_l = 0.1, t_d = 3e-4.
 #pragma once
 
 #include "gs_iterate.cuh"
 
 namespace gsk {
+
+constexpr float kTolLit = 0.1f;    // t_l, Sec. II
+constexpr float kTolDark = 3e-4f;  // t_d, Sec. II
+
+// partial-sum rows of the loss kernel (each [grid])
+enum LossRow { kRowFlag = 0, kRowSumI = 1, kRowMaxI = 2, kRowLoss = 3, kRowEl = 4, kRowEd = 5 };
 
 // Grid barrier for the loss kernel (same protocol as grid_sync).
 static __device__ bool loss_sync(const LossParams& p, unsigned& target, Shared& sh) {
@@ -86,12 +100,29 @@ __global__ void __launch_bounds__(kThreads, 1) gs_loss_kernel(const LossParams p
     const int r0 = split(b, gridDim.x, N);
     const int r1 = split(b + 1, gridDim.x, N);
     bool bad = false;
+    double sum_i = 0.0;
+    float max_i = 0.f;
     for (int e = threadIdx.x; e < (r1 - r0) * N; e += kThreads) {
       const float x = p.I[static_cast<size_t>(r0) * N + e];
       bad |= !(fabsf(x) <= FLT_MAX);
+      sum_i += static_cast<double>(x);
+      max_i = fmaxf(max_i, x);
     }
-    if (__syncthreads_or(bad) && threadIdx.x == 0) p.partials[b] = __longlong_as_double(0x7ff8000000000000ll);
-    else if (threadIdx.x == 0) p.partials[b] = 0.0;
+    const int any_bad = __syncthreads_or(bad);
+    const double bsum = block_sum(sum_i, sh);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) max_i = fmaxf(max_i, __shfl_xor_sync(0xffffffffu, max_i, o));
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) sh.red[threadIdx.x >> 5] = static_cast<double>(max_i);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double bmax = 0.0;
+      for (int w = 0; w < kThreads / 32; ++w) bmax = fmax(bmax, sh.red[w]);
+      const int G = gridDim.x;
+      p.partials[kRowFlag * G + b] = any_bad ? __longlong_as_double(0x7ff8000000000000ll) : 0.0;
+      p.partials[kRowSumI * G + b] = bsum;
+      p.partials[kRowMaxI * G + b] = bmax;
+    }
     // transpose this block's column blocks through shared memory (coalesced
     // on both sides): IT[c][y] = I[y][c]
     const int lo = split(b, gridDim.x, L::NBLK);
@@ -123,12 +154,14 @@ __global__ void __launch_bounds__(kThreads, 1) gs_loss_kernel(const LossParams p
       const int ridx = valid ? idx : base;
       float2 v[32];
       const float* ph = p.phi + static_cast<size_t>(ridx) * N + t;
+      const float* pp = p.p_slm ? p.p_slm + static_cast<size_t>(ridx) * N + t : nullptr;
       float2* su = grp.sm + t;
 #pragma unroll 1
       for (int i = 0; i < 32; ++i) {
         float s, c;
         sincosf(ph[T * i], &s, &c);
-        su[T * i] = make_float2(c, s);
+        const float a = pp ? pp[T * i] : 1.f;
+        su[T * i] = make_float2(a * c, a * s);
       }
 #pragma unroll
       for (int i = 0; i < 32; ++i) v[i] = su[T * i];
@@ -141,13 +174,28 @@ __global__ void __launch_bounds__(kThreads, 1) gs_loss_kernel(const LossParams p
     }
   }
   if (!loss_sync(p, target, sh)) return;
+  // Scale of the reconstructed intensity for the physical error:
+  // Ir = |y|^2/N * (sum I / sum p^2) / max I, It = I / max I.
+  float ir_scale = 0.f, it_scale = 0.f;
   {
-    double tot = 0.0;
-    for (int c = 0; c < static_cast<int>(gridDim.x); ++c) tot += p.partials[c];
-    if (!(tot == 0.0)) {  // a non-finite target
+    double tot = 0.0, sum_i = 0.0, max_i = 0.0;
+    const int G = gridDim.x;
+    for (int c = 0; c < G; ++c) {
+      tot += p.partials[kRowFlag * G + c];
+      sum_i += p.partials[kRowSumI * G + c];
+      max_i = fmax(max_i, p.partials[kRowMaxI * G + c]);
+    }
+    const double ep = p.p_slm ? *p.energy : static_cast<double>(N) * N;
+    if (max_i > 0.0 && ep > 0.0) {
+      ir_scale = static_cast<float>((sum_i / ep) / max_i * p.inv_n);
+      it_scale = static_cast<float>(1.0 / max_i);
+    }
+    if (!(tot == 0.0) || (p.p_slm && !(ep > 0.0 && ep <= DBL_MAX))) {  // a non-finite target or a bad p
       if (b == 0 && threadIdx.x == 0) {
         atomicCAS(p.status, 0, GS_ENUMERIC);
-        p.loss[0] = __longlong_as_double(0x7ff8000000000000ll);
+        const double nan = __longlong_as_double(0x7ff8000000000000ll);
+        p.loss[0] = nan;
+        if (p.phys) p.phys[0] = p.phys[1] = nan;
       }
       return;
     }
@@ -156,7 +204,8 @@ __global__ void __launch_bounds__(kThreads, 1) gs_loss_kernel(const LossParams p
   // Pass 2 (columns): y = DFT_y(B) = F x; r = |y|^2/N - I; loss partial;
   // B = swap(IDFT_y(r y)) for the adjoint.
   const bool want_grad = p.grad != nullptr;
-  double acc = 0.0;
+  const bool want_phys = p.phys != nullptr;
+  double acc = 0.0, acc_l = 0.0, acc_d = 0.0;
   {
     const int lo = split(b, gridDim.x, L::NBLK);
     const int hi = split(b + 1, gridDim.x, L::NBLK);
@@ -188,15 +237,38 @@ __global__ void __launch_bounds__(kThreads, 1) gs_loss_kernel(const LossParams p
         for (int i = 0; i < 32; ++i) v[i] = blk[L::boff(t + T * i, gq)];
         group_fft<LN>(v, grp, stw);
         const float* icol = its + gq * N + t;
+        float* sa2 = reinterpret_cast<float*>(grp.sm) + t;  // |y|^2 for the physical error
         float part = 0.f;
 #pragma unroll
         for (int i = 0; i < 32; ++i) {
           const float2 y = v[i];
-          const float r = (y.x * y.x + y.y * y.y) * p.inv_n - icol[T * i];
+          const float a2 = y.x * y.x + y.y * y.y;
+          const float r = a2 * p.inv_n - icol[T * i];
           part = fmaf(r, r, part);
+          if (want_phys) sa2[T * i] = a2;
           v[i] = make_float2(r * y.y, r * y.x);  // swapped: the next forward DFT acts as the inverse
         }
         if (gact) acc += static_cast<double>(part);
+        if (want_phys) {  // Eq. (phys-error), once per call: a rolled loop
+          float el = 0.f, ed = 0.f;
+#pragma unroll 1
+          for (int i = 0; i < 32; ++i) {
+            const float ir = sa2[T * i] * ir_scale;  // reconstructed intensity
+            const float iv = icol[T * i];
+            if (iv > 0.f) {
+              const float it = iv * it_scale;
+              const float rel = fabsf(it - ir) / it;
+              if (rel - kTolLit > 0.f) el += kTolDark * rel / kTolLit - kTolDark;
+            } else if (ir - kTolDark > 0.f) {
+              ed += ir - kTolDark;
+            }
+          }
+          if (gact) {
+            acc_l += static_cast<double>(el);
+            acc_d += static_cast<double>(ed);
+          }
+          grp.sync();
+        }
         if (want_grad) {
           group_fft<LN>(v, grp, stw);
           if (gact) {
@@ -217,19 +289,32 @@ __global__ void __launch_bounds__(kThreads, 1) gs_loss_kernel(const LossParams p
     if (want_grad && threadIdx.x == 0) bulk_wait_all();
   }
   {
+    const int G = gridDim.x;
     const double tot = block_sum(acc, sh);
-    if (threadIdx.x == 0) p.partials[gridDim.x + b] = tot;
+    if (threadIdx.x == 0) p.partials[kRowLoss * G + b] = tot;
+    if (want_phys) {
+      const double tl = block_sum(acc_l, sh);
+      if (threadIdx.x == 0) p.partials[kRowEl * G + b] = tl;
+      const double td = block_sum(acc_d, sh);
+      if (threadIdx.x == 0) p.partials[kRowEd * G + b] = td;
+    }
   }
   if (!loss_sync(p, target, sh)) {
     if (threadIdx.x == 0 && sh.pending) mbar_wait_bounded(&sh.mbar, sh.pending_phase);
     return;
   }
   if (b == 0 && threadIdx.x < 32) {
-    double s = 0.0;
-    for (int c = threadIdx.x; c < static_cast<int>(gridDim.x); c += 32) s += p.partials[gridDim.x + c];
+    const int G = gridDim.x;
+    for (int row = kRowLoss; row <= (want_phys ? kRowEd : kRowLoss); ++row) {
+      double s = 0.0;
+      for (int c = threadIdx.x; c < G; c += 32) s += p.partials[row * G + c];
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (threadIdx.x == 0) p.loss[0] = s;
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+      if (threadIdx.x == 0) {
+        if (row == kRowLoss) p.loss[0] = s;
+        else p.phys[row - kRowEl] = s;
+      }
+    }
   }
   if (!want_grad) return;
 
@@ -252,13 +337,15 @@ __global__ void __launch_bounds__(kThreads, 1) gs_loss_kernel(const LossParams p
       for (int i = 0; i < 32; ++i) su[T * i] = v[i];
       if (valid) {
         const float* ph = p.phi + static_cast<size_t>(idx) * N + t;
+        const float* pp = p.p_slm ? p.p_slm + static_cast<size_t>(idx) * N + t : nullptr;
         float* gr = p.grad + static_cast<size_t>(idx) * N + t;
 #pragma unroll 1
         for (int i = 0; i < 32; ++i) {
           float s, c;
           sincosf(ph[T * i], &s, &c);
+          const float a = pp ? pp[T * i] : 1.f;  // x = p exp(i phi)
           const float2 w = su[T * i];
-          gr[T * i] = scale * (c * w.x - s * w.y);
+          gr[T * i] = scale * a * (c * w.x - s * w.y);
         }
       }
       grp.sync();

@@ -84,6 +84,7 @@ def test_null_context_calls(lib):
     assert lib.gs_destroy(None) == B.GS_OK
     assert lib.gs_set_slm_amplitude(None, None) == B.GS_EINVAL
     assert lib.gs_test_barrier_timeout(None, 1) == B.GS_EINVAL
+    assert lib.gs_physical_error(None, None, None, None) == B.GS_EINVAL
     assert lib.gs_loss_grad(None, None, None, None, None) == B.GS_EINVAL
 
 

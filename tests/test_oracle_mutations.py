@@ -52,14 +52,14 @@ def _gs_step_late_residual(u, m):
     return u1, O.gap_to_M(u1, m), O.gap_to_S(v)
 
 
-def _grad_wrong_sign(phi, I):
+def _grad_wrong_sign(phi, I, p=None):
     x = np.exp(1j * phi)
     y = sfft.fft2(x)
     r = np.abs(y) ** 2 / phi.size - I
     return -4.0 * np.imag(np.conj(x) * sfft.ifft2(r * y))
 
 
-def _grad_dropped_factor(phi, I):
+def _grad_dropped_factor(phi, I, p=None):
     x = np.exp(1j * phi)
     y = sfft.fft2(x)
     r = np.abs(y) ** 2 / phi.size - I

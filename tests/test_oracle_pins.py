@@ -352,19 +352,19 @@ def test_target_start_is_hermitian():
 # ---------------------------------------------------------------- gradient (differentiable form)
 
 
-def check_gradient_fd(n=32, seed=11, h=1e-6):
+def check_gradient_fd(n=32, seed=11, h=1e-6, p=None):
     rng = np.random.default_rng(seed)
     phi = rng.random((n, n)) * 2 * np.pi
     I = S.spot_target(seed, n, n, 4).astype(np.float64)
     I *= I.size / I.sum()  # sum I = N
-    g = O.intensity_loss_grad(phi, I)
+    g = O.intensity_loss_grad(phi, I, p)
     idx = rng.choice(phi.size, size=48, replace=False)
     fd = np.empty(len(idx))
     for t, k in enumerate(idx):
         e = np.zeros(phi.size)
         e[k] = h
         e = e.reshape(phi.shape)
-        fd[t] = (O.intensity_loss(phi + e, I) - O.intensity_loss(phi - e, I)) / (2 * h)
+        fd[t] = (O.intensity_loss(phi + e, I, p) - O.intensity_loss(phi - e, I, p)) / (2 * h)
     ga = g.ravel()[idx]
     err = np.linalg.norm(ga - fd) / np.linalg.norm(fd)
     assert err <= 1e-6, err
@@ -372,6 +372,10 @@ def check_gradient_fd(n=32, seed=11, h=1e-6):
 
 def test_gradient_finite_differences():
     check_gradient_fd()
+
+
+def test_gradient_finite_differences_with_laser_amplitude():
+    check_gradient_fd(p=laser_profile(32, 32, 9).astype(np.float64))
 
 
 def test_gradient_single_pixel_is_zero():
@@ -384,30 +388,43 @@ def test_gradient_single_pixel_is_zero():
 
 
 def _field_with_intensity(I, Ir):
-    """A field whose normalised reconstructed intensity is exactly Ir."""
+    """A field whose normalised reconstructed intensity is exactly Ir (Ir must
+    carry the same total as I / max I: a field conserves its energy)."""
     n = I.size
     amp = np.sqrt(Ir * I.max() * n / I.sum())
     return O.ifft2u(amp.astype(complex))
 
 
+def _moved(It, pix, new_value, peak):
+    """It with pixel `pix` set to `new_value` and the difference taken from the
+    peak pixel (kept within the lit tolerance), so the total is unchanged."""
+    Ir = It.copy()
+    delta = new_value - Ir[pix]
+    Ir[pix] = new_value
+    Ir[peak] -= delta
+    assert abs(delta) / It[peak] < O.TL_LIT
+    return Ir
+
+
 def test_physical_error_special_cases():
     I = S.spot_target(4, 16, 16, 3)
     It = I.astype(np.float64) / I.max()
+    peak = np.unravel_index(np.argmax(It), It.shape)
     # perfect reconstruction: no violation anywhere
     e_l, e_d = O.physical_error(I, _field_with_intensity(I, It))
     assert abs(e_l) < 1e-12 and abs(e_d) < 1e-12
-    lit = np.argwhere(It > 0.5)[0]
-    dark = np.argwhere(It == 0)[0]
+    lit = tuple(np.argwhere((It > 0.05) & (It < 0.2))[0])
+    dark = tuple(np.argwhere(It == 0)[0])
     # a lit pixel off by 3 t_l counts (3 - 1) t_d; one within t_l counts nothing
-    Ir = It.copy()
-    Ir[tuple(lit)] *= 1 + 3 * O.TL_LIT
+    Ir = _moved(It, lit, It[lit] * (1 + 3 * O.TL_LIT), peak)
     e_l, e_d = O.physical_error(I, _field_with_intensity(I, Ir))
     assert abs(e_l - 2 * O.TD_DARK) < 1e-9 and abs(e_d) < 1e-12
-    Ir = It.copy()
-    Ir[tuple(lit)] *= 1 + 0.5 * O.TL_LIT
+    Ir = _moved(It, lit, It[lit] * (1 + 0.5 * O.TL_LIT), peak)
     assert abs(O.physical_error(I, _field_with_intensity(I, Ir))[0]) < 1e-12
     # a dark pixel at 5 t_d counts 4 t_d
-    Ir = It.copy()
-    Ir[tuple(dark)] = 5 * O.TD_DARK
+    Ir = _moved(It, dark, 5 * O.TD_DARK, peak)
     e_l, e_d = O.physical_error(I, _field_with_intensity(I, Ir))
     assert abs(e_d - 4 * O.TD_DARK) < 1e-10 and abs(e_l) < 1e-12
+    # the energy normalisation: scaling the field changes nothing
+    u = _field_with_intensity(I, Ir)
+    assert np.allclose(O.physical_error(I, 3.0 * u), (e_l, e_d), rtol=1e-9, atol=1e-15)
