@@ -69,6 +69,79 @@ def test_autograd_and_adam():
     lc.close()
 
 
+def gpu_physical_error(I, phi, p=None):
+    import torch
+
+    from paper_1302_0120_gb300 import _binding as B
+    from paper_1302_0120_gb300 import build_lib
+    from paper_1302_0120_gb300.differentiable import LossContext
+
+    build_lib.build()
+    lc = LossContext(I.shape[0])
+    pt = None
+    if p is not None:
+        pt = torch.from_numpy(p).cuda()
+        assert B.gs_set_slm_amplitude(lc.handle, pt.data_ptr()) == 0
+    e = torch.full((2,), -1.0, dtype=torch.float64, device="cuda")
+    It, Pt = torch.from_numpy(I).cuda(), torch.from_numpy(phi).cuda()
+    assert B.gs_physical_error(lc.handle, It.data_ptr(), Pt.data_ptr(), e.data_ptr()) == 0
+    st = lc.status()
+    out = e.cpu().numpy()
+    lc.close()
+    return out, st
+
+
+@pytest.mark.parametrize("n,iters", [(64, 20), (256, 30), (1024, 20)])
+def test_physical_error_of_gs_masks(n, iters):
+    """E (Eq. phys-error) of a GPU Gerchberg-Saxton mask, against the oracle's
+    E of the same mask; E is continuous in the field, so FP32 stays close."""
+    from tests.gpu_util import gpu_gs
+
+    I = S.spot_target(50 + n, n, n, 10 if n == 64 else 40, (0.5, 1.0))
+    ph, _, _, st = gpu_gs(I, S.random_phase(51 + n, n, n), iters)
+    assert st == 0
+    e, st = gpu_physical_error(I, ph)
+    assert st == 0
+    ref = O.physical_error(I, np.exp(1j * ph.astype(np.float64)))
+    assert ref[0] > 0 and ref[1] > 0
+    assert np.allclose(e, ref, rtol=2e-3, atol=0), (e, ref)
+
+
+def test_physical_error_consistent_target_is_zero():
+    n = 64
+    rng = np.random.default_rng(8)
+    phi = (rng.random((n, n)) * 2 * np.pi).astype(np.float32)
+    I = O.consistent_target(phi).astype(np.float32)  # no dark pixel, exact reconstruction
+    e, st = gpu_physical_error(I, phi)
+    assert st == 0 and e[0] == 0.0 and e[1] == 0.0
+
+
+def test_loss_and_physical_error_with_laser_amplitude():
+    import torch
+
+    from paper_1302_0120_gb300 import _binding as B
+    from paper_1302_0120_gb300.differentiable import LossContext
+
+    n = 128
+    I = normalized_target(60, n, 10)
+    phi = S.random_phase(61, n, n)
+    p = S.laser_amplitude(n, n)
+    lc = LossContext(n)
+    pt = torch.from_numpy(p).cuda()
+    assert B.gs_set_slm_amplitude(lc.handle, pt.data_ptr()) == 0
+    loss, grad = lc.loss_grad(torch.from_numpy(I).cuda(), torch.from_numpy(phi).cuda())
+    assert lc.status() == 0
+    ref_l = O.intensity_loss(phi, I, p)
+    ref_g = O.intensity_loss_grad(phi, I, p)
+    assert abs(loss.item() - ref_l) <= 1e-4 * ref_l
+    g = grad.cpu().numpy()
+    assert np.linalg.norm(g - ref_g) / np.linalg.norm(ref_g) <= 1e-3
+    lc.close()
+    e, st = gpu_physical_error(I, phi, p)
+    ref = O.physical_error(I, p.astype(np.float64) * np.exp(1j * phi.astype(np.float64)))
+    assert st == 0 and np.allclose(e, ref, rtol=2e-3, atol=0), (e, ref)
+
+
 def test_nonfinite_target():
     from paper_1302_0120_gb300 import GS_ENUMERIC
 
