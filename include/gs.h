@@ -68,7 +68,18 @@ enum {
    * the initial condition of Sec. IV (P_M uhat^0 of the paper, garbled in
    * the text, read this way). phase_in is ignored and may be NULL. With a
    * real target this start is conjugate-symmetric, so F u stays real. */
-  GS_INIT_FROM_TARGET = 2u
+  GS_INIT_FROM_TARGET = 2u,
+  /* Run the DFTs of Eq. (e:PM) and the inverse transforms on the tensor
+   * cores: each length-n transform (n = 256, 512, 1024; square grids only) is
+   * the four-step factorisation n = 32 x (n/32) with both stages as dense
+   * DFT-matrix products, FP16 operands and FP32 accumulation; projections,
+   * gaps and reductions are unchanged (FP32 field, FP64 sums). The paper
+   * computes in single or double precision only (Sec. V); this reduced
+   * precision form has no counterpart there. One iteration differs from the
+   * FP32 one by about 1e-3 (relative L2). The transforms' inputs must stay in
+   * the FP16 range: a mask whose n * sum p^2 exceeds 2^31 is rejected like an
+   * invalid target (GS_ENUMERIC); p = 1 always qualifies. */
+  GS_TENSOR_CORE = 4u
 };
 
 typedef struct gs_ctx gs_ctx;
@@ -80,13 +91,15 @@ typedef struct gs_ctx gs_ctx;
  * (Sec. II: "n_x, n_y the respective number of pixels").
  *   out     host pointer that receives the context (set to NULL on failure).
  *   nx, ny  powers of two in [32, 4096].
- *   flags   GS_* flags (GS_FINAL_RESIDUAL, GS_INIT_FROM_TARGET).
+ *   flags   GS_* flags (GS_FINAL_RESIDUAL, GS_INIT_FROM_TARGET,
+ *           GS_TENSOR_CORE).
  *   stream  a cudaStream_t, or NULL for the legacy default stream. All later
  *           work of this context is enqueued on it.
  * The context owns its device workspace (gs_workspace_bytes bytes): the field,
  * the scaled amplitude, per-block FP64 partial sums, twiddle tables, a
  * barrier counter and a status word. Synchronous (allocates and uploads).
- * Returns GS_EINVAL for bad sizes or a NULL out, GS_ENOMEM, GS_ECUDA.
+ * Returns GS_EINVAL for bad sizes, an unknown flag, GS_TENSOR_CORE with a grid
+ * other than 256, 512 or 1024 square, or a NULL out; GS_ENOMEM, GS_ECUDA.
  */
 int gs_create(gs_ctx** out, int nx, int ny, unsigned flags, void* stream);
 

@@ -14,6 +14,7 @@ from ._binding import (  # noqa: F401
     GS_FINAL_RESIDUAL,
     GS_INIT_FROM_TARGET,
     GS_OK,
+    GS_TENSOR_CORE,
     GSError,
     gs_create,
     gs_create_batched,

@@ -21,6 +21,7 @@ GS_ENUMERIC = -5
 
 GS_FINAL_RESIDUAL = 1
 GS_INIT_FROM_TARGET = 2
+GS_TENSOR_CORE = 4
 
 _c_int = ctypes.c_int
 _c_uint = ctypes.c_uint

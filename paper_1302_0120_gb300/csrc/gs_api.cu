@@ -169,7 +169,10 @@ int gs_create_batched(gs_ctx** out, int nx, int ny, int max_batch, unsigned flag
   if (out == nullptr) return GS_EINVAL;
   *out = nullptr;
   if (!valid_dim(nx) || !valid_dim(ny) || max_batch < 1 || max_batch > gsk::kMaxBatch) return GS_EINVAL;
-  if ((flags & ~static_cast<unsigned>(GS_FINAL_RESIDUAL | GS_INIT_FROM_TARGET)) != 0) return GS_EINVAL;
+  if ((flags & ~static_cast<unsigned>(GS_FINAL_RESIDUAL | GS_INIT_FROM_TARGET | GS_TENSOR_CORE)) != 0)
+    return GS_EINVAL;
+  const bool tc = (flags & GS_TENSOR_CORE) != 0;
+  if (tc && !(nx == ny && nx >= 256 && nx <= 1024)) return GS_EINVAL;
   gs_ctx* c = new (std::nothrow) gs_ctx();
   if (c == nullptr) return GS_ENOMEM;
   c->nx = nx;
@@ -180,7 +183,7 @@ int gs_create_batched(gs_ctx** out, int nx, int ny, int max_batch, unsigned flag
   c->L = make_layout(nx, ny, max_batch);
   if (cudaGetDevice(&c->device) != cudaSuccess ||
       cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess ||
-      gsk::iteration_occupancy(nx, ny, &c->blocks_per_sm) != cudaSuccess || c->blocks_per_sm < 1) {
+      gsk::iteration_occupancy(nx, ny, &c->blocks_per_sm, tc) != cudaSuccess || c->blocks_per_sm < 1) {
     cudaGetLastError();
     delete c;
     return GS_ECUDA;
@@ -249,6 +252,7 @@ int gs_run_batched(gs_ctx* c, int batch, const float* target_intensity, const fl
   p.iters = iters;
   p.final_resid = (c->flags & GS_FINAL_RESIDUAL) ? 1 : 0;
   p.extra_arrivals = c->extra_arrivals;
+  p.tensor_core = (c->flags & GS_TENSOR_CORE) ? 1 : 0;
   const double n = static_cast<double>(c->nx) * c->ny;
   p.inv_sqrt_n = static_cast<float>(1.0 / std::sqrt(n));
   p.inv_n = 1.0 / n;

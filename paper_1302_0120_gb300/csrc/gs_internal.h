@@ -13,6 +13,9 @@ constexpr int kMaxBatch = 64;                   // masks per launch
 // Group exchange buffers: (256 / T) groups of (n + n/32) complex, T = n/32,
 // which is 256 * 33 complex whatever n is.
 constexpr int kGroupSmemBytes = kThreads * 33 * 8;
+// Extra shared memory of the tensor-core kernels: stage twiddles [32][32]
+// complex and a 32-entry cos/sin table.
+constexpr int kTcExtraSmemBytes = 32 * 32 * 8 + 32 * 8;
 
 struct Params {
   int nx, ny;          // grid, powers of two in [32, 4096]
@@ -47,13 +50,17 @@ struct Params {
   unsigned extra_arrivals;  // test hook: arrivals a barrier waits for beyond the grid (0 in use)
   float inv_sqrt_n;    // 1/sqrt(N)
   double inv_n;        // 1/N
+  int tensor_core;     // host side: launch the tensor-core kernel (square 256, 512, 1024)
 };
 
 // Kernel for log2(nx) = LX and the given log2(ny); defined per LX in gs_inst.cu.
 template <int LX>
 const void* iterate_kernel_lx(int ly);
+// Kernel with tensor-core transforms for an n x n grid, log2(n) = l in 8..10
+// (gs_tc_inst.cu); null otherwise.
+const void* iterate_kernel_tc(int l);
 
-size_t iteration_smem_bytes(int nx, int ny);
+size_t iteration_smem_bytes(int nx, int ny, bool tensor_core = false);
 
 // Intensity loss and gradient (square grids), see gs_loss.cuh.
 struct LossParams {
@@ -79,6 +86,6 @@ cudaError_t launch_loss(const LossParams& p, int grid, cudaStream_t s);
 cudaError_t launch_iterations(const Params& p, int grid, cudaStream_t s);
 // sum p^2 of an SLM amplitude into *energy (NaN if p has a negative or non-finite value)
 cudaError_t launch_energy(const float* p, long long n, double* energy, cudaStream_t s);
-cudaError_t iteration_occupancy(int nx, int ny, int* blocks_per_sm);
+cudaError_t iteration_occupancy(int nx, int ny, int* blocks_per_sm, bool tensor_core = false);
 
 }  // namespace gsk

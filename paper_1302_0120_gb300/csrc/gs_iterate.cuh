@@ -1,6 +1,8 @@
 // gs_iterate.cuh -- the persistent Gerchberg-Saxton iteration kernel for sm_103a.
 //
-// The kernel is a template on (log2 nx, log2 ny); gs_inst.cu instantiates it.
+// The kernel is a template on (log2 nx, log2 ny) and on where the transforms
+// run: the FP32 ALUs (gs_fft.cuh; gs_inst.cu instantiates every size) or the
+// tensor cores (gs_tc.cuh; gs_tc_inst.cu, square 256, 512 and 1024).
 //
 // One cooperative launch runs a whole run (or a chunk of up to 128 iterations)
 // of Eq. (e:AP), u^{nu+1} = P_S P_M u^nu, as a sequence of passes over the
@@ -32,10 +34,12 @@
 
 #include <cfloat>
 #include <cmath>
+#include <type_traits>
 
 #include "gs.h"
 #include "gs_fft.cuh"
 #include "gs_internal.h"
+#include "gs_tc.cuh"
 #include "gs_tma.cuh"
 
 namespace gsk {
@@ -63,6 +67,15 @@ constexpr int kAmpSmemBytes = 8192 * 4;  // amplitude of one column block (<= 81
 constexpr int kAmpSmemOffset = kGroupSmemBytes;
 constexpr int kBlockSmemOffset = kGroupSmemBytes + kAmpSmemBytes;
 constexpr int kBlockSmemBytes = 8192 * 8;  // one column block of the field
+// Tensor-core kernels only: the block's stage twiddles and cos/sin table.
+constexpr int kTcTwOffset = kBlockSmemOffset + kBlockSmemBytes;
+constexpr int kTcCsOffset = kTcTwOffset + kTcTwBytes;
+static_assert(kTcTwBytes + kTcCsBytes == kTcExtraSmemBytes, "tensor-core tables match the launch size");
+
+// Stands in for TcFft in the kernels whose transforms run on the FP32 ALUs.
+struct NoTc {
+  static constexpr bool kEnabled = false;
+};
 
 __device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
   unsigned v;
@@ -183,9 +196,10 @@ struct FieldLayout {
 // One pass over this block's share of rows (kInit, kRow; LOGN = log2 nx) or
 // column blocks (kCol, kResid; LOGN = log2 ny). Returns this thread's FP64
 // contribution to the pass's gap sum.
-template <int LOGN, int LX, int LY, bool HOLD>
+template <int LOGN, int LX, int LY, bool HOLD, class TCF>
 __device__ __forceinline__ double run_pass(const Params& p, int mb, int kind, bool last, unsigned char* smem,
-                                           Shared& sh, unsigned& mphase, const StageTw<LOGN>& tw_rows) {
+                                           Shared& sh, unsigned& mphase, const StageTw<LOGN>& tw_rows,
+                                           const TCF& tcf) {
   // this mask's arrays
   const size_t moff = static_cast<size_t>(mb) * static_cast<size_t>(p.mstride);
   float2* const Bm = p.B + moff;
@@ -209,7 +223,7 @@ __device__ __forceinline__ double run_pass(const Params& p, int mb, int kind, bo
   // stage twiddles: the kernel's register copy for square grids, else
   // loaded once for this pass
   StageTw<LOGN> tw_own;
-  if constexpr (!HOLD) tw_own.load(grp.tw, t);
+  if constexpr (!HOLD && !TCF::kEnabled) tw_own.load(grp.tw, t);
   const StageTw<LOGN>& stw = [&]() -> const StageTw<LOGN>& {
     if constexpr (HOLD) return tw_rows;
     else return tw_own;
@@ -219,6 +233,15 @@ __device__ __forceinline__ double run_pass(const Params& p, int mb, int kind, bo
   const int nfft = (kind == kCol || (kind == kRow && !(last && !p.final_resid))) ? 2 : 1;
   const float inv_sqrt_n = p.inv_sqrt_n;
   double acc = 0.0;
+  // One forward transform of the group's vector: on the FP32 ALUs, or on the
+  // tensor cores through the warp's slice of the exchange buffers.
+  auto fft = [&](float2(&x)[32]) {
+    if constexpr (TCF::kEnabled) {
+      tcf.run(x, smem + (threadIdx.x >> 5) * kTcWarpBytes, reinterpret_cast<const float2*>(smem + kTcTwOffset));
+    } else {
+      group_fft<LOGN>(x, grp, stw);
+    }
+  };
 
   if constexpr (LOGN == LX) {
   if (rows) {
@@ -262,7 +285,7 @@ __device__ __forceinline__ double run_pass(const Params& p, int mb, int kind, bo
       float part = 0.f;
 #pragma unroll 1
       for (int h = 0; h < nfft; ++h) {
-        group_fft<LOGN>(v, grp, stw);
+        fft(v);
         if (h != 0 || kind != kRow) continue;
         // v = swap(IDFT_x(B)) = swap(sqrt(N) P_M u^nu). Gap to S and Eq. (e:PS).
         if (p.p_slm == nullptr) {  // p = 1
@@ -382,7 +405,7 @@ __device__ __forceinline__ double run_pass(const Params& p, int mb, int kind, bo
       float part = 0.f;
 #pragma unroll 1
       for (int h = 0; h < nfft; ++h) {
-        group_fft<LOGN>(v, grp, stw);
+        fft(v);
         if (h != 0 || from_m) continue;
         // v = Y = F u^nu along this column. Residual and Eq. (e:Mhat).
         const float* mcol = ms + gq * N + t;
@@ -459,7 +482,7 @@ static __device__ void build_amplitude(const Params& p, int mb, float s, unsigne
   __syncthreads();
 }
 
-template <int LX, int LY>
+template <int LX, int LY, bool TC = false>
 __global__ void __launch_bounds__(kThreads, 1) gs_iterate(const Params p) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ Shared sh;
@@ -469,7 +492,17 @@ __global__ void __launch_bounds__(kThreads, 1) gs_iterate(const Params p) {
   unsigned target = 0;
   unsigned mphase = 0;
   StageTw<LX> tw_rows;  // square grids: stage twiddles held for the whole run
-  if constexpr (LX == LY) tw_rows.load(p.twx, threadIdx.x & ((1 << (LX - 5)) - 1));
+  if constexpr (LX == LY && !TC) tw_rows.load(p.twx, threadIdx.x & ((1 << (LX - 5)) - 1));
+  // Tensor-core transforms: the block's tables, then the DFT-matrix fragments
+  // held in registers for the whole run.
+  using TCF = typename std::conditional<TC, TcFft<LX>, NoTc>::type;
+  static_assert(!TC || LX == LY, "tensor-core kernels are square");
+  TCF tcf;
+  if constexpr (TC) {
+    tc_build_tables<LX>(reinterpret_cast<float2*>(smem + kTcTwOffset), reinterpret_cast<float2*>(smem + kTcCsOffset));
+    __syncthreads();
+    tcf.load(reinterpret_cast<const float2*>(smem + kTcCsOffset));
+  }
   if (threadIdx.x == 0) {
     mbar_init(&sh.mbar, 1);
     fence_barrier_init();
@@ -504,7 +537,10 @@ __global__ void __launch_bounds__(kThreads, 1) gs_iterate(const Params p) {
         const double total = warp_slot_sum(p, mb);
         if (threadIdx.x == 0) {
           const double ep = energy_of(p);
-          const bool bad = !(total > 0.0) || !(total <= DBL_MAX) || !(ep > 0.0) || !(ep <= DBL_MAX);
+          // FP16 operands: every transform input is below sqrt(n sum p^2)
+          // (Cauchy-Schwarz), which must stay below the FP16 range.
+          const bool range = !TC || (ep * static_cast<double>(p.nx) <= 2147483648.0);
+          const bool bad = !(total > 0.0) || !(total <= DBL_MAX) || !(ep > 0.0) || !(ep <= DBL_MAX) || !range;
           sh.bad[mb] = bad ? 1 : 0;
           if (b == 0) p.mask_flags[mb] = bad ? 1 : 0;  // for later launches of the run
           sh.scale[mb] = bad ? 0.f : static_cast<float>(sqrt(energy_of(p) / total));
@@ -567,11 +603,11 @@ __global__ void __launch_bounds__(kThreads, 1) gs_iterate(const Params p) {
       if (sh.bad[mb]) continue;
       double a;
       if constexpr (LX == LY) {
-        a = run_pass<LX, LX, LY, true>(p, mb, kind, last, smem, sh, mphase, tw_rows);
+        a = run_pass<LX, LX, LY, true>(p, mb, kind, last, smem, sh, mphase, tw_rows, tcf);
       } else {
         const StageTw<LY> none{};
-        a = (kind == kInit || kind == kRow) ? run_pass<LX, LX, LY, false>(p, mb, kind, last, smem, sh, mphase, tw_rows)
-                                            : run_pass<LY, LX, LY, false>(p, mb, kind, last, smem, sh, mphase, none);
+        a = (kind == kInit || kind == kRow) ? run_pass<LX, LX, LY, false>(p, mb, kind, last, smem, sh, mphase, tw_rows, tcf)
+                                            : run_pass<LY, LX, LY, false>(p, mb, kind, last, smem, sh, mphase, none, tcf);
       }
       if (slot >= 0) {
         const double tot = block_sum(a, sh);

@@ -48,8 +48,9 @@ static int log2_exact(int n) {
   return l;
 }
 
-static const void* kernel_for(int nx, int ny) {
+static const void* kernel_for(int nx, int ny, bool tc) {
   const int ly = log2_exact(ny);
+  if (tc) return nx == ny ? iterate_kernel_tc(ly) : nullptr;
   switch (log2_exact(nx)) {
     case 5: return iterate_kernel_lx<5>(ly);
     case 6: return iterate_kernel_lx<6>(ly);
@@ -63,26 +64,27 @@ static const void* kernel_for(int nx, int ny) {
   }
 }
 
-size_t iteration_smem_bytes(int nx, int ny) {
+size_t iteration_smem_bytes(int nx, int ny, bool tensor_core) {
   (void)nx;
   (void)ny;
-  // group exchange buffers, one column block of the amplitude, one of the field
-  return kGroupSmemBytes + 8192 * 4 + 8192 * 8;
+  // group exchange buffers, one column block of the amplitude, one of the
+  // field; then the tensor-core tables
+  return kGroupSmemBytes + 8192 * 4 + 8192 * 8 + (tensor_core ? kTcExtraSmemBytes : 0);
 }
 
-cudaError_t iteration_occupancy(int nx, int ny, int* blocks_per_sm) {
-  const void* k = kernel_for(nx, ny);
+cudaError_t iteration_occupancy(int nx, int ny, int* blocks_per_sm, bool tensor_core) {
+  const void* k = kernel_for(nx, ny, tensor_core);
   if (k == nullptr) return cudaErrorInvalidValue;
-  const size_t smem = iteration_smem_bytes(nx, ny);
+  const size_t smem = iteration_smem_bytes(nx, ny, tensor_core);
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
   if (e != cudaSuccess) return e;
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k, kThreads, smem);
 }
 
 cudaError_t launch_iterations(const Params& p, int grid, cudaStream_t s) {
-  const void* k = kernel_for(p.nx, p.ny);
+  const void* k = kernel_for(p.nx, p.ny, p.tensor_core != 0);
   if (k == nullptr) return cudaErrorInvalidValue;
-  const size_t smem = iteration_smem_bytes(p.nx, p.ny);
+  const size_t smem = iteration_smem_bytes(p.nx, p.ny, p.tensor_core != 0);
   void* args[] = {const_cast<Params*>(&p)};
   return cudaLaunchCooperativeKernel(k, dim3(grid), dim3(kThreads), args, smem, s);
 }

@@ -19,7 +19,7 @@ class GerchbergSaxton:
     """
 
     def __init__(self, nx: int, ny: int, final_residual: bool = True, stream=None, max_batch: int = 1,
-                 init_from_target: bool = False):
+                 init_from_target: bool = False, tensor_core: bool = False):
         import torch
 
         if stream is None:
@@ -28,7 +28,9 @@ class GerchbergSaxton:
         self.final_residual = bool(final_residual)
         self.stream = stream
         self.max_batch = int(max_batch)
-        flags = (B.GS_FINAL_RESIDUAL if final_residual else 0) | (B.GS_INIT_FROM_TARGET if init_from_target else 0)
+        flags = ((B.GS_FINAL_RESIDUAL if final_residual else 0) | (B.GS_INIT_FROM_TARGET if init_from_target else 0)
+                 | (B.GS_TENSOR_CORE if tensor_core else 0))
+        self.tensor_core = bool(tensor_core)
         self.init_from_target = bool(init_from_target)
         self._p = None
         self.handle = B.gs_create_batched(self.nx, self.ny, self.max_batch, flags, stream.cuda_stream)

@@ -119,6 +119,19 @@ WORKLOADS = {
 }
 
 
+def mixed_batch(seed: int, count: int = 64, sizes=(256, 512, 1024), spots=(10, 200)):
+    """``count`` masks of mixed size: each size drawn uniformly from ``sizes``
+    and each spot count uniformly from ``spots[0]..spots[1]``; peaks U[0.5, 1].
+    Returns a list of ``(I, phi0)``."""
+    rng = np.random.default_rng([seed, 0xB47C])
+    out = []
+    for k in range(count):
+        n = int(sizes[int(rng.integers(0, len(sizes)))])
+        ns = int(rng.integers(spots[0], spots[1] + 1))
+        out.append((spot_target(1000 * seed + k, n, n, ns, (0.5, 1.0)), random_phase(1000 * seed + k, n, n)))
+    return out
+
+
 def workload(name: str, seed: int = 0):
     """Return ``(I, phi0, iters)`` for a named workload."""
     w = WORKLOADS[name]

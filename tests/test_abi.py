@@ -72,6 +72,10 @@ def test_create_validates_before_cuda(lib):
         assert h.value is None
     assert lib.gs_create(None, 64, 64, 1, None) == B.GS_EINVAL
     assert lib.gs_create(ctypes.byref(h), 64, 64, 0x80, None) == B.GS_EINVAL
+    # the tensor-core form exists for square 256, 512 and 1024 only
+    for nx, ny in ((64, 64), (128, 128), (2048, 2048), (512, 256), (1024, 512)):
+        assert lib.gs_create(ctypes.byref(h), nx, ny, B.GS_FINAL_RESIDUAL | B.GS_TENSOR_CORE, None) == B.GS_EINVAL
+        assert h.value is None
 
 
 def test_null_context_calls(lib):
@@ -95,6 +99,7 @@ def test_noalloc_validates_before_cuda(lib):
     for nx, ny in ((1024, 512), (1024, 1024), (4096, 128), (4096, 4096), (16, 64), (33, 64), (64, 8192)):
         assert lib.gs_run_noalloc(nx, ny, 1, None, None, None, 1, None, None, None, None) == B.GS_EINVAL
     assert lib.gs_run_noalloc(64, 64, 0x80, None, None, None, 1, None, None, None, None) == B.GS_EINVAL
+    assert lib.gs_run_noalloc(256, 256, B.GS_TENSOR_CORE, None, None, None, 1, None, None, None, None) == B.GS_EINVAL
     assert lib.gs_run_noalloc(64, 64, 1, None, None, None, 1, None, None, None, None) == B.GS_EINVAL
     assert lib.gs_run_noalloc(64, 64, 1, None, None, None, -1, None, None, None, None) == B.GS_EINVAL
 
