@@ -19,7 +19,43 @@ constexpr size_t kAlign = 256;
 
 size_t align_up(size_t x) { return (x + kAlign - 1) & ~(kAlign - 1); }
 
-bool valid_dim(int n) { return n >= 32 && n <= 4096 && (n & (n - 1)) == 0; }
+bool is_pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
+
+// 2^a 3^b 5^c
+bool smooth5(int n) {
+  if (n < 1) return false;
+  for (int f : {2, 3, 5})
+    while (n % f == 0) n /= f;
+  return n == 1;
+}
+
+// A grid side: a power of two in [32, 4096], or a 5-smooth number in
+// [32, kMaxGeneralSide] (the general kernel).
+bool valid_dim(int n) {
+  if (n < 32) return false;
+  if (is_pow2(n)) return n <= 4096;
+  return n <= gsk::kMaxGeneralSide && smooth5(n);
+}
+
+// Radix plan of a 5-smooth length for the general kernel: radices 3 and 5
+// first (their unit-stride reads and odd-stride writes stay free of bank
+// conflicts while the sub-transforms are short), then 8s, then a 4 or 2.
+// Code c of stage s sits in bits 3s..3s+2 (2 -> 0, 3 -> 1, 4 -> 2, 5 -> 3, 8 -> 4).
+void radix_plan(int n, unsigned* plan, int* nst) {
+  std::vector<int> r;
+  while (n % 3 == 0) { r.push_back(3); n /= 3; }
+  while (n % 5 == 0) { r.push_back(5); n /= 5; }
+  while (n % 8 == 0) { r.push_back(8); n /= 8; }
+  if (n == 4) r.push_back(4);
+  if (n == 2) r.push_back(2);
+  unsigned code = 0;
+  for (size_t s = 0; s < r.size(); ++s) {
+    const unsigned c = r[s] == 2 ? 0u : r[s] == 3 ? 1u : r[s] == 4 ? 2u : r[s] == 5 ? 3u : 4u;
+    code |= c << (3 * s);
+  }
+  *plan = code;
+  *nst = static_cast<int>(r.size());
+}
 
 int ilog2i(int n) {
   int l = 0;
@@ -77,8 +113,14 @@ float2 unit_root(long long k, long long M) {
 // Stage twiddle tables of a length-n transform, in the layout stage_c reads:
 // for the stage after Ns = 2^nsl points (nsl = 5, 10) with radix R, entry
 // offset(nsl) + (m - 1) Ns + r holds W_{Ns R}^{r m}.
-std::vector<float2> twiddles(int n) {
+// The general kernel (a side that is not a power of two) reads instead the
+// plain table W_n^k, k < n, for both sides.
+std::vector<float2> twiddles(int n, bool general) {
   std::vector<float2> w(kTwiddleEntries, make_float2(0.f, 0.f));
+  if (general) {
+    for (int k = 0; k < n; ++k) w[k] = unit_root(k, n);
+    return w;
+  }
   for (int nsl = 5; nsl < 12; nsl += 5) {
     const int ns = 1 << nsl;
     if (n <= ns) break;
@@ -172,7 +214,7 @@ int gs_create_batched(gs_ctx** out, int nx, int ny, int max_batch, unsigned flag
   if ((flags & ~static_cast<unsigned>(GS_FINAL_RESIDUAL | GS_INIT_FROM_TARGET | GS_TENSOR_CORE)) != 0)
     return GS_EINVAL;
   const bool tc = (flags & GS_TENSOR_CORE) != 0;
-  if (tc && !(nx == ny && nx >= 256 && nx <= 1024)) return GS_EINVAL;
+  if (tc && !(nx == ny && is_pow2(nx) && nx >= 256 && nx <= 1024)) return GS_EINVAL;
   gs_ctx* c = new (std::nothrow) gs_ctx();
   if (c == nullptr) return GS_ENOMEM;
   c->nx = nx;
@@ -193,8 +235,9 @@ int gs_create_batched(gs_ctx** out, int nx, int ny, int max_batch, unsigned flag
     delete c;
     return GS_ENOMEM;
   }
-  const std::vector<float2> wx = twiddles(nx);
-  const std::vector<float2> wy = twiddles(ny);
+  const bool general = !is_pow2(nx) || !is_pow2(ny);
+  const std::vector<float2> wx = twiddles(nx, general);
+  const std::vector<float2> wy = twiddles(ny, general);
   const std::vector<float> ones(4096, 1.0f);
   bool ok = cudaMemcpy(c->ws + c->L.twx, wx.data(), wx.size() * sizeof(float2), cudaMemcpyHostToDevice) == cudaSuccess &&
             cudaMemcpy(c->ws + c->L.ones, ones.data(), ones.size() * sizeof(float), cudaMemcpyHostToDevice) == cudaSuccess &&
@@ -231,6 +274,8 @@ int gs_run_batched(gs_ctx* c, int batch, const float* target_intensity, const fl
   p.ny = c->ny;
   p.lognx = ilog2i(c->nx);
   p.logny = ilog2i(c->ny);
+  radix_plan(c->nx, &p.planx, &p.nstx);
+  radix_plan(c->ny, &p.plany, &p.nsty);
   p.B = at<float2>(c, c->L.B);
   p.mT = at<float>(c, c->L.mT);
   p.I = target_intensity;
@@ -374,13 +419,15 @@ int enqueue_loss(gs_ctx* c, const float* target_intensity, const float* phase, d
 }  // namespace
 
 int gs_loss_grad(gs_ctx* c, const float* target_intensity, const float* phase, double* loss_out, float* grad_out) {
-  if (c == nullptr || target_intensity == nullptr || phase == nullptr || loss_out == nullptr || c->nx != c->ny)
+  if (c == nullptr || target_intensity == nullptr || phase == nullptr || loss_out == nullptr || c->nx != c->ny ||
+      !is_pow2(c->nx))
     return GS_EINVAL;
   return enqueue_loss(c, target_intensity, phase, loss_out, grad_out, nullptr);
 }
 
 int gs_physical_error(gs_ctx* c, const float* target_intensity, const float* phase, double* error_out) {
-  if (c == nullptr || target_intensity == nullptr || phase == nullptr || error_out == nullptr || c->nx != c->ny)
+  if (c == nullptr || target_intensity == nullptr || phase == nullptr || error_out == nullptr || c->nx != c->ny ||
+      !is_pow2(c->nx))
     return GS_EINVAL;
   return enqueue_loss(c, target_intensity, phase, at<double>(c, c->L.lossbuf), nullptr, error_out);
 }

@@ -1,0 +1,275 @@
+// gs_general.cuh -- passes of the iteration kernel for grids whose sides are
+// not powers of two (any 5-smooth side 2^a 3^b 5^c in [32, 1536]), such as
+// the 800 x 600 SLM of Sec. V.
+//
+// The pass structure, projections and FP64 gap sums are those of the
+// power-of-two kernel (gs_iterate.cuh); what differs is the transform and the
+// data movement:
+//   * The field B is stored row-major [ny][nx]; m transposed [nx][ny].
+//   * A row pass gives each warp one row: the row is read coalesced into the
+//     warp's shared-memory buffer, transformed, projected and transformed
+//     again there, and written back coalesced.
+//   * A column pass moves 8 adjacent columns at a time: the block reads the
+//     [ny][8] tile in 64-byte row segments into eight per-warp column buffers,
+//     each warp transforms, projects and transforms its column, and the block
+//     writes the tile back the same way.
+//   * A length-n transform is a Stockham auto-sort FFT with radices 3 and 5
+//     first, then 8, 4 and 2 (gen_fft), each stage read from one of the warp's
+//     two buffers and written to the other; twiddles W_n^k come from a
+//     per-block shared-memory copy of a table rounded once from double.
+#pragma once
+
+#include "gs_common.cuh"
+#include "gs_fft.cuh"
+
+namespace gsk {
+
+// Radix of stage code c (3 bits per stage in Params::planx / plany).
+__host__ __device__ constexpr int radix_of_code(unsigned c) {
+  return c == 0 ? 2 : c == 1 ? 3 : c == 2 ? 4 : c == 3 ? 5 : 8;
+}
+
+// 3-point DFT, exp(-2 pi i jk/3): with t = a1 + a2 and d = (sqrt3/2)(a1 - a2),
+// y1,2 = a0 - t/2 -/+ i d.
+__device__ __forceinline__ void dft3(float2 (&a)[3]) {
+  constexpr float h = 0.8660254037844386f;  // sqrt(3)/2
+  const float2 t = cadd(a[1], a[2]);
+  const float2 d = make_float2(h * (a[1].x - a[2].x), h * (a[1].y - a[2].y));
+  const float2 c = make_float2(fmaf(-0.5f, t.x, a[0].x), fmaf(-0.5f, t.y, a[0].y));
+  a[0] = cadd(a[0], t);
+  a[1] = make_float2(c.x + d.y, c.y - d.x);
+  a[2] = make_float2(c.x - d.y, c.y + d.x);
+}
+
+// 5-point DFT, exp(-2 pi i jk/5), from the symmetric and antisymmetric pairs
+// b1 = a1 + a4, b2 = a2 + a3, d1 = a1 - a4, d2 = a2 - a3:
+//   y1,4 = a0 + c1 b1 + c2 b2 -/+ i (s1 d1 + s2 d2)
+//   y2,3 = a0 + c2 b1 + c1 b2 -/+ i (s2 d1 - s1 d2)
+// with ck = cos(2 pi k/5), sk = sin(2 pi k/5).
+__device__ __forceinline__ void dft5(float2 (&a)[5]) {
+  constexpr float c1 = 0.30901699437494745f, c2 = -0.8090169943749475f;
+  constexpr float s1 = 0.9510565162951535f, s2 = 0.5877852522924731f;
+  const float2 b1 = cadd(a[1], a[4]), b2 = cadd(a[2], a[3]);
+  const float2 d1 = csub(a[1], a[4]), d2 = csub(a[2], a[3]);
+  const float2 e1 = make_float2(fmaf(c1, b1.x, fmaf(c2, b2.x, a[0].x)), fmaf(c1, b1.y, fmaf(c2, b2.y, a[0].y)));
+  const float2 e2 = make_float2(fmaf(c2, b1.x, fmaf(c1, b2.x, a[0].x)), fmaf(c2, b1.y, fmaf(c1, b2.y, a[0].y)));
+  const float2 f1 = make_float2(fmaf(s1, d1.x, s2 * d2.x), fmaf(s1, d1.y, s2 * d2.y));
+  const float2 f2 = make_float2(fmaf(s2, d1.x, -s1 * d2.x), fmaf(s2, d1.y, -s1 * d2.y));
+  a[0] = cadd(a[0], cadd(b1, b2));
+  // e - i f = (e.x + f.y, e.y - f.x)
+  a[1] = make_float2(e1.x + f1.y, e1.y - f1.x);
+  a[4] = make_float2(e1.x - f1.y, e1.y + f1.x);
+  a[2] = make_float2(e2.x + f2.y, e2.y - f2.x);
+  a[3] = make_float2(e2.x - f2.y, e2.y + f2.x);
+}
+
+template <int R>
+__device__ __forceinline__ void small_dft(float2 (&a)[R]) {
+  if constexpr (R == 3) dft3(a);
+  else if constexpr (R == 5) dft5(a);
+  else dft<R>(a);
+}
+
+// One Stockham stage of radix R on a length-n transform whose first stages
+// formed sub-transforms of length ns: butterfly j (r = j mod ns) reads
+// src[j + m n/R], multiplies by W_{ns R}^{r m} = W_n^{(n/(ns R)) r m},
+// transforms over m and writes dst[(j - r) R + r + k ns].
+template <int R>
+__device__ __forceinline__ void gen_stage(const float2* src, float2* dst, int n, int ns, const float2* tw) {
+  const int nb = n / R;
+  const int step = n / (ns * R);
+  for (int j = threadIdx.x & 31; j < nb; j += 32) {
+    const int r = j % ns;
+    float2 a[R];
+#pragma unroll
+    for (int m = 0; m < R; ++m) a[m] = src[j + m * nb];
+    if (ns > 1) {
+#pragma unroll
+      for (int m = 1; m < R; ++m) a[m] = cmul(a[m], tw[step * r * m]);
+    }
+    small_dft<R>(a);
+    const int base = (j - r) * R + r;
+#pragma unroll
+    for (int k = 0; k < R; ++k) dst[base + k * ns] = a[k];
+  }
+}
+
+// Forward unnormalised DFT of the length-n vector in `a` by the warp, using
+// `b` as the second buffer; returns the buffer that holds the result (a for
+// an even number of stages, b for an odd one).
+__device__ __forceinline__ float2* gen_fft(float2* a, float2* b, int n, unsigned plan, int nst, const float2* tw) {
+  int ns = 1;
+#pragma unroll 1
+  for (int s = 0; s < nst; ++s) {
+    const int R = radix_of_code((plan >> (3 * s)) & 7u);
+    switch (R) {
+      case 2: gen_stage<2>(a, b, n, ns, tw); break;
+      case 3: gen_stage<3>(a, b, n, ns, tw); break;
+      case 4: gen_stage<4>(a, b, n, ns, tw); break;
+      case 5: gen_stage<5>(a, b, n, ns, tw); break;
+      default: gen_stage<8>(a, b, n, ns, tw); break;
+    }
+    __syncwarp();
+    ns *= R;
+    float2* t = a;
+    a = b;
+    b = t;
+  }
+  return a;
+}
+
+// Copy the twiddle tables to shared memory (once per launch).
+__device__ __forceinline__ void gen_load_twiddles(const Params& p, unsigned char* smem) {
+  float2* t = reinterpret_cast<float2*>(smem);
+  for (int e = threadIdx.x; e < p.nx; e += kThreads) t[e] = p.twx[e];
+  for (int e = threadIdx.x; e < p.ny; e += kThreads) t[p.nx + e] = p.twy[e];
+  __syncthreads();
+}
+
+// m = s sqrt(I), transposed ([nx][ny]), for this block's columns.
+__device__ __forceinline__ void gen_build_amplitude(const Params& p, int mb, float s) {
+  const size_t moff = static_cast<size_t>(mb) * static_cast<size_t>(p.mstride);
+  const float* const Im = p.I + moff;
+  float* const mTm = p.mT + moff;
+  const int lo = split(blockIdx.x, gridDim.x, p.nx);
+  const int hi = split(blockIdx.x + 1, gridDim.x, p.nx);
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int x = lo + w; x < hi; x += kThreads / 32)
+    for (int y = lane; y < p.ny; y += 32)
+      mTm[static_cast<size_t>(x) * p.ny + y] = s * sqrtf(Im[static_cast<size_t>(y) * p.nx + x]);
+  __syncthreads();
+}
+
+// Wrap an angle as the power-of-two kernel does: (-pi, pi].
+__device__ __forceinline__ float gen_phase(float2 u) {
+  const float a = atan2f(u.y, u.x);
+  return (a <= -3.14159274f) ? 3.14159274f : a;
+}
+
+// One pass over this block's share of rows (kInit, kRow) or of 8-column
+// groups (kCol, kResid, kInitM). Returns this thread's FP64 contribution to
+// the pass's gap sum.
+static __device__ __noinline__ double run_pass_gen(const Params& p, int mb, int kind, bool last, unsigned char* smem) {
+  const size_t moff = static_cast<size_t>(mb) * static_cast<size_t>(p.mstride);
+  float2* const Bm = p.B + moff;
+  const float* const mTm = p.mT + moff;
+  const int nx = p.nx, ny = p.ny;
+  const int nmax = nx > ny ? nx : ny;
+  const float2* twx = reinterpret_cast<const float2*>(smem);
+  const float2* twy = twx + nx;
+  float2* wbase = reinterpret_cast<float2*>(smem) + gen_tw_entries(nx, ny);
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  float2* const A = wbase + w * gen_warp_stride(nmax);
+  float2* const Bf = A + nmax + 1;
+  const float inv_sqrt_n = p.inv_sqrt_n;
+  const bool two = (kind == kCol || (kind == kRow && !(last && !p.final_resid)));
+  double acc = 0.0;
+
+  if (kind == kInit || kind == kRow) {
+    const int lo = split(blockIdx.x, gridDim.x, ny);
+    const int hi = split(blockIdx.x + 1, gridDim.x, ny);
+    for (int row = lo + w; row < hi; row += kThreads / 32) {
+      float2* src = Bm + static_cast<size_t>(row) * nx;
+      const float* pp = p.p_slm ? p.p_slm + static_cast<size_t>(row) * nx : nullptr;
+      if (kind == kInit) {
+        const float* ph = p.phi_in + moff + static_cast<size_t>(row) * nx;
+        float* po = p.phi_out + moff + static_cast<size_t>(row) * nx;
+        for (int x = lane; x < nx; x += 32) {
+          float s, c;
+          sincosf(ph[x], &s, &c);
+          const float a = pp ? pp[x] : 1.f;  // u0 = p exp(i phi0)
+          A[x] = make_float2(a * c, a * s);
+          if (last) po[x] = gen_phase(A[x]);  // zero iterations
+        }
+      } else {
+        for (int x = lane; x < nx; x += 32) A[x] = src[x];
+      }
+      __syncwarp();
+      float2* res = gen_fft(A, Bf, nx, p.planx, p.nstx, twx);
+      if (kind == kRow) {
+        // res = swap(IDFT_x(B)) = swap(sqrt(N) P_M u^nu): gap to S, Eq. (e:PS)
+        float part = 0.f;
+        float* po = p.phi_out + moff + static_cast<size_t>(row) * nx;
+        for (int x = lane; x < nx; x += 32) {
+          const float2 t = res[x];
+          const float vx = t.y, vy = t.x;
+          const float a = pp ? pp[x] : 1.f;
+          const float a2 = vx * vx + vy * vy;
+          const float rs = rsqrtf(a2);
+          const float mag = a2 > 0.f ? a2 * rs : 0.f;
+          const float d = mag * inv_sqrt_n - a;
+          part += d * d;
+          const float f = a * rs;
+          const float2 u = a2 > 0.f ? make_float2(vx * f, vy * f) : make_float2(a, 0.f);
+          res[x] = u;
+          if (last) po[x] = gen_phase(u);
+        }
+        acc += static_cast<double>(part);
+        __syncwarp();
+        if (two) res = gen_fft(res, res == A ? Bf : A, nx, p.planx, p.nstx, twx);
+      }
+      if (kind == kInit || two)
+        for (int x = lane; x < nx; x += 32) src[x] = res[x];
+      __syncwarp();
+    }
+    return acc;
+  }
+
+  // Column passes: groups of 8 adjacent columns; warp k owns column c0 + k.
+  const int ncg = (nx + 7) >> 3;
+  const int lo = split(blockIdx.x, gridDim.x, ncg);
+  const int hi = split(blockIdx.x + 1, gridDim.x, ncg);
+  const int stride = gen_warp_stride(nmax);
+  const bool store = (kind == kCol || kind == kInitM);
+  // which of a warp's buffers holds the stored result: A after two transforms,
+  // else A or Bf by the parity of the stage count
+  const int out_off = (kind == kCol || (p.nsty & 1) == 0) ? 0 : nmax + 1;
+  for (int cg = lo; cg < hi; ++cg) {
+    const int c0 = cg << 3;
+    const int wc = min(8, nx - c0);
+    __syncthreads();  // the previous group's tile has been written back
+    for (int e = threadIdx.x; e < ny * 8; e += kThreads) {
+      const int y = e >> 3, k = e & 7;
+      if (k < wc)
+        wbase[k * stride + y] = (kind == kInitM)
+                                    ? make_float2(0.f, mTm[static_cast<size_t>(c0 + k) * ny + y])  // swap((m, 0))
+                                    : Bm[static_cast<size_t>(y) * nx + c0 + k];
+    }
+    __syncthreads();
+    if (w < wc) {
+      float2* res = gen_fft(A, Bf, ny, p.plany, p.nsty, twy);
+      if (kind != kInitM) {
+        // res = Y = F u^nu along this column: residual and Eq. (e:Mhat)
+        const float* mcol = mTm + static_cast<size_t>(c0 + w) * ny;
+        float part = 0.f;
+        for (int y = lane; y < ny; y += 32) {
+          const float m = mcol[y];
+          const float2 Y = res[y];
+          const float a2 = Y.x * Y.x + Y.y * Y.y;
+          const float rs = rsqrtf(a2);
+          const float mag = a2 > 0.f ? a2 * rs : 0.f;
+          const float d = mag * inv_sqrt_n - m;
+          part += d * d;
+          if (kind == kCol) {
+            const float f = m * rs;
+            const float2 Yh = a2 > 0.f ? make_float2(Y.x * f, Y.y * f) : make_float2(m, 0.f);
+            res[y] = make_float2(Yh.y, Yh.x);  // swapped: the next forward DFT acts as the inverse
+          }
+        }
+        acc += static_cast<double>(part);
+        __syncwarp();
+        if (kind == kCol) res = gen_fft(res, res == A ? Bf : A, ny, p.plany, p.nsty, twy);
+      }
+    }
+    if (store) {
+      __syncthreads();
+      for (int e = threadIdx.x; e < ny * 8; e += kThreads) {
+        const int y = e >> 3, k = e & 7;
+        if (k < wc) Bm[static_cast<size_t>(y) * nx + c0 + k] = wbase[k * stride + out_off + y];
+      }
+    }
+  }
+  return acc;
+}
+
+}  // namespace gsk

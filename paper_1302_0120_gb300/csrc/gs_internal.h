@@ -51,7 +51,26 @@ struct Params {
   float inv_sqrt_n;    // 1/sqrt(N)
   double inv_n;        // 1/N
   int tensor_core;     // host side: launch the tensor-core kernel (square 256, 512, 1024)
+  // Grids with a side that is not a power of two (gs_general.cuh): the
+  // radices of the row and column transforms, 3 bits per stage (code c means
+  // radix kRadixOf[c]), first stage in the low bits, and the stage counts.
+  unsigned planx, plany;
+  int nstx, nsty;
 };
+
+// Sides of the general kernel: 5-smooth (2^a 3^b 5^c) in [32, kMaxGeneralSide].
+constexpr int kMaxGeneralSide = 1536;
+constexpr int kMaxGeneralStages = 10;
+
+// Shared-memory layout of the general kernel: the two twiddle tables (nx,
+// then ny complex), then per warp two buffers of max(nx, ny) complex.
+inline __host__ __device__ int gen_tw_entries(int nx, int ny) { return (nx + ny + 1) & ~1; }
+inline __host__ __device__ int gen_warp_stride(int nmax) { return 2 * nmax + 2; }  // complex; 16-byte multiple
+inline __host__ __device__ size_t gen_smem_bytes(int nx, int ny) {
+  const int nmax = nx > ny ? nx : ny;
+  return (static_cast<size_t>(gen_tw_entries(nx, ny)) + static_cast<size_t>(kThreads / 32) * gen_warp_stride(nmax)) *
+         sizeof(float2);
+}
 
 // Kernel for log2(nx) = LX and the given log2(ny); defined per LX in gs_inst.cu.
 template <int LX>
@@ -59,6 +78,8 @@ const void* iterate_kernel_lx(int ly);
 // Kernel with tensor-core transforms for an n x n grid, log2(n) = l in 8..10
 // (gs_tc_inst.cu); null otherwise.
 const void* iterate_kernel_tc(int l);
+// Kernel for grids with a side that is not a power of two (gs_general_inst.cu).
+const void* iterate_kernel_general();
 
 size_t iteration_smem_bytes(int nx, int ny, bool tensor_core = false);
 

@@ -37,36 +37,15 @@
 #include <type_traits>
 
 #include "gs.h"
+#include "gs_common.cuh"
 #include "gs_fft.cuh"
+#include "gs_general.cuh"
 #include "gs_internal.h"
 #include "gs_tc.cuh"
 #include "gs_tma.cuh"
 
 namespace gsk {
 
-enum PassKind { kInit = 0, kCol = 1, kRow = 2, kResid = 3, kInitM = 4 };
-
-// A barrier wait gives up after this long and reports GS_ETIMEOUT.
-constexpr unsigned long long kBarrierTimeoutNs = 1000000000ull;
-constexpr unsigned kMaxSpins = 1u << 26;
-
-struct Shared {
-  uint64_t mbar;  // completion of the amplitude bulk copy
-  int flag;
-  int pending;    // a bulk copy into shared memory may still be in flight
-  int m_block;    // column block whose amplitude is in shared memory (-1: none)
-  unsigned pending_phase;  // the mbarrier phase that copy completes
-  double red[kThreads / 32];
-  float scale[kMaxBatch];  // sqrt(N / sum I) per mask
-  int bad[kMaxBatch];      // mask with a non-finite, negative or zero target
-};
-
-// Shared-memory layout of the iteration kernel (dynamic part): group exchange
-// buffers, the staged amplitude columns, then the staged field columns.
-constexpr int kAmpSmemBytes = 8192 * 4;  // amplitude of one column block (<= 8192 values)
-constexpr int kAmpSmemOffset = kGroupSmemBytes;
-constexpr int kBlockSmemOffset = kGroupSmemBytes + kAmpSmemBytes;
-constexpr int kBlockSmemBytes = 8192 * 8;  // one column block of the field
 // Tensor-core kernels only: the block's stage twiddles and cos/sin table.
 constexpr int kTcTwOffset = kBlockSmemOffset + kBlockSmemBytes;
 constexpr int kTcCsOffset = kTcTwOffset + kTcTwBytes;
@@ -76,94 +55,6 @@ static_assert(kTcTwBytes + kTcCsBytes == kTcExtraSmemBytes, "tensor-core tables 
 struct NoTc {
   static constexpr bool kEnabled = false;
 };
-
-__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
-  unsigned v;
-  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
-
-__device__ __forceinline__ unsigned long long global_ns() {
-  unsigned long long t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-
-__device__ __forceinline__ void fail(const Params& p, int code) {
-  atomicCAS(p.status, 0, code);
-  atomicExch(p.abort_flag, 1);
-}
-
-// sum p^2 of the SLM amplitude (N for p = 1): the energy of every field in S.
-__device__ __forceinline__ double energy_of(const Params& p) {
-  return p.p_slm ? *p.energy : static_cast<double>(p.nx) * p.ny;
-}
-
-// Record an error for the host without stopping the run (other masks go on).
-__device__ __forceinline__ void fail_status(const Params& p, int code) { atomicCAS(p.status, 0, code); }
-
-// Contiguous share [lo, hi) of `total` items for block b of G.
-__device__ __forceinline__ int split(int b, int G, int total) {
-  return static_cast<int>((static_cast<long long>(b) * total) / G);
-}
-
-// Sum of one double per thread over the block, in a fixed order. The result
-// is returned to every thread.
-static __device__ double block_sum(double x, Shared& sh) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-  __syncthreads();
-  if ((threadIdx.x & 31) == 0) sh.red[threadIdx.x >> 5] = x;
-  __syncthreads();
-  double s = 0.0;
-#pragma unroll
-  for (int w = 0; w < kThreads / 32; ++w) s += sh.red[w];
-  return s;
-}
-
-// Sum of partials[row][0..G) in a fixed order (row = slot * batch + mask),
-// computed by one warp; the result is returned to every lane of that warp.
-static __device__ double warp_slot_sum(const Params& p, int row) {
-  const int G = gridDim.x;
-  const double* src = p.partials + static_cast<size_t>(row) * G;
-  double s = 0.0;
-  for (int c = threadIdx.x & 31; c < G; c += 32) s += src[c];
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  return s;
-}
-
-// Grid-wide barrier over a zero-initialised arrival counter. Returns false in
-// every thread of the block if the wait gave up (status GS_ETIMEOUT).
-static __device__ bool grid_sync(const Params& p, unsigned& target, Shared& sh) {
-  __syncthreads();
-  target += gridDim.x;
-  if (threadIdx.x == 0) {
-    int ok = 1;
-    __threadfence();
-    atomicAdd(p.bar, 1u);
-    const unsigned want = target + p.extra_arrivals;
-    unsigned spins = 0;
-    unsigned long long t0 = 0;
-    while (static_cast<int>(ld_acquire_gpu(p.bar) - want) < 0) {
-      ++spins;
-      if ((spins & 255u) == 0) {
-        const unsigned long long now = global_ns();
-        if (t0 == 0) t0 = now;
-        if (now - t0 > kBarrierTimeoutNs || spins > kMaxSpins) {
-          ok = 0;
-          fail(p, GS_ETIMEOUT);
-          break;
-        }
-      }
-    }
-    __threadfence();
-    if (ok && *reinterpret_cast<volatile int*>(p.abort_flag) != 0) ok = 0;  // another block failed
-    sh.flag = ok;
-  }
-  __syncthreads();
-  return sh.flag != 0;
-}
 
 // Storage of the field B between passes: column blocks of W adjacent columns,
 // each block one contiguous [ny][W] array, with the W elements of each of its
@@ -492,7 +383,7 @@ __global__ void __launch_bounds__(kThreads, 1) gs_iterate(const Params p) {
   unsigned target = 0;
   unsigned mphase = 0;
   StageTw<LX> tw_rows;  // square grids: stage twiddles held for the whole run
-  if constexpr (LX == LY && !TC) tw_rows.load(p.twx, threadIdx.x & ((1 << (LX - 5)) - 1));
+  if constexpr (LX > 0 && LX == LY && !TC) tw_rows.load(p.twx, threadIdx.x & ((1 << (LX - 5)) - 1));
   // Tensor-core transforms: the block's tables, then the DFT-matrix fragments
   // held in registers for the whole run.
   using TCF = typename std::conditional<TC, TcFft<LX>, NoTc>::type;
@@ -510,6 +401,7 @@ __global__ void __launch_bounds__(kThreads, 1) gs_iterate(const Params p) {
     sh.m_block = -1;
   }
   __syncthreads();
+  if constexpr (LX == 0) gen_load_twiddles(p, smem);  // sides that are not powers of two
 
   if (p.do_init) {
     // A0: FP64 energy of each mask's target over this block's rows. A
@@ -570,7 +462,10 @@ __global__ void __launch_bounds__(kThreads, 1) gs_iterate(const Params p) {
       }
     }
     for (int mb = 0; mb < p.batch; ++mb)
-      if (!sh.bad[mb]) build_amplitude(p, mb, sh.scale[mb], smem);
+      if (!sh.bad[mb]) {
+        if constexpr (LX == 0) gen_build_amplitude(p, mb, sh.scale[mb]);
+        else build_amplitude(p, mb, sh.scale[mb], smem);
+      }
   } else if (threadIdx.x == 0) {
     // later launches of a run: the invalid masks were flagged by the first
     for (int mb = 0; mb < p.batch; ++mb) sh.bad[mb] = p.mask_flags[mb];
@@ -602,7 +497,9 @@ __global__ void __launch_bounds__(kThreads, 1) gs_iterate(const Params p) {
     for (int mb = 0; mb < p.batch; ++mb) {
       if (sh.bad[mb]) continue;
       double a;
-      if constexpr (LX == LY) {
+      if constexpr (LX == 0) {
+        a = run_pass_gen(p, mb, kind, last, smem);
+      } else if constexpr (LX == LY) {
         a = run_pass<LX, LX, LY, true>(p, mb, kind, last, smem, sh, mphase, tw_rows, tcf);
       } else {
         const StageTw<LY> none{};

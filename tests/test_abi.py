@@ -60,20 +60,24 @@ def test_workspace_bytes(lib):
         assert w >= 20 * n * n
         assert w < 20 * n * n + (4 << 20)
     assert B.gs_workspace_bytes(1024, 512) > 0
-    for bad in ((16, 64), (64, 16), (33, 64), (8192, 64), (0, 0), (-64, 64), (100, 128)):
+    # sides that are not powers of two: 5-smooth, at most 1536
+    for ok in ((800, 600), (600, 800), (1536, 1536), (96, 4096), (1000, 45 * 32)):
+        assert B.gs_workspace_bytes(*ok) >= 20 * ok[0] * ok[1]
+    for bad in ((16, 64), (64, 16), (33, 64), (8192, 64), (0, 0), (-64, 64), (98, 128), (77, 64), (1600, 600),
+                (1620, 64), (30, 64)):
         assert B.gs_workspace_bytes(*bad) == 0
 
 
 def test_create_validates_before_cuda(lib):
     h = ctypes.c_void_p(123)
-    for nx, ny in ((33, 64), (64, 8192), (16, 16), (0, 64)):
+    for nx, ny in ((33, 64), (64, 8192), (16, 16), (0, 64), (98, 64), (1600, 600)):
         rc = lib.gs_create(ctypes.byref(h), nx, ny, 1, None)
         assert rc == B.GS_EINVAL
         assert h.value is None
     assert lib.gs_create(None, 64, 64, 1, None) == B.GS_EINVAL
     assert lib.gs_create(ctypes.byref(h), 64, 64, 0x80, None) == B.GS_EINVAL
     # the tensor-core form exists for square 256, 512 and 1024 only
-    for nx, ny in ((64, 64), (128, 128), (2048, 2048), (512, 256), (1024, 512)):
+    for nx, ny in ((64, 64), (128, 128), (2048, 2048), (512, 256), (1024, 512), (800, 800), (768, 768)):
         assert lib.gs_create(ctypes.byref(h), nx, ny, B.GS_FINAL_RESIDUAL | B.GS_TENSOR_CORE, None) == B.GS_EINVAL
         assert h.value is None
 

@@ -49,7 +49,7 @@ def check_fft_direct(shape, seed=0):
     assert err2 <= 1e-12, err2
 
 
-@pytest.mark.parametrize("shape", [(8, 8), (16, 16), (32, 32), (8, 32), (32, 8)])
+@pytest.mark.parametrize("shape", [(8, 8), (16, 16), (32, 32), (8, 32), (32, 8), (6, 10), (15, 12), (24, 20), (45, 8)])
 def test_fft_matches_direct_dft(shape):
     check_fft_direct(shape)
 
@@ -220,9 +220,22 @@ def test_gap_chain_nonsquare():
     assert np.all(r[:-1] - g >= -1e-12) and np.all(g - r[1:] >= -1e-12)
 
 
-def check_consistent_fixed_point(n=32, seed=1):
+def test_gap_chain_not_power_of_two():
+    """The 800 x 600 grid of Sec. V, scaled down to 40 x 30 (5-smooth sides)."""
+    I = S.spot_target(10, 30, 40, 5, (0.5, 1.0))
+    phi0 = S.random_phase(10, 30, 40)
+    res = O.gs_run(I, phi0, 25)
+    r, g = res["r"], res["g"]
+    assert np.all(r[:-1] - g >= -1e-12) and np.all(g - r[1:] >= -1e-12) and r[-1] < r[0]
+
+
+def test_consistent_fixed_point_not_power_of_two():
+    check_consistent_fixed_point(shape=(30, 40))
+
+
+def check_consistent_fixed_point(n=32, seed=1, shape=None):
     rng = np.random.default_rng(seed)
-    phi_t = (rng.random((n, n)) * 2 * np.pi).astype(np.float32)
+    phi_t = (rng.random(shape or (n, n)) * 2 * np.pi).astype(np.float32)
     I = O.consistent_target(phi_t)  # FP64, exact
     res = O.gs_run(I, phi_t, 1)
     assert res["r"][0] <= 1e-12 and res["r"][1] <= 1e-12 and res["g"][0] <= 1e-12
