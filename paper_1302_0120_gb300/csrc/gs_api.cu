@@ -113,12 +113,25 @@ float2 unit_root(long long k, long long M) {
 // Stage twiddle tables of a length-n transform, in the layout stage_c reads:
 // for the stage after Ns = 2^nsl points (nsl = 5, 10) with radix R, entry
 // offset(nsl) + (m - 1) Ns + r holds W_{Ns R}^{r m}.
-// The general kernel (a side that is not a power of two) reads instead the
-// plain table W_n^k, k < n, for both sides.
+// The general kernel (a side that is not a power of two) reads instead, for
+// both sides, the stage tables of its radix plan: the stage with
+// sub-transform length ns and radix R holds W_{ns R}^{r m} at entry
+// ns - 1 + (m - 1) ns + r (1 <= m < R, r < ns); n - 1 entries in all.
 std::vector<float2> twiddles(int n, bool general) {
   std::vector<float2> w(kTwiddleEntries, make_float2(0.f, 0.f));
   if (general) {
-    for (int k = 0; k < n; ++k) w[k] = unit_root(k, n);
+    unsigned plan = 0;
+    int nst = 0;
+    radix_plan(n, &plan, &nst);
+    int ns = 1;
+    for (int s = 0; s < nst; ++s) {
+      const unsigned c = (plan >> (3 * s)) & 7u;
+      const int R = c == 0 ? 2 : c == 1 ? 3 : c == 2 ? 4 : c == 3 ? 5 : 8;
+      for (int m = 1; m < R; ++m)
+        for (int r = 0; r < ns; ++r)
+          w[ns - 1 + (m - 1) * ns + r] = unit_root(static_cast<long long>(r) * m, static_cast<long long>(ns) * R);
+      ns *= R;
+    }
     return w;
   }
   for (int nsl = 5; nsl < 12; nsl += 5) {

@@ -15,12 +15,19 @@
 //     writes the tile back the same way.
 //   * A length-n transform is a Stockham auto-sort FFT with radices 3 and 5
 //     first, then 8, 4 and 2 (gen_fft), each stage read from one of the warp's
-//     two buffers and written to the other; twiddles W_n^k come from a
-//     per-block shared-memory copy of a table rounded once from double.
+//     two buffers and written to the other. Each lane takes several
+//     butterflies at once so that their shared-memory loads overlap. The
+//     twiddles of the stage with sub-transform length ns and radix R sit at
+//     entries ns - 1 + (m - 1) ns + r (W_{ns R}^{r m}), so that consecutive
+//     butterflies read consecutive entries; the tables are rounded once from
+//     double on the host and copied to shared memory per launch.
+//   * Rows and column tiles arrive by cp.async, every copy of a lane in
+//     flight at once.
 #pragma once
 
 #include "gs_common.cuh"
 #include "gs_fft.cuh"
+#include "gs_tma.cuh"
 
 namespace gsk {
 
@@ -71,26 +78,53 @@ __device__ __forceinline__ void small_dft(float2 (&a)[R]) {
 }
 
 // One Stockham stage of radix R on a length-n transform whose first stages
-// formed sub-transforms of length ns: butterfly j (r = j mod ns) reads
-// src[j + m n/R], multiplies by W_{ns R}^{r m} = W_n^{(n/(ns R)) r m},
-// transforms over m and writes dst[(j - r) R + r + k ns].
+// formed sub-transforms of length ns: butterfly j = q ns + r reads
+// src[j + m n/R], multiplies by W_{ns R}^{r m} (stage table tw), transforms
+// over m and writes dst[q ns R + r + k ns]. A lane takes U butterflies
+// (j, j + 32, ...) at a time.
 template <int R>
-__device__ __forceinline__ void gen_stage(const float2* src, float2* dst, int n, int ns, const float2* tw) {
+__device__ __forceinline__ void gen_stage(const float2* __restrict__ src, float2* __restrict__ dst, int n, int ns,
+                                          const float2* __restrict__ tw) {
+  constexpr int U = 1;
   const int nb = n / R;
-  const int step = n / (ns * R);
-  for (int j = threadIdx.x & 31; j < nb; j += 32) {
-    const int r = j % ns;
-    float2 a[R];
+  const int lane = threadIdx.x & 31;
+  const int qinc = 32 / ns, rinc = 32 % ns;
+  int q = lane / ns, r = lane % ns;
+  const float2* const tws = tw + (ns - 1);
+  for (int j0 = lane; j0 < nb; j0 += 32 * U) {
+    float2 a[U][R];
+    int base[U], rr[U];
 #pragma unroll
-    for (int m = 0; m < R; ++m) a[m] = src[j + m * nb];
+    for (int u = 0; u < U; ++u) {
+      const int j = j0 + 32 * u;
+      rr[u] = r;
+      base[u] = q * ns * R + r;
+      if (j < nb) {
+#pragma unroll
+        for (int m = 0; m < R; ++m) a[u][m] = src[j + m * nb];
+      }
+      q += qinc;
+      r += rinc;
+      if (r >= ns) {
+        r -= ns;
+        ++q;
+      }
+    }
     if (ns > 1) {
 #pragma unroll
-      for (int m = 1; m < R; ++m) a[m] = cmul(a[m], tw[step * r * m]);
-    }
-    small_dft<R>(a);
-    const int base = (j - r) * R + r;
+      for (int u = 0; u < U; ++u)
+        if (j0 + 32 * u < nb) {
 #pragma unroll
-    for (int k = 0; k < R; ++k) dst[base + k * ns] = a[k];
+          for (int m = 1; m < R; ++m) a[u][m] = cmul(a[u][m], tws[(m - 1) * ns + rr[u]]);
+        }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (j0 + 32 * u < nb) {
+        small_dft<R>(a[u]);
+#pragma unroll
+        for (int k = 0; k < R; ++k) dst[base[u] + k * ns] = a[u][k];
+      }
   }
 }
 
@@ -140,6 +174,14 @@ __device__ __forceinline__ void gen_build_amplitude(const Params& p, int mb, flo
   __syncthreads();
 }
 
+// Asynchronous 8-byte copy global -> shared (cp.async); completed for the
+// issuing thread by cp_async_wait_all.
+__device__ __forceinline__ void cp_async8(void* dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 // Wrap an angle as the power-of-two kernel does: (-pi, pi].
 __device__ __forceinline__ float gen_phase(float2 u) {
   const float a = atan2f(u.y, u.x);
@@ -149,7 +191,7 @@ __device__ __forceinline__ float gen_phase(float2 u) {
 // One pass over this block's share of rows (kInit, kRow) or of 8-column
 // groups (kCol, kResid, kInitM). Returns this thread's FP64 contribution to
 // the pass's gap sum.
-static __device__ __noinline__ double run_pass_gen(const Params& p, int mb, int kind, bool last, unsigned char* smem) {
+static __device__ __forceinline__ double run_pass_gen(const Params& p, int mb, int kind, bool last, unsigned char* smem) {
   const size_t moff = static_cast<size_t>(mb) * static_cast<size_t>(p.mstride);
   float2* const Bm = p.B + moff;
   const float* const mTm = p.mT + moff;
@@ -174,38 +216,63 @@ static __device__ __noinline__ double run_pass_gen(const Params& p, int mb, int 
       if (kind == kInit) {
         const float* ph = p.phi_in + moff + static_cast<size_t>(row) * nx;
         float* po = p.phi_out + moff + static_cast<size_t>(row) * nx;
-        for (int x = lane; x < nx; x += 32) {
-          float s, c;
-          sincosf(ph[x], &s, &c);
-          const float a = pp ? pp[x] : 1.f;  // u0 = p exp(i phi0)
-          A[x] = make_float2(a * c, a * s);
-          if (last) po[x] = gen_phase(A[x]);  // zero iterations
+        for (int x0 = lane; x0 < nx; x0 += 32 * 4) {
+          float f[4], a[4];
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            const int x = x0 + 32 * k;
+            f[k] = x < nx ? ph[x] : 0.f;
+            a[k] = (pp && x < nx) ? pp[x] : 1.f;  // u0 = p exp(i phi0)
+          }
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            float s, c;
+            sincosf(f[k], &s, &c);
+            if (x0 + 32 * k < nx) A[x0 + 32 * k] = make_float2(a[k] * c, a[k] * s);
+          }
+        }
+        if (last) {  // zero iterations
+          __syncwarp();
+          for (int x = lane; x < nx; x += 32) po[x] = gen_phase(A[x]);
         }
       } else {
-        for (int x = lane; x < nx; x += 32) A[x] = src[x];
+        for (int x = lane; x < nx; x += 32) cp_async8(A + x, src + x);
+        cp_async_wait_all();
       }
       __syncwarp();
       float2* res = gen_fft(A, Bf, nx, p.planx, p.nstx, twx);
       if (kind == kRow) {
         // res = swap(IDFT_x(B)) = swap(sqrt(N) P_M u^nu): gap to S, Eq. (e:PS)
         float part = 0.f;
-        float* po = p.phi_out + moff + static_cast<size_t>(row) * nx;
-        for (int x = lane; x < nx; x += 32) {
-          const float2 t = res[x];
-          const float vx = t.y, vy = t.x;
-          const float a = pp ? pp[x] : 1.f;
-          const float a2 = vx * vx + vy * vy;
-          const float rs = rsqrtf(a2);
-          const float mag = a2 > 0.f ? a2 * rs : 0.f;
-          const float d = mag * inv_sqrt_n - a;
-          part += d * d;
-          const float f = a * rs;
-          const float2 u = a2 > 0.f ? make_float2(vx * f, vy * f) : make_float2(a, 0.f);
-          res[x] = u;
-          if (last) po[x] = gen_phase(u);
+        for (int x0 = lane; x0 < nx; x0 += 32 * 8) {
+          float a[8];
+#pragma unroll
+          for (int k = 0; k < 8; ++k) a[k] = (pp && x0 + 32 * k < nx) ? pp[x0 + 32 * k] : 1.f;
+          float2 t8[8];
+#pragma unroll
+          for (int k = 0; k < 8; ++k) t8[k] = (x0 + 32 * k < nx) ? res[x0 + 32 * k] : make_float2(1.f, 0.f);
+#pragma unroll
+          for (int k = 0; k < 8; ++k) {
+            const int x = x0 + 32 * k;
+            if (x < nx) {
+              const float2 t = t8[k];
+              const float vx = t.y, vy = t.x;
+              const float a2 = vx * vx + vy * vy;
+              const float rs = rsqrtf(a2);
+              const float mag = a2 > 0.f ? a2 * rs : 0.f;
+              const float d = mag * inv_sqrt_n - a[k];
+              part += d * d;
+              const float f = a[k] * rs;
+              res[x] = a2 > 0.f ? make_float2(vx * f, vy * f) : make_float2(a[k], 0.f);
+            }
+          }
         }
         acc += static_cast<double>(part);
         __syncwarp();
+        if (last) {
+          float* po = p.phi_out + moff + static_cast<size_t>(row) * nx;
+          for (int x = lane; x < nx; x += 32) po[x] = gen_phase(res[x]);
+        }
         if (two) res = gen_fft(res, res == A ? Bf : A, nx, p.planx, p.nstx, twx);
       }
       if (kind == kInit || two)
@@ -228,12 +295,18 @@ static __device__ __noinline__ double run_pass_gen(const Params& p, int mb, int 
     const int c0 = cg << 3;
     const int wc = min(8, nx - c0);
     __syncthreads();  // the previous group's tile has been written back
-    for (int e = threadIdx.x; e < ny * 8; e += kThreads) {
-      const int y = e >> 3, k = e & 7;
-      if (k < wc)
-        wbase[k * stride + y] = (kind == kInitM)
-                                    ? make_float2(0.f, mTm[static_cast<size_t>(c0 + k) * ny + y])  // swap((m, 0))
-                                    : Bm[static_cast<size_t>(y) * nx + c0 + k];
+    {
+      const int k = threadIdx.x & 7;  // column of this thread in every round
+      if (k < wc) {
+        if (kind == kInitM) {
+          for (int y = threadIdx.x >> 3; y < ny; y += kThreads / 8)  // swap((m, 0))
+            wbase[k * stride + y] = make_float2(0.f, mTm[static_cast<size_t>(c0 + k) * ny + y]);
+        } else {
+          for (int y = threadIdx.x >> 3; y < ny; y += kThreads / 8)
+            cp_async8(wbase + k * stride + y, Bm + static_cast<size_t>(y) * nx + c0 + k);
+          cp_async_wait_all();
+        }
+      }
     }
     __syncthreads();
     if (w < wc) {
@@ -242,18 +315,30 @@ static __device__ __noinline__ double run_pass_gen(const Params& p, int mb, int 
         // res = Y = F u^nu along this column: residual and Eq. (e:Mhat)
         const float* mcol = mTm + static_cast<size_t>(c0 + w) * ny;
         float part = 0.f;
-        for (int y = lane; y < ny; y += 32) {
-          const float m = mcol[y];
-          const float2 Y = res[y];
-          const float a2 = Y.x * Y.x + Y.y * Y.y;
-          const float rs = rsqrtf(a2);
-          const float mag = a2 > 0.f ? a2 * rs : 0.f;
-          const float d = mag * inv_sqrt_n - m;
-          part += d * d;
-          if (kind == kCol) {
-            const float f = m * rs;
-            const float2 Yh = a2 > 0.f ? make_float2(Y.x * f, Y.y * f) : make_float2(m, 0.f);
-            res[y] = make_float2(Yh.y, Yh.x);  // swapped: the next forward DFT acts as the inverse
+        for (int y0 = lane; y0 < ny; y0 += 32 * 8) {
+          float mv[8];
+          float2 yv[8];
+#pragma unroll
+          for (int u = 0; u < 8; ++u) mv[u] = (y0 + 32 * u < ny) ? mcol[y0 + 32 * u] : 0.f;
+#pragma unroll
+          for (int u = 0; u < 8; ++u) yv[u] = (y0 + 32 * u < ny) ? res[y0 + 32 * u] : make_float2(1.f, 0.f);
+#pragma unroll
+          for (int u = 0; u < 8; ++u) {
+            const int y = y0 + 32 * u;
+            if (y < ny) {
+              const float m = mv[u];
+              const float2 Y = yv[u];
+              const float a2 = Y.x * Y.x + Y.y * Y.y;
+              const float rs = rsqrtf(a2);
+              const float mag = a2 > 0.f ? a2 * rs : 0.f;
+              const float d = mag * inv_sqrt_n - m;
+              part += d * d;
+              if (kind == kCol) {
+                const float f = m * rs;
+                const float2 Yh = a2 > 0.f ? make_float2(Y.x * f, Y.y * f) : make_float2(m, 0.f);
+                res[y] = make_float2(Yh.y, Yh.x);  // swapped: the next forward DFT acts as the inverse
+              }
+            }
           }
         }
         acc += static_cast<double>(part);
