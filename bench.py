@@ -382,6 +382,111 @@ def run_gpu(args):
                           "loss_first": float(losses[0]), "loss_last": float(losses[-1])}
         lc.close()
 
+    def timed(fn, steps):
+        """Mean device ms of fn() over `steps` launches, L2 flushed before each."""
+        fn()
+        torch.cuda.synchronize(dev)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        for a_, b_ in ev:
+            flush.zero_()
+            a_.record(stream)
+            fn()
+            b_.record(stream)
+        torch.cuda.synchronize(dev)
+        return statistics.mean(a_.elapsed_time(b_) for a_, b_ in ev)
+
+    # tensor-core form (FP16 DFT-matrix products, FP32 accumulation) on the
+    # same workload: time per mask and the final residual against the FP32 one
+    tensor_core = None
+    if args.tc_steps > 0 and ws == 1:
+        gst = GerchbergSaxton(nx, ny, final_residual=True, stream=stream, tensor_core=True)
+        out_t = torch.empty_like(phi0)
+        res_t = {}
+
+        def tc_step():
+            res_t["r"] = gst.run(I, phi0, iters, phase_out=out_t)[1]
+
+        ms_t = timed(tc_step, args.tc_steps)
+        if gst.status() != 0:
+            raise RuntimeError("tensor-core run failed")
+        r_t = float(res_t["r"][-1].item())
+        tensor_core = {"ms_per_mask": round(ms_t, 4), "fp32_ms_per_mask": round(mean_ms, 4),
+                       "speedup_vs_fp32": round(mean_ms / ms_t, 4), "final_residual": r_t,
+                       "final_residual_rel_diff_vs_fp32": round(abs(r_t - r_final) / r_final, 6),
+                       "matched_within_2pct": abs(r_t - r_final) <= 0.02 * r_final, "steps": args.tc_steps}
+        gst.close()
+
+    # the paper's own timing experiment (Sec. V): an 800 x 600 SLM, 25
+    # iterations in single precision from the start P_S(F^-1 m), reported
+    # there as 45 ms on a Tesla C2070 including a 1 ms target upload; here on
+    # the device and through gs_run_host (target upload and phase download
+    # inside the timed region)
+    paper_800x600 = None
+    if args.paper_steps > 0 and ws == 1:
+        from paper_1302_0120_gb300 import _binding as B8
+
+        I8 = S.spot_target(800 + rank, 600, 800, 50, (0.5, 1.0))
+        gsp = GerchbergSaxton(800, 600, final_residual=False, stream=stream, init_from_target=True)
+        I8d = torch.from_numpy(I8).to(dev)
+        o8 = torch.empty_like(I8d)
+        ms_p = timed(lambda: gsp.run(I8d, None, 25, phase_out=o8, residuals=False, object_gap=False), args.paper_steps)
+        pin8 = torch.from_numpy(I8).pin_memory()
+        pout8 = torch.empty_like(pin8).pin_memory()
+        host_ms = []
+        for k in range(args.paper_steps + 2):
+            flush.zero_()
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            rc = B8.gs_run_host(gsp.handle, pin8.data_ptr(), 0, 25, pout8.data_ptr(), 0, 0)
+            if rc != 0:
+                raise RuntimeError(f"gs_run_host 800x600: {B8.gs_strerror(rc)}")
+            if k >= 2:
+                host_ms.append(1e3 * (time.perf_counter() - t0))
+        if gsp.status() != 0:
+            raise RuntimeError("800x600 run failed")
+        paper_800x600 = {"iters": 25, "init": "target (P_S F^-1 m)", "device_ms": round(ms_p, 4),
+                         "e2e_ms": round(statistics.mean(host_ms), 4), "paper_ms_c2070": 45.0,
+                         "speedup_vs_paper_e2e": round(45.0 / statistics.mean(host_ms), 1), "grid_ctas": gsp.grid}
+        gsp.close()
+
+    # 64 masks of mixed size (256^2, 512^2, 1024^2 by seed, 10..200 spots), 50
+    # iterations, one batched launch per size: FP32 and tensor-core forms
+    mixed64 = None
+    if args.mixed_steps > 0 and ws == 1:
+        masks = S.mixed_batch(rank + 4)
+        groups = {}
+        for k, (Im, Pm) in enumerate(masks):
+            groups.setdefault(Im.shape[0], []).append(k)
+        mixed64 = {"masks": len(masks), "iters": 50, "sizes": {str(k_): len(v_) for k_, v_ in sorted(groups.items())}}
+        rfin = {}
+        for tc in (False, True):
+            ctxs = []
+            for n_, ks in sorted(groups.items()):
+                Ig = torch.from_numpy(np.stack([masks[k][0] for k in ks])).to(dev)
+                Pg = torch.from_numpy(np.stack([masks[k][1] for k in ks])).to(dev)
+                ctxs.append((GerchbergSaxton(n_, n_, final_residual=True, stream=stream, max_batch=len(ks),
+                                             tensor_core=tc), Ig, Pg, torch.empty_like(Pg), ks))
+            keep = {}
+
+            def mixed_step():
+                for c_, Ig, Pg, Og, ks in ctxs:
+                    keep[id(c_)] = (c_.run_batched(Ig, Pg, 50, phase_out=Og)[1], ks)
+
+            ms_m = timed(mixed_step, args.mixed_steps)
+            for c_, *_ in ctxs:
+                if c_.status() != 0:
+                    raise RuntimeError("mixed batch failed")
+            for rr, ks in keep.values():
+                rr = rr.cpu().numpy()
+                for j, k in enumerate(ks):
+                    rfin[(tc, k)] = float(rr[j][-1])
+            for c_, *_ in ctxs:
+                c_.close()
+            mixed64["tensor_core_ms" if tc else "fp32_ms"] = round(ms_m, 4)
+            mixed64["tensor_core_ms_per_mask" if tc else "fp32_ms_per_mask"] = round(ms_m / len(masks), 4)
+        mixed64["worst_final_residual_rel_diff_tc_vs_fp32"] = round(
+            max(abs(rfin[(True, k)] - rfin[(False, k)]) / rfin[(False, k)] for k in range(len(masks))), 6)
+
     # end to end through the public host-pointer call (gs_run_host)
     pin_I = torch.from_numpy(I_np).pin_memory()
     pin_phi = torch.from_numpy(phi_np).pin_memory()
@@ -464,6 +569,9 @@ def run_gpu(args):
         "batched_throughput": batched,
         "serving": serving,
         "differentiable": differentiable,
+        "tensor_core": tensor_core,
+        "paper_800x600": paper_800x600,
+        "mixed64": mixed64,
         "wall_s": round(wall, 3),
     }
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -489,6 +597,9 @@ def main(argv=None):
     ap.add_argument("--serve-seconds", type=float, default=2.0, help="length of the serving stream (0: skip)")
     ap.add_argument("--serve-rate", type=float, default=1000.0, help="request rate of the serving stream (Hz)")
     ap.add_argument("--adam-steps", type=int, default=200, help="Adam steps of the differentiable-form field (0: skip)")
+    ap.add_argument("--tc-steps", type=int, default=20, help="timed runs of the tensor-core field (0: skip)")
+    ap.add_argument("--paper-steps", type=int, default=20, help="timed runs of the 800x600 field (0: skip)")
+    ap.add_argument("--mixed-steps", type=int, default=5, help="timed runs of the 64-mask mixed batch (0: skip)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget-s", type=float, default=12.0)
     ap.add_argument("--ref-sample-iters", type=int, default=2)
