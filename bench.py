@@ -450,38 +450,36 @@ def run_gpu(args):
         gsp.close()
 
     # 64 masks of mixed size (256^2, 512^2, 1024^2 by seed, 10..200 spots), 50
-    # iterations, one batched launch per size: FP32 and tensor-core forms
+    # iterations in one persistent launch (gs_run_mixed): FP32 and tensor-core forms
     mixed64 = None
     if args.mixed_steps > 0 and ws == 1:
+        from paper_1302_0120_gb300 import MixedGerchbergSaxton
+
         masks = S.mixed_batch(rank + 4)
         groups = {}
         for k, (Im, Pm) in enumerate(masks):
             groups.setdefault(Im.shape[0], []).append(k)
-        mixed64 = {"masks": len(masks), "iters": 50, "sizes": {str(k_): len(v_) for k_, v_ in sorted(groups.items())}}
+        Tm = {n_: torch.from_numpy(np.stack([masks[k][0] for k in ks])).to(dev) for n_, ks in groups.items()}
+        Pm_ = {n_: torch.from_numpy(np.stack([masks[k][1] for k in ks])).to(dev) for n_, ks in groups.items()}
+        mixed64 = {"masks": len(masks), "iters": 50, "launches_per_run": 1,
+                   "sizes": {str(k_): len(v_) for k_, v_ in sorted(groups.items())}}
         rfin = {}
         for tc in (False, True):
-            ctxs = []
-            for n_, ks in sorted(groups.items()):
-                Ig = torch.from_numpy(np.stack([masks[k][0] for k in ks])).to(dev)
-                Pg = torch.from_numpy(np.stack([masks[k][1] for k in ks])).to(dev)
-                ctxs.append((GerchbergSaxton(n_, n_, final_residual=True, stream=stream, max_batch=len(ks),
-                                             tensor_core=tc), Ig, Pg, torch.empty_like(Pg), ks))
+            gm = MixedGerchbergSaxton({n_: len(ks) for n_, ks in groups.items()}, stream=stream, tensor_core=tc)
             keep = {}
 
             def mixed_step():
-                for c_, Ig, Pg, Og, ks in ctxs:
-                    keep[id(c_)] = (c_.run_batched(Ig, Pg, 50, phase_out=Og)[1], ks)
+                keep["out"] = gm.run(Tm, Pm_, 50)
 
             ms_m = timed(mixed_step, args.mixed_steps)
-            for c_, *_ in ctxs:
-                if c_.status() != 0:
-                    raise RuntimeError("mixed batch failed")
-            for rr, ks in keep.values():
-                rr = rr.cpu().numpy()
+            if gm.status() != 0:
+                raise RuntimeError("mixed batch failed")
+            for n_, ks in groups.items():
+                rr = keep["out"][n_][1].cpu().numpy()
                 for j, k in enumerate(ks):
                     rfin[(tc, k)] = float(rr[j][-1])
-            for c_, *_ in ctxs:
-                c_.close()
+            mixed64["grid_ctas"] = gm.grid
+            gm.close()
             mixed64["tensor_core_ms" if tc else "fp32_ms"] = round(ms_m, 4)
             mixed64["tensor_core_ms_per_mask" if tc else "fp32_ms_per_mask"] = round(ms_m / len(masks), 4)
         mixed64["worst_final_residual_rel_diff_tc_vs_fp32"] = round(

@@ -155,6 +155,54 @@ int gs_run_batched(gs_ctx* c, int batch, const float* target_intensity, const fl
                    float* phase_out, double* residual_out, double* object_gap_out);
 
 /*
+ * gs_create_mixed -- a context for batches of square masks of three sizes,
+ * 256 x 256, 512 x 512 and 1024 x 1024, iterated together in one launch.
+ *
+ * Operation: none yet; sizes one workspace per size (as gs_create_batched
+ * for n = 256 << k with max_batch[k] masks) for gs_run_mixed, which runs
+ * Eq. (e:AP) on every mask of every size in one persistent launch.
+ *   out        host pointer that receives the context (NULL on failure).
+ *   max_batch  host int[3]: masks of size 256 << k, each 0..64, sum 1..64.
+ *   flags      GS_FINAL_RESIDUAL, GS_INIT_FROM_TARGET, GS_TENSOR_CORE.
+ *   stream     a cudaStream_t, or NULL for the legacy default stream.
+ * Only gs_run_mixed, gs_status, gs_set_grid, gs_get_grid and gs_destroy
+ * accept a mixed context; the single-size calls return GS_EINVAL.
+ * Returns GS_EINVAL for NULL pointers, a bad max_batch or an unknown flag;
+ * GS_ENOMEM, GS_ECUDA.
+ */
+int gs_create_mixed(gs_ctx** out, const int* max_batch, unsigned flags, void* stream);
+
+/*
+ * gs_run_mixed -- enqueue K iterations of Eq. (e:AP) for batch[k] masks of
+ * size n_k = 256 << k (k = 0, 1, 2) in one persistent launch (chunks of 128
+ * iterations, as gs_run).
+ *
+ * Every pass of the launch visits the masks of all three sizes before its
+ * grid barrier; each mask follows exactly the single-size path (same
+ * transforms, projections and gaps), so its phase is bit-identical to a
+ * gs_run_batched run of its size; its gaps can differ in the last bits
+ * because the FP64 partial sums are grouped by the launch's block count.
+ *   batch            host int[3], 0 <= batch[k] <= max_batch[k], sum >= 1.
+ *   target_intensity host array of 3 device pointers; entry k: float
+ *                    [batch[k]][n_k][n_k] (ignored when batch[k] = 0).
+ *   phase_in         host array of 3 device pointers as above, or NULL
+ *                    (whole array or entries) with GS_INIT_FROM_TARGET.
+ *   iters            K >= 0.
+ *   phase_out        host array of 3 device pointers, float
+ *                    [batch[k]][n_k][n_k], may alias phase_in.
+ *   residual_out     NULL or host array of 3 device pointers (entries may be
+ *                    NULL): double [batch[k]][K (+1 with GS_FINAL_RESIDUAL)].
+ *   object_gap_out   NULL or host array of 3 device pointers: double
+ *                    [batch[k]][K].
+ * Asynchronous on the context's stream; errors found on the device
+ * (GS_ENUMERIC per mask, GS_ETIMEOUT) are reported by gs_status. Returns
+ * GS_EINVAL for a NULL or non-mixed context, a bad batch, missing pointers or
+ * K < 0; GS_ECUDA if a launch fails.
+ */
+int gs_run_mixed(gs_ctx* c, const int* batch, const float* const* target_intensity, const float* const* phase_in,
+                 int iters, float* const* phase_out, double* const* residual_out, double* const* object_gap_out);
+
+/*
  * gs_run_host -- gs_run on HOST buffers: end-to-end call including transfers.
  *
  * Same operation and argument meaning as gs_run, but every array is host

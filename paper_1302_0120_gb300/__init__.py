@@ -18,10 +18,12 @@ from ._binding import (  # noqa: F401
     GSError,
     gs_create,
     gs_create_batched,
+    gs_create_mixed,
     gs_destroy,
     gs_get_grid,
     gs_run,
     gs_run_batched,
+    gs_run_mixed,
     gs_run_host,
     gs_set_grid,
     gs_set_slm_amplitude,
@@ -30,4 +32,4 @@ from ._binding import (  # noqa: F401
     gs_workspace_bytes,
     gs_workspace_bytes_batched,
 )
-from .solver import GerchbergSaxton  # noqa: F401
+from .solver import GerchbergSaxton, MixedGerchbergSaxton  # noqa: F401

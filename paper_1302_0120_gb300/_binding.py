@@ -46,6 +46,8 @@ SIGNATURES = {
     "gs_set_slm_amplitude": (_c_int, [_vp, _vp]),
     "gs_test_barrier_timeout": (_c_int, [_vp, _c_int]),
     "gs_physical_error": (_c_int, [_vp, _vp, _vp, _vp]),
+    "gs_create_mixed": (_c_int, [ctypes.POINTER(_vp), _vp, _c_uint, _vp]),
+    "gs_run_mixed": (_c_int, [_vp, _vp, _vp, _vp, _c_int, _vp, _vp, _vp]),
 }
 
 _lib = None
@@ -102,6 +104,40 @@ def gs_run_batched(ctx: int, batch: int, target_intensity: int, phase_in: int, i
     """Enqueue a run of `batch` strided masks on device pointers; returns the status code."""
     return lib().gs_run_batched(_vp(ctx), int(batch), _vp(target_intensity), _vp(phase_in), int(iters),
                                 _vp(phase_out), _vp(residual_out or 0), _vp(object_gap_out or 0))
+
+
+def _arr3(ctype, vals):
+    return (ctype * 3)(*vals)
+
+
+def gs_create_mixed(max_batch, flags: int = GS_FINAL_RESIDUAL, stream: int | None = None) -> int:
+    """Create a context for masks of size 256, 512 and 1024 (max_batch per
+    size, a sequence of 3 ints) run together; returns its handle. Raises GSError."""
+    h = _vp()
+    mb = _arr3(_c_int, [int(x) for x in max_batch])
+    rc = lib().gs_create_mixed(ctypes.byref(h), ctypes.cast(mb, _vp), int(flags), _vp(stream or 0))
+    if rc != GS_OK:
+        raise GSError(rc, "gs_create_mixed")
+    return h.value
+
+
+def gs_run_mixed(ctx: int, batch, target_intensity, phase_in, iters: int, phase_out, residual_out=None,
+                 object_gap_out=None) -> int:
+    """Enqueue one launch over three size classes. ``batch`` is 3 ints; the
+    array arguments are sequences of 3 device pointers (0 for unused entries)
+    or None where the header allows NULL; returns the status code."""
+    keep = []
+
+    def ptrs(v):
+        if v is None:
+            return None
+        a = _arr3(_vp, [int(x or 0) or None for x in v])
+        keep.append(a)
+        return ctypes.cast(a, _vp)
+
+    b = _arr3(_c_int, [int(x) for x in batch])
+    return lib().gs_run_mixed(_vp(ctx), ctypes.cast(b, _vp), ptrs(target_intensity), ptrs(phase_in), int(iters),
+                              ptrs(phase_out), ptrs(residual_out), ptrs(object_gap_out))
 
 
 def gs_create(nx: int, ny: int, flags: int = GS_FINAL_RESIDUAL, stream: int | None = None) -> int:

@@ -163,6 +163,12 @@ struct gs_ctx {
   unsigned char* ws = nullptr;
   double* dres = nullptr;  // device residual staging for gs_run_host
   size_t dres_cap = 0;     // doubles
+  // gs_create_mixed: one workspace per size class n = 256 << k (max_batch > 0),
+  // at byte offset mbase[k]; L above is the first such class, at offset 0.
+  bool mixed = false;
+  int mixed_max[3] = {0, 0, 0};
+  Layout Lm[3]{};
+  size_t mbase[3] = {0, 0, 0};
 };
 
 namespace {
@@ -178,7 +184,7 @@ int max_grid(const gs_ctx* c) {
   return m < 1 ? 1 : m;
 }
 
-int choose_grid(const gs_ctx* c) {
+int choose_grid_for(const gs_ctx* c, long long pixels) {
   const int cap = max_grid(c);
   int g;
   if (c->grid_override > 0) {
@@ -188,7 +194,7 @@ int choose_grid(const gs_ctx* c) {
     // 2048 pixels): there the passes are latency-bound and more blocks
     // shorten each block's share (measured on 256 x 256: 1.61 -> 1.34 ms per
     // 100 iterations)
-    const long long n = static_cast<long long>(c->nx) * c->ny;
+    const long long n = pixels;
     g = static_cast<int>(n / 4096);
     const int small = static_cast<int>(n / 2048 < 32 ? n / 2048 : 32);
     if (g < small) g = small;
@@ -197,6 +203,8 @@ int choose_grid(const gs_ctx* c) {
   if (g < 1) g = 1;
   return g;
 }
+
+int choose_grid(const gs_ctx* c) { return choose_grid_for(c, static_cast<long long>(c->nx) * c->ny); }
 
 }  // namespace
 
@@ -280,7 +288,7 @@ int gs_run(gs_ctx* c, const float* target_intensity, const float* phase_in, int 
 int gs_run_batched(gs_ctx* c, int batch, const float* target_intensity, const float* phase_in, int iters,
                    float* phase_out, double* residual_out, double* object_gap_out) {
   const bool from_target = (c != nullptr) && (c->flags & GS_INIT_FROM_TARGET);
-  if (c == nullptr || target_intensity == nullptr || (phase_in == nullptr && !from_target) ||
+  if (c == nullptr || c->mixed || target_intensity == nullptr || (phase_in == nullptr && !from_target) ||
       phase_out == nullptr || iters < 0 || batch < 1 || batch > c->max_batch)
     return GS_EINVAL;
   const int grid = choose_grid(c);
@@ -342,6 +350,155 @@ int gs_run_batched(gs_ctx* c, int batch, const float* target_intensity, const fl
   return GS_OK;
 }
 
+int gs_create_mixed(gs_ctx** out, const int* max_batch, unsigned flags, void* stream) {
+  if (out == nullptr) return GS_EINVAL;
+  *out = nullptr;
+  if (max_batch == nullptr) return GS_EINVAL;
+  int total = 0;
+  for (int k = 0; k < 3; ++k) {
+    if (max_batch[k] < 0 || max_batch[k] > gsk::kMaxBatch) return GS_EINVAL;
+    total += max_batch[k];
+  }
+  if (total < 1 || total > gsk::kMaxBatch) return GS_EINVAL;
+  if ((flags & ~static_cast<unsigned>(GS_FINAL_RESIDUAL | GS_INIT_FROM_TARGET | GS_TENSOR_CORE)) != 0)
+    return GS_EINVAL;
+  const bool tc = (flags & GS_TENSOR_CORE) != 0;
+  gs_ctx* c = new (std::nothrow) gs_ctx();
+  if (c == nullptr) return GS_ENOMEM;
+  c->mixed = true;
+  c->flags = flags;
+  c->stream = static_cast<cudaStream_t>(stream);
+  size_t off = 0;
+  int primary = -1;
+  for (int k = 0; k < 3; ++k) {
+    c->mixed_max[k] = max_batch[k];
+    if (max_batch[k] == 0) continue;
+    const int n = 256 << k;
+    if (primary < 0) primary = k;
+    c->Lm[k] = make_layout(n, n, max_batch[k]);
+    c->mbase[k] = off;
+    off += c->Lm[k].total;
+  }
+  c->L = c->Lm[primary];
+  c->nx = c->ny = 256 << primary;
+  c->max_batch = total;
+  if (cudaGetDevice(&c->device) != cudaSuccess ||
+      cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess ||
+      gsk::mixed_occupancy(tc, &c->blocks_per_sm) != cudaSuccess || c->blocks_per_sm < 1) {
+    cudaGetLastError();
+    delete c;
+    return GS_ECUDA;
+  }
+  if (cudaMalloc(&c->ws, off) != cudaSuccess) {
+    cudaGetLastError();
+    delete c;
+    return GS_ENOMEM;
+  }
+  bool ok = true;
+  for (int k = 0; k < 3 && ok; ++k) {
+    if (max_batch[k] == 0) continue;
+    const Layout& L = c->Lm[k];
+    unsigned char* w = c->ws + c->mbase[k];
+    const std::vector<float2> tw = twiddles(256 << k, false);
+    ok = cudaMemcpy(w + L.twx, tw.data(), tw.size() * sizeof(float2), cudaMemcpyHostToDevice) == cudaSuccess &&
+         cudaMemcpy(w + L.twy, tw.data(), tw.size() * sizeof(float2), cudaMemcpyHostToDevice) == cudaSuccess &&
+         cudaMemset(w + L.bar, 0, L.dI - L.bar) == cudaSuccess;
+  }
+  if (!ok) {
+    cudaGetLastError();
+    cudaFree(c->ws);
+    delete c;
+    return GS_ECUDA;
+  }
+  *out = c;
+  return GS_OK;
+}
+
+int gs_run_mixed(gs_ctx* c, const int* batch, const float* const* target_intensity, const float* const* phase_in,
+                 int iters, float* const* phase_out, double* const* residual_out, double* const* object_gap_out) {
+  if (c == nullptr || !c->mixed || batch == nullptr || target_intensity == nullptr || phase_out == nullptr ||
+      iters < 0)
+    return GS_EINVAL;
+  const bool from_target = (c->flags & GS_INIT_FROM_TARGET) != 0;
+  if (phase_in == nullptr && !from_target) return GS_EINVAL;
+  int total = 0;
+  for (int k = 0; k < 3; ++k) {
+    if (batch[k] < 0 || batch[k] > c->mixed_max[k]) return GS_EINVAL;
+    if (batch[k] > 0 && (target_intensity[k] == nullptr || phase_out[k] == nullptr ||
+                         (!from_target && phase_in[k] == nullptr)))
+      return GS_EINVAL;
+    total += batch[k];
+  }
+  if (total < 1) return GS_EINVAL;
+  int largest = 0;
+  for (int k = 0; k < 3; ++k)
+    if (batch[k] > 0) largest = k;
+  const long long px = static_cast<long long>(256 << largest) * (256 << largest);
+  const int grid = choose_grid_for(c, px);  // the single-size rule for the largest class present
+  const Layout& P = c->L;  // the primary class holds the barrier, status and abort words
+  unsigned char* const pw = c->ws;
+  gsk::MixedParams mp{};
+  for (int k = 0; k < 3; ++k) {
+    gsk::Params& p = mp.cls[k];
+    const int n = 256 << k;
+    p.nx = p.ny = n;
+    p.lognx = p.logny = 8 + k;
+    p.batch = batch[k];
+    p.mstride = static_cast<long long>(n) * n;
+    p.rstride = iters + ((c->flags & GS_FINAL_RESIDUAL) ? 1 : 0);
+    p.gstride = iters;
+    p.iters = iters;
+    p.final_resid = (c->flags & GS_FINAL_RESIDUAL) ? 1 : 0;
+    p.init_target = from_target ? 1 : 0;
+    p.extra_arrivals = c->extra_arrivals;
+    p.tensor_core = (c->flags & GS_TENSOR_CORE) ? 1 : 0;
+    p.inv_sqrt_n = static_cast<float>(1.0 / n);
+    p.inv_n = 1.0 / (static_cast<double>(n) * n);
+    p.bar = reinterpret_cast<unsigned*>(pw + P.bar);
+    p.status = reinterpret_cast<int*>(pw + P.status);
+    p.abort_flag = reinterpret_cast<int*>(pw + P.abort_flag);
+    if (c->mixed_max[k] == 0) continue;
+    const Layout& L = c->Lm[k];
+    unsigned char* w = c->ws + c->mbase[k];
+    p.B = reinterpret_cast<float2*>(w + L.B);
+    p.mT = reinterpret_cast<float*>(w + L.mT);
+    p.partials = reinterpret_cast<double*>(w + L.partials);
+    p.twx = reinterpret_cast<const float2*>(w + L.twx);
+    p.twy = reinterpret_cast<const float2*>(w + L.twy);
+    p.ones = reinterpret_cast<const float*>(w + L.ones);
+    p.mask_flags = reinterpret_cast<int*>(w + L.mask_flags);
+    p.energy = reinterpret_cast<const double*>(w + L.energy);
+    if (batch[k] == 0) continue;
+    p.I = target_intensity[k];
+    p.phi_in = phase_in ? phase_in[k] : nullptr;
+    p.phi_out = phase_out[k];
+    p.r_out = residual_out ? residual_out[k] : nullptr;
+    p.g_out = object_gap_out ? object_gap_out[k] : nullptr;
+  }
+  if (cudaMemsetAsync(mp.cls[0].abort_flag, 0, sizeof(int), c->stream) != cudaSuccess) {
+    cudaGetLastError();
+    return GS_ECUDA;
+  }
+  int it0 = 0;
+  do {
+    int it1 = it0 + gsk::kMaxIterPerLaunch;
+    if (it1 > iters) it1 = iters;
+    for (int k = 0; k < 3; ++k) {
+      mp.cls[k].it0 = it0;
+      mp.cls[k].it1 = it1;
+      mp.cls[k].do_init = (it0 == 0) ? 1 : 0;
+      mp.cls[k].do_final = (it1 == iters) ? 1 : 0;
+    }
+    if (cudaMemsetAsync(mp.cls[0].bar, 0, sizeof(unsigned), c->stream) != cudaSuccess ||
+        gsk::launch_mixed(mp, grid, (c->flags & GS_TENSOR_CORE) != 0, c->stream) != cudaSuccess) {
+      cudaGetLastError();
+      return GS_ECUDA;
+    }
+    it0 = it1;
+  } while (it0 < iters);
+  return GS_OK;
+}
+
 int gs_status(gs_ctx* c) {
   if (c == nullptr) return GS_EINVAL;
   if (cudaStreamSynchronize(c->stream) != cudaSuccess) {
@@ -362,8 +519,8 @@ int gs_status(gs_ctx* c) {
 int gs_run_host(gs_ctx* c, const float* target_intensity, const float* phase_in, int iters, float* phase_out,
                 double* residual_out, double* object_gap_out) {
   const bool from_target = (c != nullptr) && (c->flags & GS_INIT_FROM_TARGET);
-  if (c == nullptr || target_intensity == nullptr || (phase_in == nullptr && !from_target) || phase_out == nullptr ||
-      iters < 0)
+  if (c == nullptr || c->mixed || target_intensity == nullptr || (phase_in == nullptr && !from_target) ||
+      phase_out == nullptr || iters < 0)
     return GS_EINVAL;
   const size_t n = static_cast<size_t>(c->nx) * c->ny;
   const size_t nres = static_cast<size_t>(iters) + 1;
@@ -438,21 +595,21 @@ int enqueue_loss(gs_ctx* c, const float* target_intensity, const float* phase, d
 }  // namespace
 
 int gs_loss_grad(gs_ctx* c, const float* target_intensity, const float* phase, double* loss_out, float* grad_out) {
-  if (c == nullptr || target_intensity == nullptr || phase == nullptr || loss_out == nullptr || c->nx != c->ny ||
-      !is_pow2(c->nx))
+  if (c == nullptr || c->mixed || target_intensity == nullptr || phase == nullptr || loss_out == nullptr ||
+      c->nx != c->ny || !is_pow2(c->nx))
     return GS_EINVAL;
   return enqueue_loss(c, target_intensity, phase, loss_out, grad_out, nullptr);
 }
 
 int gs_physical_error(gs_ctx* c, const float* target_intensity, const float* phase, double* error_out) {
-  if (c == nullptr || target_intensity == nullptr || phase == nullptr || error_out == nullptr || c->nx != c->ny ||
-      !is_pow2(c->nx))
+  if (c == nullptr || c->mixed || target_intensity == nullptr || phase == nullptr || error_out == nullptr ||
+      c->nx != c->ny || !is_pow2(c->nx))
     return GS_EINVAL;
   return enqueue_loss(c, target_intensity, phase, at<double>(c, c->L.lossbuf), nullptr, error_out);
 }
 
 int gs_set_slm_amplitude(gs_ctx* c, const float* amplitude) {
-  if (c == nullptr) return GS_EINVAL;
+  if (c == nullptr || c->mixed) return GS_EINVAL;
   c->p_slm = amplitude;
   if (amplitude != nullptr &&
       gsk::launch_energy(amplitude, static_cast<long long>(c->nx) * c->ny, at<double>(c, c->L.energy), c->stream) !=
@@ -478,6 +635,13 @@ int gs_set_grid(gs_ctx* c, int ctas) {
 
 int gs_get_grid(gs_ctx* c, int* ctas) {
   if (c == nullptr || ctas == nullptr) return GS_EINVAL;
+  if (c->mixed) {
+    int largest = 0;
+    for (int k = 0; k < 3; ++k)
+      if (c->mixed_max[k] > 0) largest = k;
+    *ctas = choose_grid_for(c, static_cast<long long>(256 << largest) * (256 << largest));
+    return GS_OK;
+  }
   *ctas = choose_grid(c);
   return GS_OK;
 }

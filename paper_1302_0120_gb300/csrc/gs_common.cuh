@@ -20,7 +20,7 @@ struct Shared {
   uint64_t mbar;  // completion of the amplitude bulk copy
   int flag;
   int pending;    // a bulk copy into shared memory may still be in flight
-  int m_block;    // column block whose amplitude is in shared memory (-1: none)
+  const float* m_block;  // global address of the amplitude block in shared memory (null: none)
   unsigned pending_phase;  // the mbarrier phase that copy completes
   double red[kThreads / 32];
   float scale[kMaxBatch];  // sqrt(N / sum I) per mask

@@ -58,6 +58,14 @@ struct Params {
   int nstx, nsty;
 };
 
+// Three size classes in one launch: square grids 256, 512 and 1024
+// (log2 n = 8 + c), any of them with an empty batch. Every class has the
+// same iteration count, flags and chunk; the barrier, status and abort words
+// are class 0's. Mask flags and partial sums are per class.
+struct MixedParams {
+  Params cls[3];
+};
+
 // Sides of the general kernel: 5-smooth (2^a 3^b 5^c) in [32, kMaxGeneralSide].
 constexpr int kMaxGeneralSide = 1536;
 constexpr int kMaxGeneralStages = 10;
@@ -80,6 +88,11 @@ const void* iterate_kernel_lx(int ly);
 const void* iterate_kernel_tc(int l);
 // Kernel for grids with a side that is not a power of two (gs_general_inst.cu).
 const void* iterate_kernel_general();
+// Kernel for three square size classes in one launch (gs_mixed_inst.cu).
+const void* iterate_kernel_mixed(bool tc);
+size_t mixed_smem_bytes(bool tensor_core);
+cudaError_t mixed_occupancy(bool tensor_core, int* blocks_per_sm);
+cudaError_t launch_mixed(const MixedParams& mp, int grid, bool tensor_core, cudaStream_t s);
 
 size_t iteration_smem_bytes(int nx, int ny, bool tensor_core = false);
 

@@ -128,7 +128,7 @@ __device__ __forceinline__ double run_pass(const Params& p, int mb, int kind, bo
   // tensor cores through the warp's slice of the exchange buffers.
   auto fft = [&](float2(&x)[32]) {
     if constexpr (TCF::kEnabled) {
-      tcf.run(x, smem + (threadIdx.x >> 5) * kTcWarpBytes, reinterpret_cast<const float2*>(smem + kTcTwOffset));
+      tcf.run(x, smem + (threadIdx.x >> 5) * kTcWarpBytes);
     } else {
       group_fft<LOGN>(x, grp, stw);
     }
@@ -260,15 +260,17 @@ __device__ __forceinline__ double run_pass(const Params& p, int mb, int kind, bo
     if (threadIdx.x == 0) {
       bulk_wait_read_all();  // a previous bulk store has read blk
       fence_proxy_async_smem();
-      const int mkey = mb * L::NBLK + cb;  // which mask's amplitude block is resident
-      const bool need_m = (sh.m_block != mkey);
+      // the amplitude block is identified by its global address, unique
+      // across masks and size classes
+      const float* const msrc = mTm + static_cast<size_t>(cb) * L::BLOCK;
+      const bool need_m = (sh.m_block != msrc);
       const unsigned bytes_b = from_m ? 0u : L::BLOCK * 8u;
       const unsigned bytes_m = L::BLOCK * 4u;
       mbar_arrive_expect_tx(&sh.mbar, bytes_b + (need_m ? bytes_m : 0u));
       if (!from_m) bulk_g2s(blk, Bm + static_cast<size_t>(cb) * L::BLOCK, bytes_b, &sh.mbar);
       // columns cb W .. cb W + W - 1 of m are contiguous in the transposed amplitude
       if (need_m) bulk_g2s(ms, mTm + static_cast<size_t>(cb) * L::BLOCK, bytes_m, &sh.mbar);
-      sh.m_block = mkey;
+      sh.m_block = msrc;
       sh.pending = 1;
       sh.pending_phase = mphase;
     }
@@ -373,157 +375,164 @@ static __device__ void build_amplitude(const Params& p, int mb, float s, unsigne
   __syncthreads();
 }
 
-template <int LX, int LY, bool TC = false>
-__global__ void __launch_bounds__(kThreads, 1) gs_iterate(const Params p) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ Shared sh;
-  if (*reinterpret_cast<volatile int*>(p.abort_flag) != 0) return;  // an earlier chunk failed
+// ---------------------------------------------------------------------------
+// The kernels. A launch iterates one or more *size classes*: each class is a
+// Params (a batch of masks of one grid, with its own arrays and partial-sum
+// region); all classes share the barrier, status and abort words and pass
+// through the same schedule, one grid barrier per pass. Shared state of mask
+// mb of a class lives at index base + mb of the block's Shared arrays.
+
+// A0, part 1: this block's FP64 share of sum I for every mask of the class.
+// A non-finite or negative pixel poisons the sum with NaN.
+static __device__ __forceinline__ void a0_partials(const Params& p, Shared& sh) {
   const int G = gridDim.x;
   const int b = blockIdx.x;
-  unsigned target = 0;
-  unsigned mphase = 0;
-  StageTw<LX> tw_rows;  // square grids: stage twiddles held for the whole run
-  if constexpr (LX > 0 && LX == LY && !TC) tw_rows.load(p.twx, threadIdx.x & ((1 << (LX - 5)) - 1));
-  // Tensor-core transforms: the block's tables, then the DFT-matrix fragments
-  // held in registers for the whole run.
-  using TCF = typename std::conditional<TC, TcFft<LX>, NoTc>::type;
-  static_assert(!TC || LX == LY, "tensor-core kernels are square");
-  TCF tcf;
-  if constexpr (TC) {
-    tc_build_tables<LX>(reinterpret_cast<float2*>(smem + kTcTwOffset), reinterpret_cast<float2*>(smem + kTcCsOffset));
-    __syncthreads();
-    tcf.load(reinterpret_cast<const float2*>(smem + kTcCsOffset));
+  const int r0 = split(b, G, p.ny);
+  const int r1 = split(b + 1, G, p.ny);
+  const int cnt = (r1 - r0) * p.nx;
+  for (int mb = 0; mb < p.batch; ++mb) {
+    const float* I = p.I + static_cast<size_t>(mb) * static_cast<size_t>(p.mstride) + static_cast<size_t>(r0) * p.nx;
+    double acc = 0.0;
+    bool bad = false;
+    for (int e = threadIdx.x; e < cnt; e += kThreads) {
+      const float x = I[e];
+      bad |= !(x >= 0.f && x <= FLT_MAX);
+      acc += static_cast<double>(x);
+    }
+    if (__syncthreads_or(bad)) acc = __longlong_as_double(0x7ff8000000000000ll);
+    const double tot = block_sum(acc, sh);
+    if (threadIdx.x == 0) p.partials[static_cast<size_t>(mb) * G + b] = tot;
   }
-  if (threadIdx.x == 0) {
-    mbar_init(&sh.mbar, 1);
-    fence_barrier_init();
-    sh.pending = 0;
-    sh.m_block = -1;
-  }
-  __syncthreads();
-  if constexpr (LX == 0) gen_load_twiddles(p, smem);  // sides that are not powers of two
+}
 
-  if (p.do_init) {
-    // A0: FP64 energy of each mask's target over this block's rows. A
-    // non-finite or negative pixel poisons the sum with NaN.
-    const int r0 = split(b, G, p.ny);
-    const int r1 = split(b + 1, G, p.ny);
-    const int cnt = (r1 - r0) * p.nx;
+// A0, part 2 (after a grid barrier): validity and scale sqrt(sum p^2 / sum I)
+// of every mask, the same in every block (each reduces the same partials in
+// the same order). Rejected masks get NaN gaps and GS_ENUMERIC; they are
+// skipped from then on. With FP16 operands every transform input is below
+// sqrt(n sum p^2) (Cauchy-Schwarz on a row or column), which must stay in
+// the FP16 range. Returns the number of rejected masks.
+static __device__ __forceinline__ int a0_scales(const Params& p, Shared& sh, int base, bool tc) {
+  const int b = blockIdx.x;
+  if (threadIdx.x < 32) {
     for (int mb = 0; mb < p.batch; ++mb) {
-      const float* I = p.I + static_cast<size_t>(mb) * static_cast<size_t>(p.mstride) + static_cast<size_t>(r0) * p.nx;
-      double acc = 0.0;
-      bool bad = false;
-      for (int e = threadIdx.x; e < cnt; e += kThreads) {
-        const float x = I[e];
-        bad |= !(x >= 0.f && x <= FLT_MAX);
-        acc += static_cast<double>(x);
-      }
-      if (__syncthreads_or(bad)) acc = __longlong_as_double(0x7ff8000000000000ll);
-      const double tot = block_sum(acc, sh);
-      if (threadIdx.x == 0) p.partials[static_cast<size_t>(mb) * G + b] = tot;
-    }
-    if (!grid_sync(p, target, sh)) return;
-    // Every block reduces the same partials in the same order.
-    if (threadIdx.x < 32) {
-      for (int mb = 0; mb < p.batch; ++mb) {
-        const double total = warp_slot_sum(p, mb);
-        if (threadIdx.x == 0) {
-          const double ep = energy_of(p);
-          // FP16 operands: every transform input is below sqrt(n sum p^2)
-          // (Cauchy-Schwarz), which must stay below the FP16 range.
-          const bool range = !TC || (ep * static_cast<double>(p.nx) <= 2147483648.0);
-          const bool bad = !(total > 0.0) || !(total <= DBL_MAX) || !(ep > 0.0) || !(ep <= DBL_MAX) || !range;
-          sh.bad[mb] = bad ? 1 : 0;
-          if (b == 0) p.mask_flags[mb] = bad ? 1 : 0;  // for later launches of the run
-          sh.scale[mb] = bad ? 0.f : static_cast<float>(sqrt(energy_of(p) / total));
-        }
+      const double total = warp_slot_sum(p, mb);
+      if (threadIdx.x == 0) {
+        const double ep = energy_of(p);
+        const bool range = !tc || (ep * static_cast<double>(p.nx) <= 2147483648.0);
+        const bool bad = !(total > 0.0) || !(total <= DBL_MAX) || !(ep > 0.0) || !(ep <= DBL_MAX) || !range;
+        sh.bad[base + mb] = bad ? 1 : 0;
+        if (b == 0) p.mask_flags[mb] = bad ? 1 : 0;  // for later launches of the run
+        sh.scale[base + mb] = bad ? 0.f : static_cast<float>(sqrt(ep / total));
       }
     }
-    __syncthreads();
-    int nbad = 0;
-    for (int mb = 0; mb < p.batch; ++mb) nbad += sh.bad[mb];
-    if (nbad > 0) {
-      // Masks with an invalid target are skipped: phase untouched, gaps NaN.
-      if (b == 0) {
-        if (threadIdx.x == 0) fail_status(p, GS_ENUMERIC);
-        const double nan = __longlong_as_double(0x7ff8000000000000ll);
-        const int nr = p.iters + (p.final_resid ? 1 : 0);
-        for (int mb = 0; mb < p.batch; ++mb) {
-          if (!sh.bad[mb]) continue;
-          if (p.r_out)
-            for (int e = threadIdx.x; e < nr; e += kThreads) p.r_out[static_cast<size_t>(mb) * p.rstride + e] = nan;
-          if (p.g_out)
-            for (int e = threadIdx.x; e < p.iters; e += kThreads) p.g_out[static_cast<size_t>(mb) * p.gstride + e] = nan;
-        }
-      }
-      if (nbad == p.batch) {
-        if (b == 0 && threadIdx.x == 0) atomicExch(p.abort_flag, 1);  // later launches of the run
-        return;
-      }
-    }
-    for (int mb = 0; mb < p.batch; ++mb)
-      if (!sh.bad[mb]) {
-        if constexpr (LX == 0) gen_build_amplitude(p, mb, sh.scale[mb]);
-        else build_amplitude(p, mb, sh.scale[mb], smem);
-      }
-  } else if (threadIdx.x == 0) {
-    // later launches of a run: the invalid masks were flagged by the first
-    for (int mb = 0; mb < p.batch; ++mb) sh.bad[mb] = p.mask_flags[mb];
   }
   __syncthreads();
+  int nbad = 0;
+  for (int mb = 0; mb < p.batch; ++mb) nbad += sh.bad[base + mb];
+  if (nbad > 0 && b == 0) {
+    // Masks with an invalid target are skipped: phase untouched, gaps NaN.
+    if (threadIdx.x == 0) fail_status(p, GS_ENUMERIC);
+    const double nan = __longlong_as_double(0x7ff8000000000000ll);
+    const int nr = p.iters + (p.final_resid ? 1 : 0);
+    for (int mb = 0; mb < p.batch; ++mb) {
+      if (!sh.bad[base + mb]) continue;
+      if (p.r_out)
+        for (int e = threadIdx.x; e < nr; e += kThreads) p.r_out[static_cast<size_t>(mb) * p.rstride + e] = nan;
+      if (p.g_out)
+        for (int e = threadIdx.x; e < p.iters; e += kThreads) p.g_out[static_cast<size_t>(mb) * p.gstride + e] = nan;
+    }
+  }
+  return nbad;
+}
 
-  // Pass schedule: [init] (col, row) x nit [resid]. Pass q (after init) sums
-  // into partial rows (1 + q) * batch + mask.
+// Later launches of a run: the invalid masks were flagged by the first.
+static __device__ __forceinline__ void restore_flags(const Params& p, Shared& sh, int base) {
+  if (threadIdx.x == 0)
+    for (int mb = 0; mb < p.batch; ++mb) sh.bad[base + mb] = p.mask_flags[mb];
+}
+
+template <int LX>
+__device__ __forceinline__ void build_amplitudes(const Params& p, Shared& sh, int base, unsigned char* smem) {
+  for (int mb = 0; mb < p.batch; ++mb)
+    if (!sh.bad[base + mb]) {
+      if constexpr (LX == 0) gen_build_amplitude(p, mb, sh.scale[base + mb]);
+      else build_amplitude(p, mb, sh.scale[base + mb], smem);
+    }
+}
+
+// Pass q0 of the schedule [init] (col, row) x nit [resid]: its kind, whether
+// it ends the run, and the partial-sum slot of its gap (-1: none). Pass q
+// after the init passes sums into slot 1 + q.
+struct PassInfo {
+  int kind;
+  int slot;
+  bool last;
+};
+
+static __device__ __forceinline__ int pass_count(const Params& p) {
   const int nit = p.it1 - p.it0;
   const int resid = (p.do_final && p.final_resid) ? 1 : 0;
   const int ninit = p.do_init ? (p.init_target ? 2 : 1) : 0;  // target start: columns then rows
-  const int npass = ninit + 2 * nit + resid;
-  for (int q0 = 0; q0 < npass; ++q0) {
-    int kind;
-    int slot = -1;
-    bool last = false;
-    const int q = q0 - ninit;
-    if (q < 0) {
-      kind = !p.init_target ? kInit : (q == -2 ? kInitM : kRow);
-      last = p.do_final && p.iters == 0 && q == -1;
-    } else if (q < 2 * nit) {
-      kind = (q & 1) ? kRow : kCol;
-      slot = 1 + q;
-      last = (kind == kRow) && p.do_final && (p.it0 + (q >> 1) == p.iters - 1);
+  return ninit + 2 * nit + resid;
+}
+
+static __device__ __forceinline__ PassInfo pass_info(const Params& p, int q0) {
+  const int nit = p.it1 - p.it0;
+  const int ninit = p.do_init ? (p.init_target ? 2 : 1) : 0;
+  const int q = q0 - ninit;
+  PassInfo f{kCol, -1, false};
+  if (q < 0) {
+    f.kind = !p.init_target ? kInit : (q == -2 ? kInitM : kRow);
+    f.last = p.do_final && p.iters == 0 && q == -1;
+  } else if (q < 2 * nit) {
+    f.kind = (q & 1) ? kRow : kCol;
+    f.slot = 1 + q;
+    f.last = (f.kind == kRow) && p.do_final && (p.it0 + (q >> 1) == p.iters - 1);
+  } else {
+    f.kind = kResid;
+    f.slot = 1 + q;
+  }
+  return f;
+}
+
+// One pass over every valid mask of a class, with the FP64 block partial of
+// each mask's gap written to its slot.
+template <int LX, int LY, bool HOLD, class TCF>
+__device__ __forceinline__ void class_pass(const Params& p, Shared& sh, int base, const PassInfo& f,
+                                           unsigned char* smem, unsigned& mphase, const StageTw<LX>& tw_rows,
+                                           const TCF& tcf) {
+  for (int mb = 0; mb < p.batch; ++mb) {
+    if (sh.bad[base + mb]) continue;
+    double a;
+    if constexpr (LX == 0) {
+      a = run_pass_gen(p, mb, f.kind, f.last, smem);
+    } else if constexpr (LX == LY) {
+      a = run_pass<LX, LX, LY, HOLD>(p, mb, f.kind, f.last, smem, sh, mphase, tw_rows, tcf);
     } else {
-      kind = kResid;
-      slot = 1 + q;
+      const StageTw<LY> none{};
+      a = (f.kind == kInit || f.kind == kRow)
+              ? run_pass<LX, LX, LY, false>(p, mb, f.kind, f.last, smem, sh, mphase, tw_rows, tcf)
+              : run_pass<LY, LX, LY, false>(p, mb, f.kind, f.last, smem, sh, mphase, none, tcf);
     }
-    for (int mb = 0; mb < p.batch; ++mb) {
-      if (sh.bad[mb]) continue;
-      double a;
-      if constexpr (LX == 0) {
-        a = run_pass_gen(p, mb, kind, last, smem);
-      } else if constexpr (LX == LY) {
-        a = run_pass<LX, LX, LY, true>(p, mb, kind, last, smem, sh, mphase, tw_rows, tcf);
-      } else {
-        const StageTw<LY> none{};
-        a = (kind == kInit || kind == kRow) ? run_pass<LX, LX, LY, false>(p, mb, kind, last, smem, sh, mphase, tw_rows, tcf)
-                                            : run_pass<LY, LX, LY, false>(p, mb, kind, last, smem, sh, mphase, none, tcf);
-      }
-      if (slot >= 0) {
-        const double tot = block_sum(a, sh);
-        if (threadIdx.x == 0) p.partials[(static_cast<size_t>(slot) * p.batch + mb) * G + b] = tot;
-      }
-    }
-    if (!grid_sync(p, target, sh)) {
-      drain_copies(sh);
-      return;
+    if (f.slot >= 0) {
+      const double tot = block_sum(a, sh);
+      if (threadIdx.x == 0) p.partials[(static_cast<size_t>(f.slot) * p.batch + mb) * gridDim.x + blockIdx.x] = tot;
     }
   }
+}
 
-  // Gaps: r from column passes, g from row passes, in FP64.
+// Gaps: r from column passes, g from row passes, in FP64, for every valid
+// mask of a class (block b reduces slots b, b + G, ...).
+static __device__ __forceinline__ void final_gaps(const Params& p, Shared& sh, int base) {
+  const int G = gridDim.x;
+  const int nit = p.it1 - p.it0;
+  const int resid = (p.do_final && p.final_resid) ? 1 : 0;
   const int nslots = 2 * nit + resid;
   if (threadIdx.x < 32) {
-    for (int s = b; s < nslots * p.batch; s += G) {
+    for (int s = blockIdx.x; s < nslots * p.batch; s += G) {
       const int slot = 1 + s / p.batch;
       const int mb = s % p.batch;
-      if (sh.bad[mb]) continue;
+      if (sh.bad[base + mb]) continue;
       const double sum = warp_slot_sum(p, slot * p.batch + mb);
       if (threadIdx.x == 0) {
         const double val = sqrt(sum / energy_of(p));
@@ -541,6 +550,150 @@ __global__ void __launch_bounds__(kThreads, 1) gs_iterate(const Params p) {
       }
     }
   }
+}
+
+static __device__ __forceinline__ void block_setup(Shared& sh) {
+  if (threadIdx.x == 0) {
+    mbar_init(&sh.mbar, 1);
+    fence_barrier_init();
+    sh.pending = 0;
+    sh.m_block = nullptr;
+  }
+  __syncthreads();
+}
+
+// One size class per launch (every grid).
+template <int LX, int LY, bool TC = false>
+__global__ void __launch_bounds__(kThreads, 1) gs_iterate(const Params p) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ Shared sh;
+  if (*reinterpret_cast<volatile int*>(p.abort_flag) != 0) return;  // an earlier chunk failed
+  unsigned target = 0;
+  unsigned mphase = 0;
+  constexpr bool kHold = LX > 0 && LX == LY && !TC;
+  StageTw<LX> tw_rows;  // square grids: stage twiddles held for the whole run
+  if constexpr (kHold) tw_rows.load(p.twx, threadIdx.x & ((1 << (LX - 5)) - 1));
+  // Tensor-core transforms: the block's tables, then the DFT-matrix fragments
+  // held in registers for the whole run.
+  static_assert(!TC || LX == LY, "tensor-core kernels are square");
+  constexpr int kR = TC ? (1 << (LX > 5 ? LX - 5 : 0)) : 32;
+  TcStage1 s1;
+  TcStage2<kR> s2;
+  const float2* tctw = reinterpret_cast<const float2*>(smem + kTcTwOffset);
+  if constexpr (TC) {
+    tc_build_tables<LX>(reinterpret_cast<float2*>(smem + kTcTwOffset), reinterpret_cast<float2*>(smem + kTcCsOffset));
+    __syncthreads();
+    s1.load(reinterpret_cast<const float2*>(smem + kTcCsOffset));
+    s2.load(reinterpret_cast<const float2*>(smem + kTcCsOffset));
+  }
+  const auto tcf = [&]() {
+    if constexpr (TC) return TcFft<LX>{s1, s2, tctw};
+    else return NoTc{};
+  }();
+  block_setup(sh);
+  if constexpr (LX == 0) gen_load_twiddles(p, smem);  // sides that are not powers of two
+
+  if (p.do_init) {
+    a0_partials(p, sh);
+    if (!grid_sync(p, target, sh)) return;
+    const int nbad = a0_scales(p, sh, 0, TC);
+    if (nbad == p.batch) {
+      if (blockIdx.x == 0 && threadIdx.x == 0) atomicExch(p.abort_flag, 1);  // later launches of the run
+      return;
+    }
+    build_amplitudes<LX>(p, sh, 0, smem);
+  } else {
+    restore_flags(p, sh, 0);
+  }
+  __syncthreads();
+
+  const int npass = pass_count(p);
+  for (int q0 = 0; q0 < npass; ++q0) {
+    class_pass<LX, LY, kHold>(p, sh, 0, pass_info(p, q0), smem, mphase, tw_rows, tcf);
+    if (!grid_sync(p, target, sh)) {
+      drain_copies(sh);
+      return;
+    }
+  }
+  final_gaps(p, sh, 0);
+}
+
+template <int C, bool TC>
+__device__ __forceinline__ void mixed_class_pass(const MixedParams& mp, Shared& sh, const PassInfo& f,
+                                                 unsigned char* smem, unsigned& mphase, const TcStage1& s1,
+                                                 const TcStage2<8 << C>& s2) {
+  constexpr int L = 8 + C;
+  const Params& p = mp.cls[C];
+  if (p.batch == 0) return;
+  const int base = (C > 0 ? mp.cls[0].batch : 0) + (C > 1 ? mp.cls[1].batch : 0);
+  const StageTw<L> none{};
+  if constexpr (TC) {
+    const TcFft<L> tcf{s1, s2, reinterpret_cast<const float2*>(smem + kTcTwOffset + C * kTcTwBytes)};
+    class_pass<L, L, false>(p, sh, base, f, smem, mphase, none, tcf);
+  } else {
+    class_pass<L, L, false>(p, sh, base, f, smem, mphase, none, NoTc{});
+  }
+}
+
+template <bool TC>
+__global__ void __launch_bounds__(kThreads, 1) gs_iterate_mixed(const MixedParams mp) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ Shared sh;
+  const Params& p0 = mp.cls[0];  // barrier, status, abort flag, schedule
+  if (*reinterpret_cast<volatile int*>(p0.abort_flag) != 0) return;
+  unsigned target = 0;
+  unsigned mphase = 0;
+  TcStage1 s1;
+  TcStage2<8> s2a;
+  TcStage2<16> s2b;
+  TcStage2<32> s2c;
+  if constexpr (TC) {
+    float2* cs = reinterpret_cast<float2*>(smem + kTcTwOffset + 3 * kTcTwBytes);
+    tc_build_tables<8>(reinterpret_cast<float2*>(smem + kTcTwOffset), cs);
+    tc_build_tables<9>(reinterpret_cast<float2*>(smem + kTcTwOffset + kTcTwBytes), cs);
+    tc_build_tables<10>(reinterpret_cast<float2*>(smem + kTcTwOffset + 2 * kTcTwBytes), cs);
+    __syncthreads();
+    s1.load(cs);
+    s2a.load(cs);
+    s2b.load(cs);
+  }
+  block_setup(sh);
+  const int total = mp.cls[0].batch + mp.cls[1].batch + mp.cls[2].batch;
+  const int base1 = mp.cls[0].batch, base2 = base1 + mp.cls[1].batch;
+
+  if (p0.do_init) {
+    for (int c = 0; c < 3; ++c) a0_partials(mp.cls[c], sh);
+    if (!grid_sync(p0, target, sh)) return;
+    const int nbad = a0_scales(mp.cls[0], sh, 0, TC) + a0_scales(mp.cls[1], sh, base1, TC) +
+                     a0_scales(mp.cls[2], sh, base2, TC);
+    if (nbad == total) {
+      if (blockIdx.x == 0 && threadIdx.x == 0) atomicExch(p0.abort_flag, 1);
+      return;
+    }
+    build_amplitudes<8>(mp.cls[0], sh, 0, smem);
+    build_amplitudes<9>(mp.cls[1], sh, base1, smem);
+    build_amplitudes<10>(mp.cls[2], sh, base2, smem);
+  } else {
+    restore_flags(mp.cls[0], sh, 0);
+    restore_flags(mp.cls[1], sh, base1);
+    restore_flags(mp.cls[2], sh, base2);
+  }
+  __syncthreads();
+
+  const int npass = pass_count(p0);
+  for (int q0 = 0; q0 < npass; ++q0) {
+    const PassInfo f = pass_info(p0, q0);
+    mixed_class_pass<0, TC>(mp, sh, f, smem, mphase, s1, s2a);
+    mixed_class_pass<1, TC>(mp, sh, f, smem, mphase, s1, s2b);
+    mixed_class_pass<2, TC>(mp, sh, f, smem, mphase, s1, s2c);
+    if (!grid_sync(p0, target, sh)) {
+      drain_copies(sh);
+      return;
+    }
+  }
+  final_gaps(mp.cls[0], sh, 0);
+  final_gaps(mp.cls[1], sh, base1);
+  final_gaps(mp.cls[2], sh, base2);
 }
 
 }  // namespace gsk

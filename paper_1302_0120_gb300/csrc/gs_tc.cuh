@@ -125,24 +125,11 @@ __device__ __forceinline__ void a_tile(uint32_t (&a)[4], const float2* cs, int m
   }
 }
 
-template <int LOGN>
-struct TcFft {
-  static constexpr int N = 1 << LOGN;
-  static constexpr int R = N >> 5;
-  static constexpr int Q = 32 / R;       // transforms per warp
-  static constexpr int KT = R / 8;       // 16-wide tiles along 2R
-  static constexpr int XS = 72;          // halves per row of the stage-1 operand (144 bytes)
-  static constexpr int ZS = 2 * R + 8;   // halves per row of the stage-2 operand (odd multiple of 16 bytes)
-  static constexpr int ZG = 32 * ZS;     // halves per transform of the stage-2 operand
-  static_assert(R == 8 || R == 16 || R == 32, "tensor-core transforms have length 256, 512 or 1024");
-  static_assert(Q * (N + 8) <= 32 * 33 && ZG * Q * 2 <= kTcWarpBytes, "buffers fit the warp slice");
-
-  static constexpr bool kEnabled = true;
-  static constexpr int KR = (R < 32) ? KT : 1;
-  // Stage 1: the 32-point real form [[C, S], [-S, C]] from its 16 x 16
-  // sub-tiles of C, S and -S (tile (mt, kt) of the 64 x 64 matrix).
+// Stage-1 fragments, the same for every transform length: the 32-point real
+// form [[C, S], [-S, C]] from its 16 x 16 sub-tiles of C, S and -S (tile
+// (mt, kt) of the 64 x 64 matrix), held in registers for a whole launch.
+struct TcStage1 {
   uint32_t fc[2][2][4], fs[2][2][4], fn[2][2][4];
-  uint32_t fr[KR][KR][4];  // stage 2 for R < 32: the R-point real form (R = 32 uses stage 1's)
 
   __device__ __forceinline__ void load(const float2* cs) {
 #pragma unroll
@@ -153,12 +140,6 @@ struct TcFft {
         a_tile<32>(fs[a][b], cs, a, 2 + b);  // rows 0..31, columns 32..63: S
         a_tile<32>(fn[a][b], cs, 2 + a, b);  // rows 32..63, columns 0..31: -S
       }
-    if constexpr (R < 32) {
-#pragma unroll
-      for (int mt = 0; mt < KT; ++mt)
-#pragma unroll
-        for (int kt = 0; kt < KT; ++kt) a_tile<R>(fr[mt][kt], cs, mt, kt);
-    }
   }
 
   // C/D += tile (mt, kt) of the 32-point real form times B.
@@ -168,11 +149,50 @@ struct TcFft {
     else if ((mt >> 1) == 0) mma_16816(d, fs[a][b], b0, b1);
     else mma_16816(d, fn[a][b], b0, b1);
   }
+};
+
+// Stage-2 fragments of the R-point real form for R < 32 (R = 32 reuses
+// stage 1's).
+template <int R>
+struct TcStage2 {
+  static constexpr int KT = R / 8;
+  uint32_t fr[KT][KT][4];
+  __device__ __forceinline__ void load(const float2* cs) {
+#pragma unroll
+    for (int mt = 0; mt < KT; ++mt)
+#pragma unroll
+      for (int kt = 0; kt < KT; ++kt) a_tile<R>(fr[mt][kt], cs, mt, kt);
+  }
+};
+
+template <>
+struct TcStage2<32> {
+  __device__ __forceinline__ void load(const float2*) {}
+};
+
+// The transform of length 2^LOGN: a view of the launch's fragments and of
+// this length's stage twiddles in shared memory.
+template <int LOGN>
+struct TcFft {
+  static constexpr bool kEnabled = true;
+  static constexpr int N = 1 << LOGN;
+  static constexpr int R = N >> 5;
+  static constexpr int Q = 32 / R;       // transforms per warp
+  static constexpr int KT = R / 8;       // 16-wide tiles along 2R
+  static constexpr int XS = 72;          // halves per row of the stage-1 operand (144 bytes)
+  static constexpr int ZS = 2 * R + 8;   // halves per row of the stage-2 operand (odd multiple of 16 bytes)
+  static constexpr int ZG = 32 * ZS;     // halves per transform of the stage-2 operand
+  static_assert(R == 8 || R == 16 || R == 32, "tensor-core transforms have length 256, 512 or 1024");
+  static_assert(Q * (N + 8) <= 32 * 33 && ZG * Q * 2 <= kTcWarpBytes, "buffers fit the warp slice");
+
+  const TcStage1& s1;
+  const TcStage2<R>& s2;
+  const float2* tw;  // stage twiddles of this length (tc_build_tables)
 
   // C/D += tile (mt, kt) of the stage-2 real form times B.
   __device__ __forceinline__ void mma2(float (&d)[4], int mt, int kt, uint32_t b0, uint32_t b1) const {
-    if constexpr (R == 32) mma32(d, mt, kt, b0, b1);
-    else mma_16816(d, fr[mt][kt], b0, b1);
+    if constexpr (R == 32) s1.mma32(d, mt, kt, b0, b1);
+    else mma_16816(d, s2.fr[mt][kt], b0, b1);
   }
 
   // Position of element j of transform gamma in the FP32 return buffer; the
@@ -183,9 +203,9 @@ struct TcFft {
     return gamma * (N + 8) + (k2 << 5) + ((j & 31) ^ ((k2 & 1) | ((k2 & 2) << 2)));
   }
 
-  // The transform. `buf` is the warp's 16-byte aligned slice (kTcWarpBytes),
-  // `tw` the block's stage twiddles. Every lane of the warp must call it.
-  __device__ __forceinline__ void run(float2 (&v)[32], unsigned char* buf, const float2* tw) const {
+  // The transform. `buf` is the warp's 16-byte aligned slice (kTcWarpBytes).
+  // Every lane of the warp must call it.
+  __device__ __forceinline__ void run(float2 (&v)[32], unsigned char* buf) const {
     const int lane = threadIdx.x & 31;
     __half* xs = reinterpret_cast<__half*>(buf);
     // Stage-1 operand B: row n = lane holds re x[.. i ..] at column i, im at 32 + i.
@@ -216,7 +236,7 @@ struct TcFft {
 #pragma unroll
       for (int mt = 0; mt < 4; ++mt)
 #pragma unroll
-        for (int kt = 0; kt < 4; ++kt) mma32(acc[mt][nt], mt, kt, b[kt >> 1][2 * (kt & 1)], b[kt >> 1][2 * (kt & 1) + 1]);
+        for (int kt = 0; kt < 4; ++kt) s1.mma32(acc[mt][nt], mt, kt, b[kt >> 1][2 * (kt & 1)], b[kt >> 1][2 * (kt & 1) + 1]);
     }
     __syncwarp();  // every lane's operand reads are done before the buffer is rewritten
 

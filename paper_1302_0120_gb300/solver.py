@@ -154,3 +154,98 @@ class GerchbergSaxton:
 
     def __exit__(self, *exc):
         self.close()
+
+
+class MixedGerchbergSaxton:
+    """Batches of square masks of sizes 256, 512 and 1024 iterated together
+    in one persistent launch (C: gs_create_mixed, gs_run_mixed).
+
+    ``max_batch`` maps each size (256, 512, 1024) to the most masks of that
+    size per run (total 1..64)."""
+
+    SIZES = (256, 512, 1024)
+
+    def __init__(self, max_batch: dict, final_residual: bool = True, stream=None, tensor_core: bool = False,
+                 init_from_target: bool = False):
+        import torch
+
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        self.final_residual = bool(final_residual)
+        self.init_from_target = bool(init_from_target)
+        self.max_batch = {n: int(max_batch.get(n, 0)) for n in self.SIZES}
+        flags = ((B.GS_FINAL_RESIDUAL if final_residual else 0) | (B.GS_INIT_FROM_TARGET if init_from_target else 0)
+                 | (B.GS_TENSOR_CORE if tensor_core else 0))
+        self.handle = B.gs_create_mixed([self.max_batch[n] for n in self.SIZES], flags, stream.cuda_stream)
+
+    def run(self, targets: dict, phases: dict | None, iters: int):
+        """Enqueue ``iters`` iterations for every size present in ``targets``
+        (size -> [batch, n, n] float32 CUDA tensor; ``phases`` likewise, or
+        None with init_from_target). Returns size -> (phase_out, r, g)."""
+        import torch
+
+        batch, tp, pp, op, rp, gp, out = [], [], [], [], [], [], {}
+        nr = iters + (1 if self.final_residual else 0)
+        for n in self.SIZES:
+            t = targets.get(n)
+            if t is None:
+                batch.append(0)
+                for lst in (tp, pp, op, rp, gp):
+                    lst.append(0)
+                continue
+            ph = None if phases is None else phases.get(n)
+            for x, name in ((t, "target"), (ph, "phase")):
+                if x is None and name == "phase" and self.init_from_target:
+                    continue
+                if not (isinstance(x, torch.Tensor) and x.is_cuda and x.dtype == torch.float32 and x.is_contiguous()
+                        and x.dim() == 3 and tuple(x.shape[1:]) == (n, n)):
+                    raise TypeError(f"{name} for size {n} must be a contiguous float32 CUDA tensor [batch, {n}, {n}]")
+            nb = t.shape[0]
+            if not 1 <= nb <= self.max_batch[n] or (ph is not None and ph.shape[0] != nb):
+                raise ValueError(f"batch {nb} of size {n} outside 1..{self.max_batch[n]} or mismatched")
+            with torch.cuda.stream(self.stream):
+                o = torch.empty_like(t)
+                r = torch.empty((nb, max(nr, 1)), dtype=torch.float64, device=t.device)
+                g = torch.empty((nb, max(iters, 1)), dtype=torch.float64, device=t.device)
+            out[n] = (o, r[:, :nr], g[:, :iters])
+            batch.append(nb)
+            tp.append(t.data_ptr())
+            pp.append(ph.data_ptr() if ph is not None else 0)
+            op.append(o.data_ptr())
+            rp.append(r.data_ptr())
+            gp.append(g.data_ptr())
+        rc = B.gs_run_mixed(self.handle, batch, tp, None if self.init_from_target and phases is None else pp,
+                            int(iters), op, rp, gp)
+        if rc != B.GS_OK:
+            raise B.GSError(rc, "gs_run_mixed")
+        return out
+
+    def status(self) -> int:
+        return B.gs_status(self.handle)
+
+    @property
+    def grid(self) -> int:
+        return B.gs_get_grid(self.handle)
+
+    def set_grid(self, ctas: int) -> None:
+        rc = B.gs_set_grid(self.handle, int(ctas))
+        if rc != B.GS_OK:
+            raise B.GSError(rc, "gs_set_grid")
+
+    def close(self) -> None:
+        if getattr(self, "handle", None):
+            B.gs_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

@@ -94,6 +94,19 @@ def test_null_context_calls(lib):
     assert lib.gs_test_barrier_timeout(None, 1) == B.GS_EINVAL
     assert lib.gs_physical_error(None, None, None, None) == B.GS_EINVAL
     assert lib.gs_loss_grad(None, None, None, None, None) == B.GS_EINVAL
+    assert lib.gs_run_mixed(None, None, None, None, 1, None, None, None) == B.GS_EINVAL
+
+
+def test_create_mixed_validates_before_cuda(lib):
+    h = ctypes.c_void_p(123)
+    for mb in ((0, 0, 0), (65, 0, 0), (40, 20, 5), (-1, 2, 2), (0, 0, 65)):
+        arr = (ctypes.c_int * 3)(*mb)
+        assert lib.gs_create_mixed(ctypes.byref(h), ctypes.cast(arr, ctypes.c_void_p), 1, None) == B.GS_EINVAL
+        assert h.value is None
+    arr = (ctypes.c_int * 3)(2, 2, 2)
+    assert lib.gs_create_mixed(None, ctypes.cast(arr, ctypes.c_void_p), 1, None) == B.GS_EINVAL
+    assert lib.gs_create_mixed(ctypes.byref(h), None, 1, None) == B.GS_EINVAL
+    assert lib.gs_create_mixed(ctypes.byref(h), ctypes.cast(arr, ctypes.c_void_p), 0x80, None) == B.GS_EINVAL
 
 
 def test_noalloc_validates_before_cuda(lib):
