@@ -97,8 +97,10 @@ static __device__ bool grid_sync(const Params& p, unsigned& target, Shared& sh) 
   target += gridDim.x;
   if (threadIdx.x == 0) {
     int ok = 1;
-    __threadfence();
-    atomicAdd(p.bar, 1u);
+    // Arrival with release semantics at GPU scope: cumulative, so it covers
+    // the block's writes that the __syncthreads above ordered before it
+    // (bulk stores were completed and fenced by their issuing thread).
+    asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(p.bar) : "memory");
     const unsigned want = target + p.extra_arrivals;
     unsigned spins = 0;
     unsigned long long t0 = 0;
@@ -114,7 +116,10 @@ static __device__ bool grid_sync(const Params& p, unsigned& target, Shared& sh) 
         }
       }
     }
-    __threadfence();
+    // The acquire load above orders this thread's later reads after every
+    // block's arrival; the proxy fence extends that to the bulk copies it
+    // issues next, and the __syncthreads below to the rest of the block.
+    asm volatile("fence.proxy.async.global;" ::: "memory");
     if (ok && *reinterpret_cast<volatile int*>(p.abort_flag) != 0) ok = 0;  // another block failed
     sh.flag = ok;
   }

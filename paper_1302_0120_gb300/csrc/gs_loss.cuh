@@ -38,8 +38,7 @@ static __device__ bool loss_sync(const LossParams& p, unsigned& target, Shared& 
   target += gridDim.x;
   if (threadIdx.x == 0) {
     int ok = 1;
-    __threadfence();
-    atomicAdd(p.bar, 1u);
+    asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(p.bar) : "memory");
     unsigned spins = 0;
     unsigned long long t0 = 0;
     while (static_cast<int>(ld_acquire_gpu(p.bar) - target) < 0) {
@@ -55,7 +54,7 @@ static __device__ bool loss_sync(const LossParams& p, unsigned& target, Shared& 
         }
       }
     }
-    __threadfence();
+    asm volatile("fence.proxy.async.global;" ::: "memory");
     if (ok && *reinterpret_cast<volatile int*>(p.abort_flag) != 0) ok = 0;
     sh.flag = ok;
   }
