@@ -141,7 +141,9 @@ int gs_run(gs_ctx* c, const float* target_intensity, const float* phase_in, int 
  * gs_run_batched -- gs_run for `batch` independent masks of the same grid.
  *
  * Operation: Eq. (e:AP) for each mask b < batch, exactly as gs_run (the
- * masks share only the launch: results are identical to separate runs).
+ * masks share only the launch: phases are identical to separate runs; the
+ * gaps agree to FP64 rounding, their partial sums being grouped by the
+ * blocks' shares of the whole batch).
  * Every array is strided by mask, mask b at offset b * (per-mask size):
  *   target_intensity, phase_in, phase_out  device, float [batch][ny][nx]
  *   residual_out   device, double [batch][K+1] (GS_FINAL_RESIDUAL) or

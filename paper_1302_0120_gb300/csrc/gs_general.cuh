@@ -188,10 +188,11 @@ __device__ __forceinline__ float gen_phase(float2 u) {
   return (a <= -3.14159274f) ? 3.14159274f : a;
 }
 
-// One pass over this block's share of rows (kInit, kRow) or of 8-column
-// groups (kCol, kResid, kInitM). Returns this thread's FP64 contribution to
-// the pass's gap sum.
-static __device__ __forceinline__ double run_pass_gen(const Params& p, int mb, int kind, bool last, unsigned char* smem) {
+// One pass over rows [lo, hi) (kInit, kRow) or 8-column groups [lo, hi)
+// (kCol, kResid, kInitM) of mask mb. Returns this thread's FP64 contribution
+// to the pass's gap sum.
+static __device__ __forceinline__ double run_pass_gen(const Params& p, int mb, int kind, bool last, int lo, int hi,
+                                                      unsigned char* smem) {
   const size_t moff = static_cast<size_t>(mb) * static_cast<size_t>(p.mstride);
   float2* const Bm = p.B + moff;
   const float* const mTm = p.mT + moff;
@@ -208,8 +209,6 @@ static __device__ __forceinline__ double run_pass_gen(const Params& p, int mb, i
   double acc = 0.0;
 
   if (kind == kInit || kind == kRow) {
-    const int lo = split(blockIdx.x, gridDim.x, ny);
-    const int hi = split(blockIdx.x + 1, gridDim.x, ny);
     for (int row = lo + w; row < hi; row += kThreads / 32) {
       float2* src = Bm + static_cast<size_t>(row) * nx;
       const float* pp = p.p_slm ? p.p_slm + static_cast<size_t>(row) * nx : nullptr;
@@ -283,9 +282,6 @@ static __device__ __forceinline__ double run_pass_gen(const Params& p, int mb, i
   }
 
   // Column passes: groups of 8 adjacent columns; warp k owns column c0 + k.
-  const int ncg = (nx + 7) >> 3;
-  const int lo = split(blockIdx.x, gridDim.x, ncg);
-  const int hi = split(blockIdx.x + 1, gridDim.x, ncg);
   const int stride = gen_warp_stride(nmax);
   const bool store = (kind == kCol || kind == kInitM);
   // which of a warp's buffers holds the stored result: A after two transforms,

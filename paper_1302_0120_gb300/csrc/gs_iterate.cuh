@@ -84,13 +84,13 @@ struct FieldLayout {
   __device__ static int boff(int y, int k) { return y * W + (k ^ swz(y)); }
 };
 
-// One pass over this block's share of rows (kInit, kRow; LOGN = log2 nx) or
-// column blocks (kCol, kResid; LOGN = log2 ny). Returns this thread's FP64
-// contribution to the pass's gap sum.
+// One pass over rows [lo, hi) (kInit, kRow; LOGN = log2 nx) or column blocks
+// [lo, hi) (kCol, kResid, kInitM; LOGN = log2 ny) of mask mb. Returns this
+// thread's FP64 contribution to the pass's gap sum.
 template <int LOGN, int LX, int LY, bool HOLD, class TCF>
-__device__ __forceinline__ double run_pass(const Params& p, int mb, int kind, bool last, unsigned char* smem,
-                                           Shared& sh, unsigned& mphase, const StageTw<LOGN>& tw_rows,
-                                           const TCF& tcf) {
+__device__ __forceinline__ double run_pass(const Params& p, int mb, int kind, bool last, int lo, int hi,
+                                           unsigned char* smem, Shared& sh, unsigned& mphase,
+                                           const StageTw<LOGN>& tw_rows, const TCF& tcf) {
   // this mask's arrays
   const size_t moff = static_cast<size_t>(mb) * static_cast<size_t>(p.mstride);
   float2* const Bm = p.B + moff;
@@ -136,8 +136,6 @@ __device__ __forceinline__ double run_pass(const Params& p, int mb, int kind, bo
 
   if constexpr (LOGN == LX) {
   if (rows) {
-    const int lo = split(blockIdx.x, gridDim.x, p.ny);
-    const int hi = split(blockIdx.x + 1, gridDim.x, p.ny);
     for (int base = lo; base < hi; base += NG) {
       const int idx = base + g;
       const bool valid = idx < hi;
@@ -249,8 +247,6 @@ __device__ __forceinline__ double run_pass(const Params& p, int mb, int kind, bo
   if constexpr (LOGN == LY) {
   constexpr int W = L::W;
   static_assert(N == L::NY, "column transforms have length ny");
-  const int lo = split(blockIdx.x, gridDim.x, L::NBLK);
-  const int hi = split(blockIdx.x + 1, gridDim.x, L::NBLK);
   const bool gact = g < W;                                // this group owns a column
   const bool wact = ((threadIdx.x & ~31) >> LOGT) < W;    // some group of this warp does
   const int gq = gact ? g : 0;                            // idle groups read a valid column
@@ -495,28 +491,45 @@ static __device__ __forceinline__ PassInfo pass_info(const Params& p, int q0) {
   return f;
 }
 
-// One pass over every valid mask of a class, with the FP64 block partial of
-// each mask's gap written to its slot.
+// One pass over every valid mask of a class. The work units of all masks
+// (rows, or column blocks) form one sequence split evenly over the blocks,
+// so that small masks of a batch do not leave blocks idle; a block works
+// through its share mask by mask and writes the FP64 partial of each mask's
+// gap to its slot (zero for the masks it does not touch).
 template <int LX, int LY, bool HOLD, class TCF>
 __device__ __forceinline__ void class_pass(const Params& p, Shared& sh, int base, const PassInfo& f,
                                            unsigned char* smem, unsigned& mphase, const StageTw<LX>& tw_rows,
                                            const TCF& tcf) {
-  for (int mb = 0; mb < p.batch; ++mb) {
+  const bool rows = (f.kind == kInit || f.kind == kRow);
+  int per;  // units of one mask
+  if constexpr (LX == 0) per = rows ? p.ny : (p.nx + 7) >> 3;
+  else per = rows ? p.ny : FieldLayout<LX, LY>::NBLK;
+  const int total = per * p.batch;
+  const int G = gridDim.x;
+  const int lo = split(blockIdx.x, G, total);
+  const int hi = split(blockIdx.x + 1, G, total);
+  const int m0 = lo / per;
+  const int m1 = (hi + per - 1) / per;  // masks [m0, m1) meet [lo, hi)
+  if (f.slot >= 0 && threadIdx.x == 0)
+    for (int mb = 0; mb < p.batch; ++mb)
+      if (mb < m0 || mb >= m1) p.partials[(static_cast<size_t>(f.slot) * p.batch + mb) * G + blockIdx.x] = 0.0;
+  for (int mb = m0; mb < m1; ++mb) {
     if (sh.bad[base + mb]) continue;
+    const int slo = max(lo, mb * per) - mb * per;
+    const int shi = min(hi, (mb + 1) * per) - mb * per;
     double a;
     if constexpr (LX == 0) {
-      a = run_pass_gen(p, mb, f.kind, f.last, smem);
+      a = run_pass_gen(p, mb, f.kind, f.last, slo, shi, smem);
     } else if constexpr (LX == LY) {
-      a = run_pass<LX, LX, LY, HOLD>(p, mb, f.kind, f.last, smem, sh, mphase, tw_rows, tcf);
+      a = run_pass<LX, LX, LY, HOLD>(p, mb, f.kind, f.last, slo, shi, smem, sh, mphase, tw_rows, tcf);
     } else {
       const StageTw<LY> none{};
-      a = (f.kind == kInit || f.kind == kRow)
-              ? run_pass<LX, LX, LY, false>(p, mb, f.kind, f.last, smem, sh, mphase, tw_rows, tcf)
-              : run_pass<LY, LX, LY, false>(p, mb, f.kind, f.last, smem, sh, mphase, none, tcf);
+      a = rows ? run_pass<LX, LX, LY, false>(p, mb, f.kind, f.last, slo, shi, smem, sh, mphase, tw_rows, tcf)
+               : run_pass<LY, LX, LY, false>(p, mb, f.kind, f.last, slo, shi, smem, sh, mphase, none, tcf);
     }
     if (f.slot >= 0) {
       const double tot = block_sum(a, sh);
-      if (threadIdx.x == 0) p.partials[(static_cast<size_t>(f.slot) * p.batch + mb) * gridDim.x + blockIdx.x] = tot;
+      if (threadIdx.x == 0) p.partials[(static_cast<size_t>(f.slot) * p.batch + mb) * G + blockIdx.x] = tot;
     }
   }
 }

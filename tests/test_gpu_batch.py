@@ -1,6 +1,8 @@
 """Batched runs (gs_run_batched): several independent masks of the same grid
-in one launch give exactly the results of separate runs (the masks share the
-launch and its barriers, not their arithmetic), and an invalid target only
+in one launch give exactly the phases of separate runs (the masks share the
+launch and its barriers, not their arithmetic) and the same gaps to FP64
+rounding (the FP64 partial sums are grouped by each block's share of the
+batch, which differs from a single mask's share), and an invalid target only
 takes its own mask out."""
 
 import numpy as np
@@ -10,6 +12,11 @@ from paper_1302_0120_gb300 import synthetic as S
 from tests.gpu_util import gpu_gs
 
 pytestmark = pytest.mark.gpu
+
+
+def same_gaps(a, b):
+    """FP64 gaps summed in a different grouping: equal to rounding."""
+    return np.allclose(a, b, rtol=1e-12, atol=0)
 
 
 def make_batch(n_masks, ny, nx, iters_seed=0, nspots=20):
@@ -48,8 +55,8 @@ def test_batch_equals_separate_runs(n, ny, nx, iters, grid):
         ph1, r1, g1, st1 = gpu_gs(I[k], P[k], iters, grid=grid)
         assert st1 == 0
         assert np.array_equal(ph[k], ph1), k
-        assert np.array_equal(r[k], r1), k
-        assert np.array_equal(g[k], g1), k
+        assert same_gaps(r[k], r1), k
+        assert same_gaps(g[k], g1), k
 
 
 def test_batch_with_an_invalid_target():
@@ -67,7 +74,7 @@ def test_batch_with_an_invalid_target():
     assert np.all(ph[1] == 9.0) and np.all(np.isnan(r[1])) and np.all(np.isnan(g[1]))
     for k in (0, 2):
         ph1, r1, g1, st1 = gpu_gs(I[k], P[k], 10)
-        assert np.array_equal(ph[k], ph1) and np.array_equal(r[k], r1) and np.array_equal(g[k], g1)
+        assert np.array_equal(ph[k], ph1) and same_gaps(r[k], r1) and same_gaps(g[k], g1)
 
 
 def test_batch_with_an_invalid_target_across_launches():
@@ -84,4 +91,4 @@ def test_batch_with_an_invalid_target_across_launches():
         ph, r = ph.cpu().numpy(), r.cpu().numpy()
     assert np.all(ph[0] == 9.0) and np.all(np.isnan(r[0]))
     ph1, r1, _, _ = gpu_gs(I[1], P[1], 140)
-    assert np.array_equal(ph[1], ph1) and np.array_equal(r[1], r1)
+    assert np.array_equal(ph[1], ph1) and same_gaps(r[1], r1)
