@@ -342,6 +342,7 @@ def run_gpu(args):
             raise RuntimeError("batched run failed")
         bper = statistics.mean(s_.elapsed_time(e_) for s_, e_ in zip(bs, be))
         batched = {"batch": nb, "steps": bsteps, "ms_per_launch": round(bper, 4),
+                   "achieved_gbs": round((BYTES_PER_PX_FIXED + BYTES_PER_PX_ITER * iters) * n * nb / (bper * 1e6), 1),
                    "ms_per_mask": round(bper / nb, 4), "masks_per_s": round(1e3 * nb / bper, 1)}
         gsb.close()
 
@@ -379,6 +380,9 @@ def run_gpu(args):
             raise RuntimeError("loss kernel failed")
         differentiable = {"n": nx, "spots": 100, "adam_steps": args.adam_steps, "lr": 0.05,
                           "ms_per_step": round(e0.elapsed_time(e1) / args.adam_steps, 4),
+                          # the loss kernel's 60 B/px over the whole step (Adam update included)
+                          "loss_kernel_gbs_lower_bound": round(
+                              60 * n * args.adam_steps / (e0.elapsed_time(e1) * 1e6), 1),
                           "loss_first": float(losses[0]), "loss_last": float(losses[-1])}
         lc.close()
 
@@ -411,6 +415,7 @@ def run_gpu(args):
             raise RuntimeError("tensor-core run failed")
         r_t = float(res_t["r"][-1].item())
         tensor_core = {"ms_per_mask": round(ms_t, 4), "fp32_ms_per_mask": round(mean_ms, 4),
+                       "achieved_gbs": round((BYTES_PER_PX_FIXED + BYTES_PER_PX_ITER * iters) * n / (ms_t * 1e6), 1),
                        "speedup_vs_fp32": round(mean_ms / ms_t, 4), "final_residual": r_t,
                        "final_residual_rel_diff_vs_fp32": round(abs(r_t - r_final) / r_final, 6),
                        "matched_within_2pct": abs(r_t - r_final) <= 0.02 * r_final, "steps": args.tc_steps}
@@ -444,7 +449,9 @@ def run_gpu(args):
                 host_ms.append(1e3 * (time.perf_counter() - t0))
         if gsp.status() != 0:
             raise RuntimeError("800x600 run failed")
+        # target start, no residual outputs: 44 + 36 K bytes per pixel
         paper_800x600 = {"iters": 25, "init": "target (P_S F^-1 m)", "device_ms": round(ms_p, 4),
+                         "achieved_gbs": round((44 + BYTES_PER_PX_ITER * 25) * 480000 / (ms_p * 1e6), 1),
                          "e2e_ms": round(statistics.mean(host_ms), 4), "paper_ms_c2070": 45.0,
                          "speedup_vs_paper_e2e": round(45.0 / statistics.mean(host_ms), 1), "grid_ctas": gsp.grid}
         gsp.close()
@@ -481,6 +488,8 @@ def run_gpu(args):
             mixed64["grid_ctas"] = gm.grid
             gm.close()
             mixed64["tensor_core_ms" if tc else "fp32_ms"] = round(ms_m, 4)
+            mbytes = sum((BYTES_PER_PX_FIXED + BYTES_PER_PX_ITER * 50) * n_ * n_ * len(ks) for n_, ks in groups.items())
+            mixed64["tensor_core_achieved_gbs" if tc else "fp32_achieved_gbs"] = round(mbytes / (ms_m * 1e6), 1)
             mixed64["tensor_core_ms_per_mask" if tc else "fp32_ms_per_mask"] = round(ms_m / len(masks), 4)
         mixed64["worst_final_residual_rel_diff_tc_vs_fp32"] = round(
             max(abs(rfin[(True, k)] - rfin[(False, k)]) / rfin[(False, k)] for k in range(len(masks))), 6)

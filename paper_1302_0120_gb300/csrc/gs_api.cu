@@ -204,7 +204,19 @@ int choose_grid_for(const gs_ctx* c, long long pixels) {
   return g;
 }
 
-int choose_grid(const gs_ctx* c) { return choose_grid_for(c, static_cast<long long>(c->nx) * c->ny); }
+int choose_grid(const gs_ctx* c) {
+  if (!c->mixed && (!is_pow2(c->nx) || !is_pow2(c->ny)) && c->grid_override <= 0) {
+    // general sides: one row per team (four per block) and one 4-column
+    // group per block, so that each pass is one round
+    const int t = gsk::kGenTeams;
+    int g = (c->ny + t - 1) / t;
+    const int gc = (c->nx + t - 1) / t;
+    if (gc > g) g = gc;
+    const int cap = max_grid(c);
+    return g > cap ? cap : g;
+  }
+  return choose_grid_for(c, static_cast<long long>(c->nx) * c->ny);
+}
 
 }  // namespace
 

@@ -6,22 +6,24 @@
 // power-of-two kernel (gs_iterate.cuh); what differs is the transform and the
 // data movement:
 //   * The field B is stored row-major [ny][nx]; m transposed [nx][ny].
-//   * A row pass gives each warp one row: the row is read coalesced into the
-//     warp's shared-memory buffer, transformed, projected and transformed
+//   * A row or column is transformed by a team of two warps (64 threads,
+//     four teams per block), which halves each transform's chain of
+//     dependent stage loops; teams synchronise on their own named barrier.
+//   * A row pass gives each team one row: the row is read coalesced into the
+//     team's shared-memory buffer, transformed, projected and transformed
 //     again there, and written back coalesced.
-//   * A column pass moves 8 adjacent columns at a time: the block reads the
-//     [ny][8] tile in 64-byte row segments into eight per-warp column buffers,
-//     each warp transforms, projects and transforms its column, and the block
+//   * A column pass moves 4 adjacent columns at a time: the block reads the
+//     [ny][4] tile in 32-byte row segments into four per-team column buffers,
+//     each team transforms, projects and transforms its column, and the block
 //     writes the tile back the same way.
 //   * A length-n transform is a Stockham auto-sort FFT with radices 3 and 5
 //     first, then 8, 4 and 2 (gen_fft), each stage read from one of the warp's
-//     two buffers and written to the other. Each lane takes several
-//     butterflies at once so that their shared-memory loads overlap. The
+//     two buffers and written to the other. The
 //     twiddles of the stage with sub-transform length ns and radix R sit at
 //     entries ns - 1 + (m - 1) ns + r (W_{ns R}^{r m}), so that consecutive
 //     butterflies read consecutive entries; the tables are rounded once from
 //     double on the host and copied to shared memory per launch.
-//   * Rows and column tiles arrive by cp.async, every copy of a lane in
+//   * Rows and column tiles arrive by cp.async, every copy of a thread in
 //     flight at once.
 #pragma once
 
@@ -77,26 +79,31 @@ __device__ __forceinline__ void small_dft(float2 (&a)[R]) {
   else dft<R>(a);
 }
 
+// Barrier of team `team` (its two warps), named barrier 1 + team.
+__device__ __forceinline__ void team_sync(int team) {
+  asm volatile("bar.sync %0, %1;" ::"r"(1 + team), "n"(kGenTeam) : "memory");
+}
+
 // One Stockham stage of radix R on a length-n transform whose first stages
 // formed sub-transforms of length ns: butterfly j = q ns + r reads
 // src[j + m n/R], multiplies by W_{ns R}^{r m} (stage table tw), transforms
-// over m and writes dst[q ns R + r + k ns]. A lane takes U butterflies
-// (j, j + 32, ...) at a time.
+// over m and writes dst[q ns R + r + k ns]. Thread t of the team takes
+// butterflies t, t + 64, ...
 template <int R>
 __device__ __forceinline__ void gen_stage(const float2* __restrict__ src, float2* __restrict__ dst, int n, int ns,
                                           const float2* __restrict__ tw) {
   constexpr int U = 1;
   const int nb = n / R;
-  const int lane = threadIdx.x & 31;
-  const int qinc = 32 / ns, rinc = 32 % ns;
-  int q = lane / ns, r = lane % ns;
+  const int tt = threadIdx.x % kGenTeam;
+  const int qinc = kGenTeam / ns, rinc = kGenTeam % ns;
+  int q = tt / ns, r = tt % ns;
   const float2* const tws = tw + (ns - 1);
-  for (int j0 = lane; j0 < nb; j0 += 32 * U) {
+  for (int j0 = tt; j0 < nb; j0 += kGenTeam * U) {
     float2 a[U][R];
     int base[U], rr[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
-      const int j = j0 + 32 * u;
+      const int j = j0 + kGenTeam * u;
       rr[u] = r;
       base[u] = q * ns * R + r;
       if (j < nb) {
@@ -113,14 +120,14 @@ __device__ __forceinline__ void gen_stage(const float2* __restrict__ src, float2
     if (ns > 1) {
 #pragma unroll
       for (int u = 0; u < U; ++u)
-        if (j0 + 32 * u < nb) {
+        if (j0 + kGenTeam * u < nb) {
 #pragma unroll
           for (int m = 1; m < R; ++m) a[u][m] = cmul(a[u][m], tws[(m - 1) * ns + rr[u]]);
         }
     }
 #pragma unroll
     for (int u = 0; u < U; ++u)
-      if (j0 + 32 * u < nb) {
+      if (j0 + kGenTeam * u < nb) {
         small_dft<R>(a[u]);
 #pragma unroll
         for (int k = 0; k < R; ++k) dst[base[u] + k * ns] = a[u][k];
@@ -128,10 +135,11 @@ __device__ __forceinline__ void gen_stage(const float2* __restrict__ src, float2
   }
 }
 
-// Forward unnormalised DFT of the length-n vector in `a` by the warp, using
-// `b` as the second buffer; returns the buffer that holds the result (a for
-// an even number of stages, b for an odd one).
-__device__ __forceinline__ float2* gen_fft(float2* a, float2* b, int n, unsigned plan, int nst, const float2* tw) {
+// Forward unnormalised DFT of the length-n vector in `a` by team `team`,
+// using `b` as the second buffer; returns the buffer that holds the result
+// (a for an even number of stages, b for an odd one).
+__device__ __forceinline__ float2* gen_fft(float2* a, float2* b, int n, unsigned plan, int nst, const float2* tw,
+                                           int team) {
   int ns = 1;
 #pragma unroll 1
   for (int s = 0; s < nst; ++s) {
@@ -143,7 +151,7 @@ __device__ __forceinline__ float2* gen_fft(float2* a, float2* b, int n, unsigned
       case 5: gen_stage<5>(a, b, n, ns, tw); break;
       default: gen_stage<8>(a, b, n, ns, tw); break;
     }
-    __syncwarp();
+    team_sync(team);
     ns *= R;
     float2* t = a;
     a = b;
@@ -201,25 +209,25 @@ static __device__ __forceinline__ double run_pass_gen(const Params& p, int mb, i
   const float2* twx = reinterpret_cast<const float2*>(smem);
   const float2* twy = twx + nx;
   float2* wbase = reinterpret_cast<float2*>(smem) + gen_tw_entries(nx, ny);
-  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  float2* const A = wbase + w * gen_warp_stride(nmax);
+  const int tm = threadIdx.x / kGenTeam, tt = threadIdx.x % kGenTeam;
+  float2* const A = wbase + tm * gen_team_stride(nmax);
   float2* const Bf = A + nmax + 1;
   const float inv_sqrt_n = p.inv_sqrt_n;
   const bool two = (kind == kCol || (kind == kRow && !(last && !p.final_resid)));
   double acc = 0.0;
 
   if (kind == kInit || kind == kRow) {
-    for (int row = lo + w; row < hi; row += kThreads / 32) {
+    for (int row = lo + tm; row < hi; row += kGenTeams) {
       float2* src = Bm + static_cast<size_t>(row) * nx;
       const float* pp = p.p_slm ? p.p_slm + static_cast<size_t>(row) * nx : nullptr;
       if (kind == kInit) {
         const float* ph = p.phi_in + moff + static_cast<size_t>(row) * nx;
         float* po = p.phi_out + moff + static_cast<size_t>(row) * nx;
-        for (int x0 = lane; x0 < nx; x0 += 32 * 4) {
+        for (int x0 = tt; x0 < nx; x0 += kGenTeam * 4) {
           float f[4], a[4];
 #pragma unroll
           for (int k = 0; k < 4; ++k) {
-            const int x = x0 + 32 * k;
+            const int x = x0 + kGenTeam * k;
             f[k] = x < nx ? ph[x] : 0.f;
             a[k] = (pp && x < nx) ? pp[x] : 1.f;  // u0 = p exp(i phi0)
           }
@@ -227,32 +235,32 @@ static __device__ __forceinline__ double run_pass_gen(const Params& p, int mb, i
           for (int k = 0; k < 4; ++k) {
             float s, c;
             sincosf(f[k], &s, &c);
-            if (x0 + 32 * k < nx) A[x0 + 32 * k] = make_float2(a[k] * c, a[k] * s);
+            if (x0 + kGenTeam * k < nx) A[x0 + kGenTeam * k] = make_float2(a[k] * c, a[k] * s);
           }
         }
         if (last) {  // zero iterations
-          __syncwarp();
-          for (int x = lane; x < nx; x += 32) po[x] = gen_phase(A[x]);
+          team_sync(tm);
+          for (int x = tt; x < nx; x += kGenTeam) po[x] = gen_phase(A[x]);
         }
       } else {
-        for (int x = lane; x < nx; x += 32) cp_async8(A + x, src + x);
+        for (int x = tt; x < nx; x += kGenTeam) cp_async8(A + x, src + x);
         cp_async_wait_all();
       }
-      __syncwarp();
-      float2* res = gen_fft(A, Bf, nx, p.planx, p.nstx, twx);
+      team_sync(tm);
+      float2* res = gen_fft(A, Bf, nx, p.planx, p.nstx, twx, tm);
       if (kind == kRow) {
         // res = swap(IDFT_x(B)) = swap(sqrt(N) P_M u^nu): gap to S, Eq. (e:PS)
         float part = 0.f;
-        for (int x0 = lane; x0 < nx; x0 += 32 * 8) {
+        for (int x0 = tt; x0 < nx; x0 += kGenTeam * 8) {
           float a[8];
 #pragma unroll
-          for (int k = 0; k < 8; ++k) a[k] = (pp && x0 + 32 * k < nx) ? pp[x0 + 32 * k] : 1.f;
+          for (int k = 0; k < 8; ++k) a[k] = (pp && x0 + kGenTeam * k < nx) ? pp[x0 + kGenTeam * k] : 1.f;
           float2 t8[8];
 #pragma unroll
-          for (int k = 0; k < 8; ++k) t8[k] = (x0 + 32 * k < nx) ? res[x0 + 32 * k] : make_float2(1.f, 0.f);
+          for (int k = 0; k < 8; ++k) t8[k] = (x0 + kGenTeam * k < nx) ? res[x0 + kGenTeam * k] : make_float2(1.f, 0.f);
 #pragma unroll
           for (int k = 0; k < 8; ++k) {
-            const int x = x0 + 32 * k;
+            const int x = x0 + kGenTeam * k;
             if (x < nx) {
               const float2 t = t8[k];
               const float vx = t.y, vy = t.x;
@@ -267,60 +275,60 @@ static __device__ __forceinline__ double run_pass_gen(const Params& p, int mb, i
           }
         }
         acc += static_cast<double>(part);
-        __syncwarp();
+        team_sync(tm);
         if (last) {
           float* po = p.phi_out + moff + static_cast<size_t>(row) * nx;
-          for (int x = lane; x < nx; x += 32) po[x] = gen_phase(res[x]);
+          for (int x = tt; x < nx; x += kGenTeam) po[x] = gen_phase(res[x]);
         }
-        if (two) res = gen_fft(res, res == A ? Bf : A, nx, p.planx, p.nstx, twx);
+        if (two) res = gen_fft(res, res == A ? Bf : A, nx, p.planx, p.nstx, twx, tm);
       }
       if (kind == kInit || two)
-        for (int x = lane; x < nx; x += 32) src[x] = res[x];
-      __syncwarp();
+        for (int x = tt; x < nx; x += kGenTeam) src[x] = res[x];
+      team_sync(tm);
     }
     return acc;
   }
 
-  // Column passes: groups of 8 adjacent columns; warp k owns column c0 + k.
-  const int stride = gen_warp_stride(nmax);
+  // Column passes: groups of 4 adjacent columns; team k owns column c0 + k.
+  const int stride = gen_team_stride(nmax);
   const bool store = (kind == kCol || kind == kInitM);
   // which of a warp's buffers holds the stored result: A after two transforms,
   // else A or Bf by the parity of the stage count
   const int out_off = (kind == kCol || (p.nsty & 1) == 0) ? 0 : nmax + 1;
   for (int cg = lo; cg < hi; ++cg) {
-    const int c0 = cg << 3;
-    const int wc = min(8, nx - c0);
+    const int c0 = cg * kGenTeams;
+    const int wc = min(kGenTeams, nx - c0);
     __syncthreads();  // the previous group's tile has been written back
     {
-      const int k = threadIdx.x & 7;  // column of this thread in every round
+      const int k = threadIdx.x % kGenTeams;  // column of this thread in every round
       if (k < wc) {
         if (kind == kInitM) {
-          for (int y = threadIdx.x >> 3; y < ny; y += kThreads / 8)  // swap((m, 0))
+          for (int y = threadIdx.x / kGenTeams; y < ny; y += kThreads / kGenTeams)  // swap((m, 0))
             wbase[k * stride + y] = make_float2(0.f, mTm[static_cast<size_t>(c0 + k) * ny + y]);
         } else {
-          for (int y = threadIdx.x >> 3; y < ny; y += kThreads / 8)
+          for (int y = threadIdx.x / kGenTeams; y < ny; y += kThreads / kGenTeams)
             cp_async8(wbase + k * stride + y, Bm + static_cast<size_t>(y) * nx + c0 + k);
           cp_async_wait_all();
         }
       }
     }
     __syncthreads();
-    if (w < wc) {
-      float2* res = gen_fft(A, Bf, ny, p.plany, p.nsty, twy);
+    if (tm < wc) {
+      float2* res = gen_fft(A, Bf, ny, p.plany, p.nsty, twy, tm);
       if (kind != kInitM) {
         // res = Y = F u^nu along this column: residual and Eq. (e:Mhat)
-        const float* mcol = mTm + static_cast<size_t>(c0 + w) * ny;
+        const float* mcol = mTm + static_cast<size_t>(c0 + tm) * ny;
         float part = 0.f;
-        for (int y0 = lane; y0 < ny; y0 += 32 * 8) {
+        for (int y0 = tt; y0 < ny; y0 += kGenTeam * 8) {
           float mv[8];
           float2 yv[8];
 #pragma unroll
-          for (int u = 0; u < 8; ++u) mv[u] = (y0 + 32 * u < ny) ? mcol[y0 + 32 * u] : 0.f;
+          for (int u = 0; u < 8; ++u) mv[u] = (y0 + kGenTeam * u < ny) ? mcol[y0 + kGenTeam * u] : 0.f;
 #pragma unroll
-          for (int u = 0; u < 8; ++u) yv[u] = (y0 + 32 * u < ny) ? res[y0 + 32 * u] : make_float2(1.f, 0.f);
+          for (int u = 0; u < 8; ++u) yv[u] = (y0 + kGenTeam * u < ny) ? res[y0 + kGenTeam * u] : make_float2(1.f, 0.f);
 #pragma unroll
           for (int u = 0; u < 8; ++u) {
-            const int y = y0 + 32 * u;
+            const int y = y0 + kGenTeam * u;
             if (y < ny) {
               const float m = mv[u];
               const float2 Y = yv[u];
@@ -338,14 +346,14 @@ static __device__ __forceinline__ double run_pass_gen(const Params& p, int mb, i
           }
         }
         acc += static_cast<double>(part);
-        __syncwarp();
-        if (kind == kCol) res = gen_fft(res, res == A ? Bf : A, ny, p.plany, p.nsty, twy);
+        team_sync(tm);
+        if (kind == kCol) res = gen_fft(res, res == A ? Bf : A, ny, p.plany, p.nsty, twy, tm);
       }
     }
     if (store) {
       __syncthreads();
-      for (int e = threadIdx.x; e < ny * 8; e += kThreads) {
-        const int y = e >> 3, k = e & 7;
+      for (int e = threadIdx.x; e < ny * kGenTeams; e += kThreads) {
+        const int y = e / kGenTeams, k = e % kGenTeams;
         if (k < wc) Bm[static_cast<size_t>(y) * nx + c0 + k] = wbase[k * stride + out_off + y];
       }
     }

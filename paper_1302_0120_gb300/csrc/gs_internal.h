@@ -70,13 +70,18 @@ struct MixedParams {
 constexpr int kMaxGeneralSide = 1536;
 constexpr int kMaxGeneralStages = 10;
 
+// The general kernel transforms a row or column with a team of two warps;
+// a block holds four teams.
+constexpr int kGenTeam = 64;
+constexpr int kGenTeams = kThreads / kGenTeam;
+
 // Shared-memory layout of the general kernel: the two twiddle tables (nx,
-// then ny complex), then per warp two buffers of max(nx, ny) complex.
+// then ny complex), then per team two buffers of max(nx, ny) complex.
 inline __host__ __device__ int gen_tw_entries(int nx, int ny) { return (nx + ny + 1) & ~1; }
-inline __host__ __device__ int gen_warp_stride(int nmax) { return 2 * nmax + 2; }  // complex; 16-byte multiple
+inline __host__ __device__ int gen_team_stride(int nmax) { return 2 * nmax + 2; }  // complex; 16-byte multiple
 inline __host__ __device__ size_t gen_smem_bytes(int nx, int ny) {
   const int nmax = nx > ny ? nx : ny;
-  return (static_cast<size_t>(gen_tw_entries(nx, ny)) + static_cast<size_t>(kThreads / 32) * gen_warp_stride(nmax)) *
+  return (static_cast<size_t>(gen_tw_entries(nx, ny)) + static_cast<size_t>(kGenTeams) * gen_team_stride(nmax)) *
          sizeof(float2);
 }
 

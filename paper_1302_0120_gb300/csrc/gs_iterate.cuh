@@ -502,7 +502,7 @@ __device__ __forceinline__ void class_pass(const Params& p, Shared& sh, int base
                                            const TCF& tcf) {
   const bool rows = (f.kind == kInit || f.kind == kRow);
   int per;  // units of one mask
-  if constexpr (LX == 0) per = rows ? p.ny : (p.nx + 7) >> 3;
+  if constexpr (LX == 0) per = rows ? p.ny : (p.nx + kGenTeams - 1) / kGenTeams;
   else per = rows ? p.ny : FieldLayout<LX, LY>::NBLK;
   const int total = per * p.batch;
   const int G = gridDim.x;
