@@ -242,6 +242,20 @@ int gs_status(gs_ctx* c);
 int gs_set_slm_amplitude(gs_ctx* c, const float* amplitude);
 
 /*
+ * gs_set_mask_group -- how many masks of a batched or mixed run are iterated
+ * together (a tuning knob; the paper has no counterpart).
+ *
+ * A batch runs group after group, each group through the whole iteration
+ * schedule of the launch, so that a group's fields (12 bytes per pixel) can
+ * stay in L2; results do not depend on it (phases bit-identical, gaps to
+ * FP64 rounding). masks = 0 (the default) iterates the whole batch (of each
+ * size) together; masks > 0 fixes the group size, capped by the batch. In a
+ * mixed run the sizes always run one after the other. Returns GS_EINVAL for a
+ * NULL context or masks < 0.
+ */
+int gs_set_mask_group(gs_ctx* c, int masks);
+
+/*
  * gs_set_grid -- tuning knob: number of thread blocks of the iteration kernel.
  *
  * ctas = 0 restores the automatic choice. A value above what the device can

@@ -48,6 +48,7 @@ SIGNATURES = {
     "gs_physical_error": (_c_int, [_vp, _vp, _vp, _vp]),
     "gs_create_mixed": (_c_int, [ctypes.POINTER(_vp), _vp, _c_uint, _vp]),
     "gs_run_mixed": (_c_int, [_vp, _vp, _vp, _vp, _c_int, _vp, _vp, _vp]),
+    "gs_set_mask_group": (_c_int, [_vp, _c_int]),
 }
 
 _lib = None
@@ -138,6 +139,11 @@ def gs_run_mixed(ctx: int, batch, target_intensity, phase_in, iters: int, phase_
     b = _arr3(_c_int, [int(x) for x in batch])
     return lib().gs_run_mixed(_vp(ctx), ctypes.cast(b, _vp), ptrs(target_intensity), ptrs(phase_in), int(iters),
                               ptrs(phase_out), ptrs(residual_out), ptrs(object_gap_out))
+
+
+def gs_set_mask_group(ctx: int, masks: int) -> int:
+    """Masks of a batched run iterated together (0: automatic); returns the status code."""
+    return lib().gs_set_mask_group(_vp(ctx), int(masks))
 
 
 def gs_create(nx: int, ny: int, flags: int = GS_FINAL_RESIDUAL, stream: int | None = None) -> int:

@@ -159,6 +159,7 @@ struct gs_ctx {
   int grid_override = 0;
   const float* p_slm = nullptr;  // caller-owned SLM amplitude, or null (p = 1)
   unsigned extra_arrivals = 0;
+  int group_override = 0;  // masks per group of a batched run (0: from the L2 budget)
   Layout L{};
   unsigned char* ws = nullptr;
   double* dres = nullptr;  // device residual staging for gs_run_host
@@ -202,6 +203,15 @@ int choose_grid_for(const gs_ctx* c, long long pixels) {
   if (g > cap) g = cap;
   if (g < 1) g = 1;
   return g;
+}
+
+// Masks iterated together: the whole batch unless the caller fixed a group
+// size. Measured on one GB300 (50 iterations): 8 x 1024^2 is fastest in one
+// group (0.58 ms per mask, 0.65 in groups of 5), 16 x 1024^2 in groups of 8
+// (0.58 vs 0.62 in one group), 64 mixed masks in one group per size.
+int group_size(const gs_ctx* c, int batch) {
+  const int g = c->group_override > 0 ? c->group_override : batch;
+  return g < batch ? g : batch;
 }
 
 int choose_grid(const gs_ctx* c) {
@@ -337,6 +347,7 @@ int gs_run_batched(gs_ctx* c, int batch, const float* target_intensity, const fl
   p.final_resid = (c->flags & GS_FINAL_RESIDUAL) ? 1 : 0;
   p.extra_arrivals = c->extra_arrivals;
   p.tensor_core = (c->flags & GS_TENSOR_CORE) ? 1 : 0;
+  p.group = group_size(c, batch);
   const double n = static_cast<double>(c->nx) * c->ny;
   p.inv_sqrt_n = static_cast<float>(1.0 / std::sqrt(n));
   p.inv_n = 1.0 / n;
@@ -464,6 +475,7 @@ int gs_run_mixed(gs_ctx* c, const int* batch, const float* const* target_intensi
     p.init_target = from_target ? 1 : 0;
     p.extra_arrivals = c->extra_arrivals;
     p.tensor_core = (c->flags & GS_TENSOR_CORE) ? 1 : 0;
+    p.group = group_size(c, batch[k] > 0 ? batch[k] : 1);
     p.inv_sqrt_n = static_cast<float>(1.0 / n);
     p.inv_n = 1.0 / (static_cast<double>(n) * n);
     p.bar = reinterpret_cast<unsigned*>(pw + P.bar);
@@ -636,6 +648,12 @@ int gs_set_slm_amplitude(gs_ctx* c, const float* amplitude) {
 int gs_test_barrier_timeout(gs_ctx* c, int enable) {
   if (c == nullptr || enable < 0) return GS_EINVAL;
   c->extra_arrivals = enable ? 1u : 0u;
+  return GS_OK;
+}
+
+int gs_set_mask_group(gs_ctx* c, int masks) {
+  if (c == nullptr || masks < 0) return GS_EINVAL;
+  c->group_override = masks;
   return GS_OK;
 }
 

@@ -51,6 +51,8 @@ struct Params {
   float inv_sqrt_n;    // 1/sqrt(N)
   double inv_n;        // 1/N
   int tensor_core;     // host side: launch the tensor-core kernel (square 256, 512, 1024)
+  int group;           // masks iterated together, 1..batch: the batch runs group after group
+                       // through the whole schedule, so that a group's fields stay in L2
   // Grids with a side that is not a power of two (gs_general.cuh): the
   // radices of the row and column transforms, 3 bits per stage (code c means
   // radix kRadixOf[c]), first stage in the low bits, and the stage counts.

@@ -491,32 +491,32 @@ static __device__ __forceinline__ PassInfo pass_info(const Params& p, int q0) {
   return f;
 }
 
-// One pass over every valid mask of a class. The work units of all masks
-// (rows, or column blocks) form one sequence split evenly over the blocks,
-// so that small masks of a batch do not leave blocks idle; a block works
-// through its share mask by mask and writes the FP64 partial of each mask's
-// gap to its slot (zero for the masks it does not touch).
+// One pass over the valid masks [w0, w1) of a class. The work units of those
+// masks (rows, or column blocks) form one sequence split evenly over the
+// blocks, so that small masks of a batch do not leave blocks idle; a block
+// works through its share mask by mask and writes the FP64 partial of each
+// mask's gap to its slot (zero for the masks it does not touch).
 template <int LX, int LY, bool HOLD, class TCF>
-__device__ __forceinline__ void class_pass(const Params& p, Shared& sh, int base, const PassInfo& f,
+__device__ __forceinline__ void class_pass(const Params& p, Shared& sh, int base, int w0, int w1, const PassInfo& f,
                                            unsigned char* smem, unsigned& mphase, const StageTw<LX>& tw_rows,
                                            const TCF& tcf) {
   const bool rows = (f.kind == kInit || f.kind == kRow);
   int per;  // units of one mask
   if constexpr (LX == 0) per = rows ? p.ny : (p.nx + kGenTeams - 1) / kGenTeams;
   else per = rows ? p.ny : FieldLayout<LX, LY>::NBLK;
-  const int total = per * p.batch;
+  const int total = per * (w1 - w0);
   const int G = gridDim.x;
   const int lo = split(blockIdx.x, G, total);
   const int hi = split(blockIdx.x + 1, G, total);
-  const int m0 = lo / per;
-  const int m1 = (hi + per - 1) / per;  // masks [m0, m1) meet [lo, hi)
+  const int m0 = w0 + lo / per;
+  const int m1 = w0 + (hi + per - 1) / per;  // masks [m0, m1) meet [lo, hi)
   if (f.slot >= 0 && threadIdx.x == 0)
-    for (int mb = 0; mb < p.batch; ++mb)
+    for (int mb = w0; mb < w1; ++mb)
       if (mb < m0 || mb >= m1) p.partials[(static_cast<size_t>(f.slot) * p.batch + mb) * G + blockIdx.x] = 0.0;
   for (int mb = m0; mb < m1; ++mb) {
     if (sh.bad[base + mb]) continue;
-    const int slo = max(lo, mb * per) - mb * per;
-    const int shi = min(hi, (mb + 1) * per) - mb * per;
+    const int slo = max(lo, (mb - w0) * per) - (mb - w0) * per;
+    const int shi = min(hi, (mb - w0 + 1) * per) - (mb - w0) * per;
     double a;
     if constexpr (LX == 0) {
       a = run_pass_gen(p, mb, f.kind, f.last, slo, shi, smem);
@@ -621,30 +621,33 @@ __global__ void __launch_bounds__(kThreads, 1) gs_iterate(const Params p) {
   __syncthreads();
 
   const int npass = pass_count(p);
-  for (int q0 = 0; q0 < npass; ++q0) {
-    class_pass<LX, LY, kHold>(p, sh, 0, pass_info(p, q0), smem, mphase, tw_rows, tcf);
-    if (!grid_sync(p, target, sh)) {
-      drain_copies(sh);
-      return;
+  const int gsz = p.group > 0 ? p.group : p.batch;
+  for (int w0 = 0; w0 < p.batch; w0 += gsz) {  // mask groups, each through the whole schedule
+    const int w1 = min(p.batch, w0 + gsz);
+    for (int q0 = 0; q0 < npass; ++q0) {
+      class_pass<LX, LY, kHold>(p, sh, 0, w0, w1, pass_info(p, q0), smem, mphase, tw_rows, tcf);
+      if (!grid_sync(p, target, sh)) {
+        drain_copies(sh);
+        return;
+      }
     }
   }
   final_gaps(p, sh, 0);
 }
 
 template <int C, bool TC>
-__device__ __forceinline__ void mixed_class_pass(const MixedParams& mp, Shared& sh, const PassInfo& f,
+__device__ __forceinline__ void mixed_class_pass(const MixedParams& mp, Shared& sh, int w0, int w1, const PassInfo& f,
                                                  unsigned char* smem, unsigned& mphase, const TcStage1& s1,
                                                  const TcStage2<8 << C>& s2) {
   constexpr int L = 8 + C;
   const Params& p = mp.cls[C];
-  if (p.batch == 0) return;
   const int base = (C > 0 ? mp.cls[0].batch : 0) + (C > 1 ? mp.cls[1].batch : 0);
   const StageTw<L> none{};
   if constexpr (TC) {
     const TcFft<L> tcf{s1, s2, reinterpret_cast<const float2*>(smem + kTcTwOffset + C * kTcTwBytes)};
-    class_pass<L, L, false>(p, sh, base, f, smem, mphase, none, tcf);
+    class_pass<L, L, false>(p, sh, base, w0, w1, f, smem, mphase, none, tcf);
   } else {
-    class_pass<L, L, false>(p, sh, base, f, smem, mphase, none, NoTc{});
+    class_pass<L, L, false>(p, sh, base, w0, w1, f, smem, mphase, none, NoTc{});
   }
 }
 
@@ -693,15 +696,24 @@ __global__ void __launch_bounds__(kThreads, 1) gs_iterate_mixed(const MixedParam
   }
   __syncthreads();
 
+  // Mask groups (each class's group size keeps a group's fields in L2), each
+  // through the whole schedule; classes one after the other.
   const int npass = pass_count(p0);
-  for (int q0 = 0; q0 < npass; ++q0) {
-    const PassInfo f = pass_info(p0, q0);
-    mixed_class_pass<0, TC>(mp, sh, f, smem, mphase, s1, s2a);
-    mixed_class_pass<1, TC>(mp, sh, f, smem, mphase, s1, s2b);
-    mixed_class_pass<2, TC>(mp, sh, f, smem, mphase, s1, s2c);
-    if (!grid_sync(p0, target, sh)) {
-      drain_copies(sh);
-      return;
+  for (int c = 0; c < 3; ++c) {
+    const Params& pc = mp.cls[c];
+    const int gsz = pc.group > 0 ? pc.group : pc.batch;
+    for (int w0 = 0; w0 < pc.batch; w0 += gsz) {
+      const int w1 = min(pc.batch, w0 + gsz);
+      for (int q0 = 0; q0 < npass; ++q0) {
+        const PassInfo f = pass_info(p0, q0);
+        if (c == 0) mixed_class_pass<0, TC>(mp, sh, w0, w1, f, smem, mphase, s1, s2a);
+        else if (c == 1) mixed_class_pass<1, TC>(mp, sh, w0, w1, f, smem, mphase, s1, s2b);
+        else mixed_class_pass<2, TC>(mp, sh, w0, w1, f, smem, mphase, s1, s2c);
+        if (!grid_sync(p0, target, sh)) {
+          drain_copies(sh);
+          return;
+        }
+      }
     }
   }
   final_gaps(mp.cls[0], sh, 0);

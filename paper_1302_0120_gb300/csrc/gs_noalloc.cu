@@ -159,6 +159,7 @@ extern "C" int gs_run_noalloc(int nx, int ny, unsigned flags, void* stream, cons
   p.mask_flags = reinterpret_cast<int*>(base + kOffWords) + 3;
   p.ones = reinterpret_cast<const float*>(base + kOffOnes);
   p.batch = 1;
+  p.group = 1;
   p.init_target = from_target ? 1 : 0;
   p.mstride = static_cast<long long>(nx) * ny;
   p.rstride = iters + ((flags & GS_FINAL_RESIDUAL) ? 1 : 0);

@@ -134,6 +134,12 @@ class GerchbergSaxton:
         if rc != B.GS_OK:
             raise B.GSError(rc, "gs_set_grid")
 
+    def set_mask_group(self, masks: int) -> None:
+        """Masks of a batch iterated together (0: automatic, C: gs_set_mask_group)."""
+        rc = B.gs_set_mask_group(self.handle, int(masks))
+        if rc != B.GS_OK:
+            raise B.GSError(rc, "gs_set_mask_group")
+
     @property
     def grid(self) -> int:
         return B.gs_get_grid(self.handle)
@@ -232,6 +238,11 @@ class MixedGerchbergSaxton:
         rc = B.gs_set_grid(self.handle, int(ctas))
         if rc != B.GS_OK:
             raise B.GSError(rc, "gs_set_grid")
+
+    def set_mask_group(self, masks: int) -> None:
+        rc = B.gs_set_mask_group(self.handle, int(masks))
+        if rc != B.GS_OK:
+            raise B.GSError(rc, "gs_set_mask_group")
 
     def close(self) -> None:
         if getattr(self, "handle", None):

@@ -73,3 +73,32 @@ def test_mixed_rejects_one_mask():
         assert gs.status() == GS_ENUMERIC
         r = {n: v[1].cpu().numpy() for n, v in out.items()}
     assert np.all(np.isnan(r[512][1])) and np.all(np.isfinite(r[512][0])) and np.all(np.isfinite(r[256]))
+
+
+@pytest.mark.parametrize("group", [1, 2])
+def test_mask_groups_do_not_change_results(group):
+    """gs_set_mask_group only reorders the work: phases bit-identical, gaps
+    to FP64 rounding."""
+    from paper_1302_0120_gb300 import GerchbergSaxton, MixedGerchbergSaxton, build_lib
+
+    build_lib.build()
+    counts = {256: 3, 512: 2}
+    ms = masks_by_size(counts, 9)
+    T, P = stacked(ms, 0), stacked(ms, 1)
+    res = {}
+    for g in (0, group):
+        with MixedGerchbergSaxton(counts) as gs:
+            gs.set_mask_group(g)
+            out = gs.run(T, P, 7)
+            assert gs.status() == 0
+            res[g] = {n: tuple(x.cpu().numpy() for x in v) for n, v in out.items()}
+        with GerchbergSaxton(512, 512, max_batch=2) as gs1:
+            gs1.set_mask_group(g)
+            ph, r, _ = gs1.run_batched(T[512], P[512], 7)
+            assert gs1.status() == 0
+            res[("single", g)] = (ph.cpu().numpy(), r.cpu().numpy())
+    for n in counts:
+        assert np.array_equal(res[0][n][0], res[group][n][0])
+        assert np.allclose(res[0][n][1], res[group][n][1], rtol=1e-12, atol=0)
+    assert np.array_equal(res[("single", 0)][0], res[("single", group)][0])
+    assert np.allclose(res[("single", 0)][1], res[("single", group)][1], rtol=1e-12, atol=0)
