@@ -368,7 +368,7 @@ def run_gpu(args):
         It *= It.size / It.sum()
         It = torch.from_numpy(It.astype(np.float32)).to(dev)
         ph0 = torch.from_numpy(S.random_phase(1001 + rank, ny, nx)).to(dev)
-        lc = LossContext(nx, stream=stream)
+        lc = LossContext(nx, stream=torch.cuda.Stream(dev))  # its own stream: the Adam step is graph-captured
         optimize_phase(It, ph0, steps=5, lctx=lc)  # warm-up
         torch.cuda.synchronize(dev)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)

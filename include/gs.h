@@ -332,6 +332,27 @@ int gs_loss_grad(gs_ctx* c, const float* target_intensity, const float* phase, d
 int gs_physical_error(gs_ctx* c, const float* target_intensity, const float* phase, double* error_out);
 
 /*
+ * gs_adam_step -- one Adam update of a phase mask from the gradient of the
+ * intensity loss (gs_loss_grad): the optimiser of the differentiable form.
+ * The paper iterates projections and has no optimiser; this is Adam (Kingma
+ * and Ba, 2015) with bias correction, the form torch's Adam computes:
+ *   m = beta1 m + (1 - beta1) g,  v = beta2 v + (1 - beta2) g^2,
+ *   phase -= (lr / (1 - beta1^t)) m / (sqrt(v / (1 - beta2^t)) + eps).
+ *   phase, m, v  device float[n], updated in place (m, v zero before step 1).
+ *   grad         device float[n].
+ *   state        device int[2], zero before step 1: state[0] is the number
+ *                of steps done (t - 1 during the call, t after it), state[1]
+ *                an internal counter; both live on the device, so that the
+ *                call can be captured once in a CUDA graph and replayed.
+ *   lr > 0, 0 <= beta1, beta2 < 1, eps > 0.
+ *   stream       a cudaStream_t or NULL. Asynchronous.
+ * Returns GS_EINVAL for NULL arrays, n < 1 or bad hyperparameters; GS_ECUDA
+ * if the launch fails.
+ */
+int gs_adam_step(float* phase, const float* grad, float* m, float* v, long long n, int* state, float lr,
+                 float beta1, float beta2, float eps, void* stream);
+
+/*
  * gs_run_noalloc -- gs_run without a context and without any allocation.
  *
  * The paper has no counterpart: this entry point exists for callers that may

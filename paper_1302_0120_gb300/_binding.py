@@ -49,6 +49,8 @@ SIGNATURES = {
     "gs_create_mixed": (_c_int, [ctypes.POINTER(_vp), _vp, _c_uint, _vp]),
     "gs_run_mixed": (_c_int, [_vp, _vp, _vp, _vp, _c_int, _vp, _vp, _vp]),
     "gs_set_mask_group": (_c_int, [_vp, _c_int]),
+    "gs_adam_step": (_c_int, [_vp, _vp, _vp, _vp, ctypes.c_longlong, _vp, ctypes.c_float, ctypes.c_float,
+                              ctypes.c_float, ctypes.c_float, _vp]),
 }
 
 _lib = None
@@ -139,6 +141,13 @@ def gs_run_mixed(ctx: int, batch, target_intensity, phase_in, iters: int, phase_
     b = _arr3(_c_int, [int(x) for x in batch])
     return lib().gs_run_mixed(_vp(ctx), ctypes.cast(b, _vp), ptrs(target_intensity), ptrs(phase_in), int(iters),
                               ptrs(phase_out), ptrs(residual_out), ptrs(object_gap_out))
+
+
+def gs_adam_step(phase: int, grad: int, m: int, v: int, n: int, state: int, lr: float, beta1: float, beta2: float,
+                 eps: float, stream: int | None = None) -> int:
+    """Enqueue one Adam update on device pointers; returns the status code."""
+    return lib().gs_adam_step(_vp(phase), _vp(grad), _vp(m), _vp(v), int(n), _vp(state), float(lr), float(beta1),
+                              float(beta2), float(eps), _vp(stream or 0))
 
 
 def gs_set_mask_group(ctx: int, masks: int) -> int:

@@ -182,13 +182,7 @@ __device__ __forceinline__ void gen_build_amplitude(const Params& p, int mb, flo
   __syncthreads();
 }
 
-// Asynchronous 8-byte copy global -> shared (cp.async); completed for the
-// issuing thread by cp_async_wait_all.
-__device__ __forceinline__ void cp_async8(void* dst, const void* src) {
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
-}
 
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 // Wrap an angle as the power-of-two kernel does: (-pi, pi].
 __device__ __forceinline__ float gen_phase(float2 u) {

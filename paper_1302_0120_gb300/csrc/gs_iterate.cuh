@@ -144,14 +144,23 @@ __device__ __forceinline__ double run_pass(const Params& p, int mb, int kind, bo
       if (kind == kInit) {
         // exp(i phi) once per run: a rolled loop through the group's exchange
         // buffer keeps a single copy of sincosf (and atan2f) in the kernel.
+        // phi (and p) arrive there first by cp.async, all 32 loads in flight.
         const float* ph = p.phi_in + moff + static_cast<size_t>(ridx) * N + t;
         float2* su = grp.sm + t;
         const float* pp = p.p_slm ? p.p_slm + static_cast<size_t>(ridx) * N + t : nullptr;
+#pragma unroll
+        for (int i = 0; i < 32; ++i) cp_async4(&su[T * i].x, ph + T * i);
+        if (pp) {
+#pragma unroll
+          for (int i = 0; i < 32; ++i) cp_async4(&su[T * i].y, pp + T * i);
+        }
+        cp_async_wait_all();
 #pragma unroll 1
         for (int i = 0; i < 32; ++i) {
           float s, c;
-          sincosf(ph[T * i], &s, &c);
-          const float a = pp ? pp[T * i] : 1.f;  // u0 = p exp(i phi0)
+          const float2 fa = su[T * i];
+          sincosf(fa.x, &s, &c);
+          const float a = pp ? fa.y : 1.f;  // u0 = p exp(i phi0)
           su[T * i] = make_float2(a * c, a * s);
         }
         if (last && valid) {  // zero iterations: the mask is arg exp(i phi^0)
@@ -169,6 +178,14 @@ __device__ __forceinline__ double run_pass(const Params& p, int mb, int kind, bo
       } else {
 #pragma unroll
         for (int i = 0; i < 32; ++i) v[i] = Bm[L::off(ridx, t + T * i)];
+        if (kind == kRow && p.p_slm != nullptr) {
+          // the laser amplitude of this row, prefetched into the (free in
+          // row passes) field staging buffer behind the first transform
+          float* sp = reinterpret_cast<float*>(smem + kBlockSmemOffset) + threadIdx.x;
+          const float* pp = p.p_slm + static_cast<size_t>(ridx) * N + t;
+#pragma unroll
+          for (int i = 0; i < 32; ++i) cp_async4(sp + kThreads * i, pp + T * i);
+        }
       }
 
       float part = 0.f;
@@ -194,12 +211,13 @@ __device__ __forceinline__ double run_pass(const Params& p, int mb, int kind, bo
           // through the group's exchange buffer keeps this variant out of the
           // unrolled hot code.
           float2* su = grp.sm + t;
-          const float* pp = p.p_slm + static_cast<size_t>(ridx) * N + t;
+          const float* sp = reinterpret_cast<const float*>(smem + kBlockSmemOffset) + threadIdx.x;
 #pragma unroll
           for (int i = 0; i < 32; ++i) su[T * i] = v[i];
+          cp_async_wait_all();
 #pragma unroll 1
           for (int i = 0; i < 32; ++i) {
-            const float a = pp[T * i];
+            const float a = sp[kThreads * i];
             const float2 w = su[T * i];
             const float vx = w.y;
             const float vy = w.x;

@@ -101,11 +101,18 @@ __global__ void __launch_bounds__(kThreads, 1) gs_loss_kernel(const LossParams p
     bool bad = false;
     double sum_i = 0.0;
     float max_i = 0.f;
-    for (int e = threadIdx.x; e < (r1 - r0) * N; e += kThreads) {
-      const float x = p.I[static_cast<size_t>(r0) * N + e];
-      bad |= !(fabsf(x) <= FLT_MAX);
-      sum_i += static_cast<double>(x);
-      max_i = fmaxf(max_i, x);
+    const float* Ib = p.I + static_cast<size_t>(r0) * N;
+    const int cnt = (r1 - r0) * N;
+    for (int e0 = threadIdx.x; e0 < cnt; e0 += 8 * kThreads) {
+      float xs[8];  // eight loads in flight before they are used
+#pragma unroll
+      for (int u = 0; u < 8; ++u) xs[u] = (e0 + u * kThreads < cnt) ? Ib[e0 + u * kThreads] : 0.f;
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        bad |= !(fabsf(xs[u]) <= FLT_MAX);
+        sum_i += static_cast<double>(xs[u]);
+        max_i = fmaxf(max_i, xs[u]);
+      }
     }
     const int any_bad = __syncthreads_or(bad);
     const double bsum = block_sum(sum_i, sh);
@@ -132,8 +139,9 @@ __global__ void __launch_bounds__(kThreads, 1) gs_loss_kernel(const LossParams p
       for (int e = threadIdx.x; e < N * W; e += kThreads) {
         const int k = e & (W - 1);
         const int y = e >> L::LW;
-        tb[y * (W + 1) + k] = p.I[static_cast<size_t>(y) * N + cb * W + k];
+        cp_async4(tb + y * (W + 1) + k, p.I + static_cast<size_t>(y) * N + cb * W + k);
       }
+      cp_async_wait_all();
       __syncthreads();
       for (int e = threadIdx.x; e < N * W; e += kThreads) {
         const int k = e >> LN;
@@ -155,11 +163,20 @@ __global__ void __launch_bounds__(kThreads, 1) gs_loss_kernel(const LossParams p
       const float* ph = p.phi + static_cast<size_t>(ridx) * N + t;
       const float* pp = p.p_slm ? p.p_slm + static_cast<size_t>(ridx) * N + t : nullptr;
       float2* su = grp.sm + t;
+      // phi (and p) by cp.async, all loads in flight, then a rolled loop
+#pragma unroll
+      for (int i = 0; i < 32; ++i) cp_async4(&su[T * i].x, ph + T * i);
+      if (pp) {
+#pragma unroll
+        for (int i = 0; i < 32; ++i) cp_async4(&su[T * i].y, pp + T * i);
+      }
+      cp_async_wait_all();
 #pragma unroll 1
       for (int i = 0; i < 32; ++i) {
         float s, c;
-        sincosf(ph[T * i], &s, &c);
-        const float a = pp ? pp[T * i] : 1.f;
+        const float2 fa = su[T * i];
+        sincosf(fa.x, &s, &c);
+        const float a = pp ? fa.y : 1.f;
         su[T * i] = make_float2(a * c, a * s);
       }
 #pragma unroll
@@ -329,20 +346,33 @@ __global__ void __launch_bounds__(kThreads, 1) gs_loss_kernel(const LossParams p
       float2 v[32];
 #pragma unroll
       for (int i = 0; i < 32; ++i) v[i] = p.B[L::off(ridx, t + T * i)];
+      // phi (and p) of this row by cp.async into the field staging buffer
+      // (free in this pass), in flight behind the transform
+      float* sph = reinterpret_cast<float*>(blk) + threadIdx.x;
+      float* spp = sph + 32 * kThreads;
+      {
+        const float* ph = p.phi + static_cast<size_t>(ridx) * N + t;
+#pragma unroll
+        for (int i = 0; i < 32; ++i) cp_async4(sph + kThreads * i, ph + T * i);
+        if (p.p_slm) {
+          const float* pp = p.p_slm + static_cast<size_t>(ridx) * N + t;
+#pragma unroll
+          for (int i = 0; i < 32; ++i) cp_async4(spp + kThreads * i, pp + T * i);
+        }
+      }
       group_fft<LN>(v, grp, stw);  // = swap(N z)
       // Im(conj(x) z) = x.re z.im - x.im z.re, with z = (v.y, v.x) / N
       float2* su = grp.sm + t;
 #pragma unroll
       for (int i = 0; i < 32; ++i) su[T * i] = v[i];
+      cp_async_wait_all();
       if (valid) {
-        const float* ph = p.phi + static_cast<size_t>(idx) * N + t;
-        const float* pp = p.p_slm ? p.p_slm + static_cast<size_t>(idx) * N + t : nullptr;
         float* gr = p.grad + static_cast<size_t>(idx) * N + t;
 #pragma unroll 1
         for (int i = 0; i < 32; ++i) {
           float s, c;
-          sincosf(ph[T * i], &s, &c);
-          const float a = pp ? pp[T * i] : 1.f;  // x = p exp(i phi)
+          sincosf(sph[kThreads * i], &s, &c);
+          const float a = p.p_slm ? spp[kThreads * i] : 1.f;  // x = p exp(i phi)
           const float2 w = su[T * i];
           gr[T * i] = scale * a * (c * w.x - s * w.y);
         }

@@ -6,7 +6,9 @@
 Both the loss and its gradient come from one launch of the library
 (gs_loss_grad): the gradient is produced by the adjoint passes in the forward
 call and scaled by the incoming gradient in ``backward``. Adam itself is
-torch's optimiser acting on the phase tensor.
+torch's optimiser acting on the phase tensor there; ``optimize_phase``
+replays one step (loss-and-gradient launch plus the library's Adam update) as
+a CUDA graph.
 """
 
 from __future__ import annotations
@@ -88,12 +90,63 @@ def intensity_loss(phase, target, lctx: LossContext):
 
 
 def optimize_phase(target, phase0, steps: int = 200, lr: float = 0.05, betas=(0.9, 0.999), eps: float = 1e-8,
-                   lctx: LossContext | None = None, record_every: int = 1):
+                   lctx: LossContext | None = None, record_every: int = 1, graph: bool = True):
     """Adam on the phase. Returns (phase, losses) with losses[k] the loss
-    before step k (and the final loss last)."""
+    before step k (and the final loss last).
+
+    With ``graph`` (the default) one step -- the loss-and-gradient launch and
+    the library's Adam update (gs_adam_step) -- is captured once as a CUDA
+    graph and replayed after three eager steps; the context then needs its own
+    (non-default) stream, and one is created when ``lctx`` is None. Otherwise
+    every step goes through the autograd function above and torch's Adam."""
     import torch
 
-    lctx = lctx or LossContext(phase0.shape[-1])
+    if lctx is None:
+        lctx = LossContext(phase0.shape[-1], stream=torch.cuda.Stream() if graph else None)
+    if not graph or lctx.stream.cuda_stream == 0 or steps < 4:
+        return _optimize_eager(target, phase0, steps, lr, betas, eps, lctx, record_every)
+    s = lctx.stream
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        phase = phase0.detach().clone()
+        grad = torch.zeros_like(phase)
+        m = torch.zeros_like(phase)
+        v = torch.zeros_like(phase)
+        state = torch.zeros(2, dtype=torch.int32, device=phase.device)
+        loss = torch.zeros(1, dtype=torch.float64, device=phase.device)
+        record = torch.zeros(steps + 1, dtype=torch.float64, device=phase.device)
+
+        def step():
+            rc = B.gs_loss_grad(lctx.handle, target.data_ptr(), phase.data_ptr(), loss.data_ptr(), grad.data_ptr())
+            if rc != B.GS_OK:
+                raise B.GSError(rc, "gs_loss_grad")
+            rc = B.gs_adam_step(phase.data_ptr(), grad.data_ptr(), m.data_ptr(), v.data_ptr(), phase.numel(),
+                                state.data_ptr(), lr, betas[0], betas[1], eps, s.cuda_stream)
+            if rc != B.GS_OK:
+                raise B.GSError(rc, "gs_adam_step")
+
+        warm = 3
+        for k in range(warm):
+            step()
+            record[k].copy_(loss[0])
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=s):
+            step()
+        for k in range(warm, steps):
+            g.replay()
+            record[k].copy_(loss[0])
+        rc = B.gs_loss_grad(lctx.handle, target.data_ptr(), phase.data_ptr(), loss.data_ptr(), 0)
+        if rc != B.GS_OK:
+            raise B.GSError(rc, "gs_loss_grad")
+        record[steps].copy_(loss[0])
+    torch.cuda.current_stream().wait_stream(s)
+    keep = list(range(0, steps, record_every)) + [steps]
+    return phase.detach(), record.cpu().numpy()[keep]
+
+
+def _optimize_eager(target, phase0, steps, lr, betas, eps, lctx, record_every):
+    import torch
+
     phase = phase0.detach().clone().requires_grad_(True)
     opt = torch.optim.Adam([phase], lr=lr, betas=betas, eps=eps)
     losses = []
