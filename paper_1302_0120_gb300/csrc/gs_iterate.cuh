@@ -148,10 +148,11 @@ __device__ __forceinline__ double run_pass(const Params& p, int mb, int kind, bo
         const float* ph = p.phi_in + moff + static_cast<size_t>(ridx) * N + t;
         float2* su = grp.sm + t;
         const float* pp = p.p_slm ? p.p_slm + static_cast<size_t>(ridx) * N + t : nullptr;
-#pragma unroll
+        // rolled: the copies do not wait, so all of them are in flight anyway
+#pragma unroll 1
         for (int i = 0; i < 32; ++i) cp_async4(&su[T * i].x, ph + T * i);
         if (pp) {
-#pragma unroll
+#pragma unroll 1
           for (int i = 0; i < 32; ++i) cp_async4(&su[T * i].y, pp + T * i);
         }
         cp_async_wait_all();
@@ -183,7 +184,7 @@ __device__ __forceinline__ double run_pass(const Params& p, int mb, int kind, bo
           // row passes) field staging buffer behind the first transform
           float* sp = reinterpret_cast<float*>(smem + kBlockSmemOffset) + threadIdx.x;
           const float* pp = p.p_slm + static_cast<size_t>(ridx) * N + t;
-#pragma unroll
+#pragma unroll 1
           for (int i = 0; i < 32; ++i) cp_async4(sp + kThreads * i, pp + T * i);
         }
       }
@@ -522,15 +523,23 @@ __device__ __forceinline__ void class_pass(const Params& p, Shared& sh, int base
   int per;  // units of one mask
   if constexpr (LX == 0) per = rows ? p.ny : (p.nx + kGenTeams - 1) / kGenTeams;
   else per = rows ? p.ny : FieldLayout<LX, LY>::NBLK;
-  const int total = per * (w1 - w0);
   const int G = gridDim.x;
-  const int lo = split(blockIdx.x, G, total);
-  const int hi = split(blockIdx.x + 1, G, total);
-  const int m0 = w0 + lo / per;
-  const int m1 = w0 + (hi + per - 1) / per;  // masks [m0, m1) meet [lo, hi)
-  if (f.slot >= 0 && threadIdx.x == 0)
-    for (int mb = w0; mb < w1; ++mb)
-      if (mb < m0 || mb >= m1) p.partials[(static_cast<size_t>(f.slot) * p.batch + mb) * G + blockIdx.x] = 0.0;
+  int lo, hi, m0, m1;
+  if (w1 - w0 == 1) {  // one mask: its own share, no mask boundaries
+    lo = split(blockIdx.x, G, per);
+    hi = split(blockIdx.x + 1, G, per);
+    m0 = w0;
+    m1 = w1;
+  } else {
+    const int total = per * (w1 - w0);
+    lo = split(blockIdx.x, G, total);
+    hi = split(blockIdx.x + 1, G, total);
+    m0 = w0 + lo / per;
+    m1 = w0 + (hi + per - 1) / per;  // masks [m0, m1) meet [lo, hi)
+    if (f.slot >= 0 && threadIdx.x == 0)
+      for (int mb = w0; mb < w1; ++mb)
+        if (mb < m0 || mb >= m1) p.partials[(static_cast<size_t>(f.slot) * p.batch + mb) * G + blockIdx.x] = 0.0;
+  }
   for (int mb = m0; mb < m1; ++mb) {
     if (sh.bad[base + mb]) continue;
     const int slo = max(lo, (mb - w0) * per) - (mb - w0) * per;
