@@ -346,18 +346,6 @@ def run_gpu(args):
                    "ms_per_mask": round(bper / nb, 4), "masks_per_s": round(1e3 * nb / bper, 1)}
         gsb.close()
 
-    # serving: a Poisson stream of 512^2 / 1024^2 requests (30 warm-started
-    # iterations each) through the continuous-batching loop
-    serving = None
-    if args.serve_seconds > 0 and ws == 1:
-        from paper_1302_0120_gb300 import serving as SV
-
-        summ, _, ex = SV.run_service(rate_hz=args.serve_rate, seconds=args.serve_seconds, sizes=(512, 1024),
-                                     lanes=(1, 2), iters=30, warmup_s=0.3)
-        ex.close()
-        serving = {k: (round(v, 4) if isinstance(v, float) else v) for k, v in summ.items() if k != "lanes"}
-        serving["lanes"] = [f"{p['name']} batch<={p['max_batch']} grid={p['grid']}" for p in summ["lanes"]]
-
     # differentiable form: 1024^2 phase, 100-spot target with sum I = N,
     # 200 Adam steps (loss + hand-written adjoint + torch Adam per step)
     differentiable = None
@@ -385,6 +373,19 @@ def run_gpu(args):
                               60 * n * args.adam_steps / (e0.elapsed_time(e1) * 1e6), 1),
                           "loss_first": float(losses[0]), "loss_last": float(losses[-1])}
         lc.close()
+
+    # serving: a Poisson stream of 512^2 / 1024^2 requests (30 warm-started
+    # iterations each) through the continuous-batching loop
+    serving = None
+    if args.serve_seconds > 0 and ws == 1:
+        from paper_1302_0120_gb300 import serving as SV
+
+        summ, sch, ex = SV.run_service(rate_hz=args.serve_rate, seconds=args.serve_seconds, sizes=(512, 1024),
+                                       lanes=(1, 2), iters=30, warmup_s=0.3)
+        ex.close()
+        del sch, ex  # the finished requests hold their targets
+        serving = {k: (round(v, 4) if isinstance(v, float) else v) for k, v in summ.items() if k != "lanes"}
+        serving["lanes"] = [f"{p['name']} batch<={p['max_batch']} grid={p['grid']}" for p in summ["lanes"]]
 
     def timed(fn, steps):
         """Mean device ms of fn() over `steps` launches, L2 flushed before each."""
