@@ -32,7 +32,7 @@ if ROOT not in sys.path:
 WORKLOAD = "spots1024"
 METRIC = "ms per 1024² phase mask (100 GS iters) at matched residual; p99 latency"
 UNIT = "ms/mask"
-# Algorithmic DRAM bytes per pixel of one mask of K iterations (see DESIGN.md):
+# Algorithmic DRAM bytes per pixel of one mask of K iterations:
 # A0 read I (4); amplitude: read I (4) + write m (4); init: read phi (4) + write B (8);
 # per iteration 36 (column pass 20, row pass 16); phase out (4); final residual pass 12.
 BYTES_PER_PX_FIXED = 4 + 8 + 12 + 4 + 12

@@ -48,7 +48,9 @@ void radix_plan(int n, unsigned* plan, int* nst) {
   while (n % 8 == 0) { r.push_back(8); n /= 8; }
   if (n == 4) r.push_back(4);
   if (n == 2) r.push_back(2);
-  unsigned code = 0;
+  unsigned code = 0;  // 3 bits per stage; 5-smooth sides up to kMaxGeneralSide need at most 7 stages
+  static_assert(3 * gsk::kMaxGeneralStages <= 32, "stage codes fit the plan word");
+  if (r.size() > static_cast<size_t>(gsk::kMaxGeneralStages)) r.resize(0);  // unreachable for valid sides
   for (size_t s = 0; s < r.size(); ++s) {
     const unsigned c = r[s] == 2 ? 0u : r[s] == 3 ? 1u : r[s] == 4 ? 2u : r[s] == 5 ? 3u : 4u;
     code |= c << (3 * s);
