@@ -43,13 +43,15 @@ FLOPS_PROJ_PER_PX = 20
 
 
 def kernel_sources_sha() -> str:
-    """Hash of the CUDA sources and the ABI header (identifies the kernel build)."""
+    """Hash of the device-code sources of the iteration kernels (the headers
+    and the instantiation units; host-only files do not change the kernel)."""
     import glob
     import hashlib
 
+    csrc = os.path.join(ROOT, "paper_1302_0120_gb300", "csrc")
     h = hashlib.sha256()
-    for f in sorted(glob.glob(os.path.join(ROOT, "paper_1302_0120_gb300", "csrc", "*"))) + [
-            os.path.join(ROOT, "include", "gs.h")]:
+    for f in sorted(glob.glob(os.path.join(csrc, "*.cuh")) + glob.glob(os.path.join(csrc, "*_inst.cu")) +
+                    [os.path.join(csrc, "gs_internal.h"), os.path.join(ROOT, "include", "gs.h")]):
         h.update(os.path.basename(f).encode())
         with open(f, "rb") as fh:
             h.update(fh.read())
