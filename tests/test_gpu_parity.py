@@ -211,3 +211,31 @@ def test_run_host_matches_device_run():
     with GerchbergSaxton(512, 512) as gs:
         ph, r, g = gs.run_host(I, phi0, 5)
     assert np.array_equal(ph, dev[0]) and np.array_equal(r, dev[1]) and np.array_equal(g, dev[2])
+
+
+@pytest.mark.parametrize("iters", [0, 5, 130])
+def test_run_host_pinned_buffers(iters):
+    """Pinned host buffers (the asynchronous-copy path of the bench's e2e
+    figure): the results are those of a device run, call after call,
+    including zero iterations and a run of two launches."""
+    import torch
+
+    from paper_1302_0120_gb300 import GerchbergSaxton
+    from paper_1302_0120_gb300 import _binding as B
+
+    I, phi0, _ = S.workload("spots512")
+    dev = gpu_gs(I, phi0, iters)
+    pI = torch.from_numpy(I).pin_memory()
+    pP = torch.from_numpy(phi0).pin_memory()
+    pO = torch.full_like(pP, 7.0).pin_memory()
+    r = np.empty(iters + 1)
+    g = np.empty(max(iters, 1))
+    with GerchbergSaxton(512, 512) as gs:
+        for _ in range(2):
+            rc = B.gs_run_host(gs.handle, pI.data_ptr(), pP.data_ptr(), iters, pO.data_ptr(), r.ctypes.data,
+                               g.ctypes.data)
+            assert rc == 0
+            assert np.array_equal(pO.numpy(), dev[0]) and np.array_equal(r, dev[1])
+            if iters:
+                assert np.array_equal(g[:iters], dev[2])
+            pO.fill_(7.0)
