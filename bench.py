@@ -402,6 +402,26 @@ def run_gpu(args):
         torch.cuda.synchronize(dev)
         return statistics.mean(a_.elapsed_time(b_) for a_, b_ in ev)
 
+    # one traced run of the headline workload (outside the timed region):
+    # per-pass work of the slowest block and barrier latency, medians over the
+    # column and the row passes
+    pass_trace = None
+    if ws == 1:
+        from paper_1302_0120_gb300 import _binding as BT
+
+        BT.gs_set_trace(gs.handle, True)
+        flush.zero_()
+        step()
+        if gs.status() != 0:
+            raise RuntimeError("traced run failed")
+        work_us, barrier_us = BT.pass_times(BT.gs_get_trace(gs.handle))
+        BT.gs_set_trace(gs.handle, False)
+        col, row = slice(1, 2 * iters + 1, 2), slice(2, 2 * iters + 1, 2)  # pass 0 is the init row pass
+        pass_trace = {"column_pass_work_us": round(float(np.median(work_us[col])), 2),
+                      "row_pass_work_us": round(float(np.median(work_us[row])), 2),
+                      "barrier_us": round(float(np.median(barrier_us[1:2 * iters + 1])), 2),
+                      "passes": int(work_us.shape[0])}
+
     # tensor-core form (FP16 DFT-matrix products, FP32 accumulation) on the
     # same workload: time per mask and the final residual against the FP32 one
     tensor_core = None
@@ -579,6 +599,7 @@ def run_gpu(args):
         "batched_throughput": batched,
         "serving": serving,
         "differentiable": differentiable,
+        "pass_trace": pass_trace,
         "tensor_core": tensor_core,
         "paper_800x600": paper_800x600,
         "mixed64": mixed64,

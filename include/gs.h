@@ -242,6 +242,32 @@ int gs_status(gs_ctx* c);
 int gs_set_slm_amplitude(gs_ctx* c, const float* amplitude);
 
 /*
+ * gs_set_trace -- record per-pass timestamps of later runs (a diagnostic; the
+ * paper reports per-iteration timings of its own FFT and constraint steps,
+ * Sec. V, this is their counterpart for the fused passes).
+ *
+ * With enable != 0 every launch of gs_run / gs_run_batched on this context
+ * writes, for each block, the globaltimer (ns) at the launch start and, for
+ * each pass, when the block finished its work and when the grid barrier
+ * released it. The record lives in the workspace; gs_get_trace reads the
+ * last launch's. Costs two stores per pass and block. Returns GS_EINVAL for
+ * a NULL or mixed context or enable < 0.
+ */
+int gs_set_trace(gs_ctx* c, int enable);
+
+/*
+ * gs_get_trace -- the timestamps of the last traced launch.
+ *
+ * Synchronises the context stream and copies (passes + 1) x grid pairs of
+ * unsigned 64-bit nanosecond stamps to host_out, row-major: row 0 holds each
+ * block's launch start (twice), row 1 + q pass q's (work done, released) per
+ * block. *passes and *grid receive the shape (0 if nothing was traced).
+ * Returns GS_EINVAL for NULL pointers, a mixed context or a capacity (in
+ * stamps) below 2 (passes + 1) grid; GS_ECUDA on a CUDA error.
+ */
+int gs_get_trace(gs_ctx* c, unsigned long long* host_out, int capacity, int* passes, int* grid);
+
+/*
  * gs_set_mask_group -- how many masks of a batched or mixed run are iterated
  * together (a tuning knob; the paper has no counterpart).
  *

@@ -49,6 +49,8 @@ SIGNATURES = {
     "gs_create_mixed": (_c_int, [ctypes.POINTER(_vp), _vp, _c_uint, _vp]),
     "gs_run_mixed": (_c_int, [_vp, _vp, _vp, _vp, _c_int, _vp, _vp, _vp]),
     "gs_set_mask_group": (_c_int, [_vp, _c_int]),
+    "gs_set_trace": (_c_int, [_vp, _c_int]),
+    "gs_get_trace": (_c_int, [_vp, _vp, _c_int, ctypes.POINTER(_c_int), ctypes.POINTER(_c_int)]),
     "gs_adam_step": (_c_int, [_vp, _vp, _vp, _vp, ctypes.c_longlong, _vp, ctypes.c_float, ctypes.c_float,
                               ctypes.c_float, ctypes.c_float, _vp]),
 }
@@ -148,6 +150,40 @@ def gs_adam_step(phase: int, grad: int, m: int, v: int, n: int, state: int, lr: 
     """Enqueue one Adam update on device pointers; returns the status code."""
     return lib().gs_adam_step(_vp(phase), _vp(grad), _vp(m), _vp(v), int(n), _vp(state), float(lr), float(beta1),
                               float(beta2), float(eps), _vp(stream or 0))
+
+
+def gs_set_trace(ctx: int, enable: bool) -> int:
+    """Record pass timestamps of later runs; returns the status code."""
+    return lib().gs_set_trace(_vp(ctx), 1 if enable else 0)
+
+
+def gs_get_trace(ctx: int):
+    """The last traced launch as a numpy uint64 array [passes + 1, grid, 2]
+    (row 0: launch start; row 1 + q: pass q done, released). Raises GSError."""
+    import numpy as np
+
+    cap = 2 * (2 * 128 + 5) * 256
+    buf = np.zeros(cap, dtype=np.uint64)
+    passes, grid = _c_int(0), _c_int(0)
+    rc = lib().gs_get_trace(_vp(ctx), _vp(buf.ctypes.data), cap, ctypes.byref(passes), ctypes.byref(grid))
+    if rc != GS_OK:
+        raise GSError(rc, "gs_get_trace")
+    return buf[: 2 * (passes.value + 1) * grid.value].reshape(passes.value + 1, grid.value, 2)
+
+
+def pass_times(trace):
+    """Per pass (microseconds): the slowest block's work (from its release by
+    the previous barrier, or the launch start, to its arrival) and the
+    barrier latency (last arrival to the median release)."""
+    import numpy as np
+
+    t = trace.astype(np.float64)
+    prev = t[:-1, :, 1]
+    done = t[1:, :, 0]
+    rel = t[1:, :, 1]
+    work = (done - prev).max(axis=1) / 1e3
+    barrier = (np.median(rel, axis=1) - done.max(axis=1)) / 1e3
+    return work, barrier
 
 
 def gs_set_mask_group(ctx: int, masks: int) -> int:

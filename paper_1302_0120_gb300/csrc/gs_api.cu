@@ -70,7 +70,7 @@ constexpr int kTwiddleEntries = 31 * 32 + 31 * 1024;
 
 // Offsets of the sub-buffers of one workspace allocation.
 struct Layout {
-  size_t B, mT, partials, twx, twy, ones, bar, status, abort_flag, mask_flags, energy, lossbuf, dI, dphi, total;
+  size_t B, mT, partials, twx, twy, ones, bar, status, abort_flag, mask_flags, energy, lossbuf, dI, dphi, trace, total;
 };
 
 Layout make_layout(int nx, int ny, int max_batch) {
@@ -93,6 +93,7 @@ Layout make_layout(int nx, int ny, int max_batch) {
   L.lossbuf = o;    o = align_up(o + sizeof(double));
   L.dI = o;         o = align_up(o + n * sizeof(float));
   L.dphi = o;       o = align_up(o + n * sizeof(float));
+  L.trace = o;      o = align_up(o + static_cast<size_t>(gsk::kTraceRows) * gsk::kMaxGrid * 2 * sizeof(unsigned long long));
   L.total = o;
   return L;
 }
@@ -161,7 +162,9 @@ struct gs_ctx {
   int grid_override = 0;
   const float* p_slm = nullptr;  // caller-owned SLM amplitude, or null (p = 1)
   unsigned extra_arrivals = 0;
-  int group_override = 0;  // masks per group of a batched run (0: from the L2 budget)
+  int group_override = 0;  // masks per group of a batched run (0: the whole batch)
+  bool trace = false;      // record pass timestamps (gs_set_trace)
+  int trace_grid = 0, trace_passes = 0;  // shape of the last traced launch
   Layout L{};
   unsigned char* ws = nullptr;
   double* dres = nullptr;  // device residual staging for gs_run_host
@@ -350,6 +353,7 @@ int gs_run_batched(gs_ctx* c, int batch, const float* target_intensity, const fl
   p.extra_arrivals = c->extra_arrivals;
   p.tensor_core = (c->flags & GS_TENSOR_CORE) ? 1 : 0;
   p.group = group_size(c, batch);
+  p.trace = c->trace ? at<unsigned long long>(c, c->L.trace) : nullptr;
   const double n = static_cast<double>(c->nx) * c->ny;
   p.inv_sqrt_n = static_cast<float>(1.0 / std::sqrt(n));
   p.inv_n = 1.0 / n;
@@ -372,6 +376,11 @@ int gs_run_batched(gs_ctx* c, int batch, const float* target_intensity, const fl
     }
     it0 = it1;
   } while (it0 < iters);
+  if (c->trace) {  // the shape of the last launch's record
+    c->trace_grid = grid;
+    c->trace_passes = (p.do_init ? (p.init_target ? 2 : 1) : 0) + 2 * (p.it1 - p.it0) +
+                      ((p.do_final && p.final_resid) ? 1 : 0);
+  }
   return GS_OK;
 }
 
@@ -650,6 +659,31 @@ int gs_set_slm_amplitude(gs_ctx* c, const float* amplitude) {
 int gs_test_barrier_timeout(gs_ctx* c, int enable) {
   if (c == nullptr || enable < 0) return GS_EINVAL;
   c->extra_arrivals = enable ? 1u : 0u;
+  return GS_OK;
+}
+
+int gs_set_trace(gs_ctx* c, int enable) {
+  if (c == nullptr || enable < 0 || c->mixed) return GS_EINVAL;
+  c->trace = enable != 0;
+  return GS_OK;
+}
+
+int gs_get_trace(gs_ctx* c, unsigned long long* host_out, int capacity, int* passes, int* grid) {
+  if (c == nullptr || host_out == nullptr || passes == nullptr || grid == nullptr || capacity < 0 || c->mixed)
+    return GS_EINVAL;
+  if (cudaStreamSynchronize(c->stream) != cudaSuccess) {
+    cudaGetLastError();
+    return GS_ECUDA;
+  }
+  *passes = c->trace_passes;
+  *grid = c->trace_grid;
+  const long long need = 2LL * (c->trace_passes + 1) * c->trace_grid;
+  if (need > capacity) return GS_EINVAL;
+  if (need > 0 && cudaMemcpy(host_out, at<unsigned long long>(c, c->L.trace), need * sizeof(unsigned long long),
+                             cudaMemcpyDeviceToHost) != cudaSuccess) {
+    cudaGetLastError();
+    return GS_ECUDA;
+  }
   return GS_OK;
 }
 

@@ -10,6 +10,9 @@ constexpr int kMaxIterPerLaunch = 128;          // iterations per persistent lau
 constexpr int kSlots = 2 * kMaxIterPerLaunch + 2;  // FP64 partial-sum slots per launch
 constexpr int kMaxGrid = 256;                   // upper bound on blocks per launch
 constexpr int kMaxBatch = 64;                   // masks per launch
+// Pass timestamps (gs_set_trace): rows of kMaxGrid (done, released) pairs,
+// row 0 the launch start, row 1 + q pass q of the launch.
+constexpr int kTraceRows = 2 * kMaxIterPerLaunch + 4;
 // Group exchange buffers: (256 / T) groups of (n + n/32) complex, T = n/32,
 // which is 256 * 33 complex whatever n is.
 constexpr int kGroupSmemBytes = kThreads * 33 * 8;
@@ -51,6 +54,7 @@ struct Params {
   float inv_sqrt_n;    // 1/sqrt(N)
   double inv_n;        // 1/N
   int tensor_core;     // host side: launch the tensor-core kernel (square 256, 512, 1024)
+  unsigned long long* trace;  // [kTraceRows][grid][2] globaltimer stamps of block 0's thread 0 per block, or null
   int group;           // masks iterated together, 1..batch: the batch runs group after group
                        // through the whole schedule, so that a group's fields stay in L2
   // Grids with a side that is not a power of two (gs_general.cuh): the

@@ -649,14 +649,20 @@ __global__ void __launch_bounds__(kThreads, 1) gs_iterate(const Params p) {
 
   const int npass = pass_count(p);
   const int gsz = p.group > 0 ? p.group : p.batch;
+  unsigned long long* const tr = (p.trace != nullptr && threadIdx.x == 0) ? p.trace + 2 * blockIdx.x : nullptr;
+  if (tr) tr[0] = tr[1] = global_ns();
   for (int w0 = 0; w0 < p.batch; w0 += gsz) {  // mask groups, each through the whole schedule
     const int w1 = min(p.batch, w0 + gsz);
     for (int q0 = 0; q0 < npass; ++q0) {
       class_pass<LX, LY, kHold>(p, sh, 0, w0, w1, pass_info(p, q0), smem, mphase, tw_rows, tcf);
+      // pass timestamps: work done, then released by the barrier
+      unsigned long long* const trq = tr ? tr + static_cast<size_t>(2 * (1 + q0)) * gridDim.x : nullptr;
+      if (trq) trq[0] = global_ns();
       if (!grid_sync(p, target, sh)) {
         drain_copies(sh);
         return;
       }
+      if (trq) trq[1] = global_ns();
     }
   }
   final_gaps(p, sh, 0);

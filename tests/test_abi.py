@@ -96,6 +96,9 @@ def test_null_context_calls(lib):
     assert lib.gs_loss_grad(None, None, None, None, None) == B.GS_EINVAL
     assert lib.gs_run_mixed(None, None, None, None, 1, None, None, None) == B.GS_EINVAL
     assert lib.gs_set_mask_group(None, 2) == B.GS_EINVAL
+    assert lib.gs_set_trace(None, 1) == B.GS_EINVAL
+    n = ctypes.c_int(0)
+    assert lib.gs_get_trace(None, None, 0, ctypes.byref(n), ctypes.byref(n)) == B.GS_EINVAL
     assert B.gs_adam_step(0, 0, 0, 0, 16, 0, 0.05, 0.9, 0.999, 1e-8) == B.GS_EINVAL
 
 
