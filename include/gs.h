@@ -26,7 +26,10 @@
  *       r^nu = || |F u^nu|/sqrt(N) - m ||_2 / sqrt(N)   (distance of u^nu to M)
  *       g^nu = || P_M u^nu - P_S P_M u^nu ||_2 / sqrt(N) (distance of P_M u^nu to S)
  *     reduced in FP64. The field itself is computed in FP32.
- *   - nx and ny must be powers of two in [32, 4096].
+ *   - nx and ny are powers of two in [8, 4096] or 5-smooth numbers
+ *     (2^a 3^b 5^c, such as the 800 x 600 SLM of Sec. V) in [8, 1536].
+ *     Grids with both sides powers of two of at least 32 run on the
+ *     register-resident kernels; every other grid on the general kernel.
  *
  * Memory and ordering:
  *   - Pointers named "device" are CUDA device pointers owned by the caller;
@@ -90,7 +93,7 @@ typedef struct gs_ctx gs_ctx;
  * Operation: none yet; sizes the workspace for Eq. (e:AP) on an nx x ny SLM
  * (Sec. II: "n_x, n_y the respective number of pixels").
  *   out     host pointer that receives the context (set to NULL on failure).
- *   nx, ny  powers of two in [32, 4096].
+ *   nx, ny  grid sides: powers of two in [8, 4096], or 5-smooth in [8, 1536].
  *   flags   GS_* flags (GS_FINAL_RESIDUAL, GS_INIT_FROM_TARGET,
  *           GS_TENSOR_CORE).
  *   stream  a cudaStream_t, or NULL for the legacy default stream. All later

@@ -29,10 +29,11 @@ bool smooth5(int n) {
   return n == 1;
 }
 
-// A grid side: a power of two in [32, 4096], or a 5-smooth number in
-// [32, kMaxGeneralSide] (the general kernel).
+// A grid side: a power of two in [8, 4096], or a 5-smooth number in
+// [8, kMaxGeneralSide] (sides that are not powers of two, or below 32, run on
+// the general kernel).
 bool valid_dim(int n) {
-  if (n < 32) return false;
+  if (n < 8) return false;
   if (is_pow2(n)) return n <= 4096;
   return n <= gsk::kMaxGeneralSide && smooth5(n);
 }
@@ -220,7 +221,7 @@ int group_size(const gs_ctx* c, int batch) {
 }
 
 int choose_grid(const gs_ctx* c) {
-  if (!c->mixed && (!is_pow2(c->nx) || !is_pow2(c->ny)) && c->grid_override <= 0) {
+  if (!c->mixed && gsk::uses_general(c->nx, c->ny) && c->grid_override <= 0) {
     // general sides: one row per team (four per block) and one 4-column
     // group per block, so that each pass is one round
     const int t = gsk::kGenTeams;
@@ -289,7 +290,7 @@ int gs_create_batched(gs_ctx** out, int nx, int ny, int max_batch, unsigned flag
     delete c;
     return GS_ENOMEM;
   }
-  const bool general = !is_pow2(nx) || !is_pow2(ny);
+  const bool general = gsk::uses_general(nx, ny);
   const std::vector<float2> wx = twiddles(nx, general);
   const std::vector<float2> wy = twiddles(ny, general);
   const std::vector<float> ones(4096, 1.0f);
@@ -631,14 +632,14 @@ int enqueue_loss(gs_ctx* c, const float* target_intensity, const float* phase, d
 
 int gs_loss_grad(gs_ctx* c, const float* target_intensity, const float* phase, double* loss_out, float* grad_out) {
   if (c == nullptr || c->mixed || target_intensity == nullptr || phase == nullptr || loss_out == nullptr ||
-      c->nx != c->ny || !is_pow2(c->nx))
+      c->nx != c->ny || gsk::uses_general(c->nx, c->ny))
     return GS_EINVAL;
   return enqueue_loss(c, target_intensity, phase, loss_out, grad_out, nullptr);
 }
 
 int gs_physical_error(gs_ctx* c, const float* target_intensity, const float* phase, double* error_out) {
   if (c == nullptr || c->mixed || target_intensity == nullptr || phase == nullptr || error_out == nullptr ||
-      c->nx != c->ny || !is_pow2(c->nx))
+      c->nx != c->ny || gsk::uses_general(c->nx, c->ny))
     return GS_EINVAL;
   return enqueue_loss(c, target_intensity, phase, at<double>(c, c->L.lossbuf), nullptr, error_out);
 }

@@ -72,7 +72,14 @@ struct MixedParams {
   Params cls[3];
 };
 
-// Sides of the general kernel: 5-smooth (2^a 3^b 5^c) in [32, kMaxGeneralSide].
+// The general kernel serves every grid with a side that is not a power of
+// two or is below 32 (the power-of-two kernels need 32 points per thread).
+inline __host__ __device__ bool uses_general(int nx, int ny) {
+  const bool px = nx > 0 && (nx & (nx - 1)) == 0, py = ny > 0 && (ny & (ny - 1)) == 0;
+  return !px || !py || nx < 32 || ny < 32;
+}
+
+// Sides of the general kernel: 5-smooth (2^a 3^b 5^c) in [8, kMaxGeneralSide].
 constexpr int kMaxGeneralSide = 1536;
 constexpr int kMaxGeneralStages = 10;
 

@@ -48,10 +48,8 @@ static int log2_exact(int n) {
   return l;
 }
 
-static bool pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
-
 static const void* kernel_for(int nx, int ny, bool tc) {
-  if (!pow2(nx) || !pow2(ny)) return tc ? nullptr : iterate_kernel_general();
+  if (uses_general(nx, ny)) return tc ? nullptr : iterate_kernel_general();
   const int ly = log2_exact(ny);
   if (tc) return nx == ny ? iterate_kernel_tc(ly) : nullptr;
   switch (log2_exact(nx)) {
@@ -68,7 +66,7 @@ static const void* kernel_for(int nx, int ny, bool tc) {
 }
 
 size_t iteration_smem_bytes(int nx, int ny, bool tensor_core) {
-  if (!pow2(nx) || !pow2(ny)) return gen_smem_bytes(nx, ny);
+  if (uses_general(nx, ny)) return gen_smem_bytes(nx, ny);
   // group exchange buffers, one column block of the amplitude, one of the
   // field; then the tensor-core tables
   return kGroupSmemBytes + 8192 * 4 + 8192 * 8 + (tensor_core ? kTcExtraSmemBytes : 0);
@@ -80,7 +78,7 @@ cudaError_t iteration_occupancy(int nx, int ny, int* blocks_per_sm, bool tensor_
   const size_t smem = iteration_smem_bytes(nx, ny, tensor_core);
   // The general kernel serves every size: allow its largest request, so that
   // contexts of different sizes do not undo each other's setting.
-  const size_t allow = (!pow2(nx) || !pow2(ny)) ? gen_smem_bytes(kMaxGeneralSide, kMaxGeneralSide) : smem;
+  const size_t allow = uses_general(nx, ny) ? gen_smem_bytes(kMaxGeneralSide, kMaxGeneralSide) : smem;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(allow));
   if (e != cudaSuccess) return e;
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k, kThreads, smem);

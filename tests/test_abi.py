@@ -63,14 +63,17 @@ def test_workspace_bytes(lib):
     # sides that are not powers of two: 5-smooth, at most 1536
     for ok in ((800, 600), (600, 800), (1536, 1536), (96, 4096), (1000, 45 * 32)):
         assert B.gs_workspace_bytes(*ok) >= 20 * ok[0] * ok[1]
-    for bad in ((16, 64), (64, 16), (33, 64), (8192, 64), (0, 0), (-64, 64), (98, 128), (77, 64), (1600, 600),
-                (1620, 64), (30, 64)):
+    for bad in ((4, 64), (64, 6), (33, 64), (8192, 64), (0, 0), (-64, 64), (98, 128), (77, 64), (1600, 600),
+                (1620, 64), (7, 64)):
         assert B.gs_workspace_bytes(*bad) == 0
+    # small sides (below 32) run on the general kernel
+    for ok in ((8, 8), (16, 64), (30, 64), (12, 10)):
+        assert B.gs_workspace_bytes(*ok) > 0
 
 
 def test_create_validates_before_cuda(lib):
     h = ctypes.c_void_p(123)
-    for nx, ny in ((33, 64), (64, 8192), (16, 16), (0, 64), (98, 64), (1600, 600)):
+    for nx, ny in ((33, 64), (64, 8192), (4, 4), (0, 64), (98, 64), (1600, 600)):
         rc = lib.gs_create(ctypes.byref(h), nx, ny, 1, None)
         assert rc == B.GS_EINVAL
         assert h.value is None

@@ -24,10 +24,18 @@ pytestmark = pytest.mark.gpu
         (1536, 45, 6, 10),    # the largest side
         (45, 1536, 6, 10),
         (243, 250, 8, 20),    # radices 3 and 5 only
+        (8, 8, 6, 1),         # small sides (below 32) on the general kernel
+        (16, 16, 10, 2),
+        (16, 64, 8, 2),
+        (64, 8, 8, 2),
+        (12, 10, 5, 1),
     ],
 )
 def test_parity(ny, nx, iters, nspots):
-    I = S.spot_target(ny + nx, ny, nx, nspots, (0.5, 1.0))
+    if min(ny, nx) < 10:  # no spot fits 7 px away from DC: a random positive target
+        I = np.random.default_rng(ny + nx).random((ny, nx)).astype(np.float32)
+    else:
+        I = S.spot_target(ny + nx, ny, nx, nspots, (0.5, 1.0))
     phi0 = S.random_phase(ny + nx, ny, nx)
     check_run(I, phi0, iters, one_step_at=(0, iters - 1))
 
