@@ -29,6 +29,7 @@ pytestmark = pytest.mark.gpu
         (16, 64, 8, 2),
         (64, 8, 8, 2),
         (12, 10, 5, 1),
+        (40, 48, 130, 3),     # two launches (128 iterations each at most)
     ],
 )
 def test_parity(ny, nx, iters, nspots):
