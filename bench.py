@@ -51,7 +51,7 @@ def kernel_sources_sha() -> str:
     csrc = os.path.join(ROOT, "paper_1302_0120_gb300", "csrc")
     h = hashlib.sha256()
     for f in sorted(glob.glob(os.path.join(csrc, "*.cuh")) + glob.glob(os.path.join(csrc, "*_inst.cu")) +
-                    [os.path.join(csrc, "gs_internal.h"), os.path.join(ROOT, "include", "gs.h")]):
+                    [os.path.join(csrc, "gs_internal.h")]):
         h.update(os.path.basename(f).encode())
         with open(f, "rb") as fh:
             h.update(fh.read())

@@ -60,7 +60,8 @@ enum {
   GS_ENOMEM = -2,   /* device or host allocation failed */
   GS_ECUDA = -3,    /* a CUDA runtime call failed (no device, launch failure) */
   GS_ETIMEOUT = -4, /* a device-side wait gave up (grid barrier did not complete) */
-  GS_ENUMERIC = -5  /* target intensity is non-finite, negative or sums to zero */
+  GS_ENUMERIC = -5, /* target intensity is non-finite, negative or sums to zero */
+  GS_ECORRUPT = -6  /* gs_check_workspace: a canary word of the workspace was overwritten */
 };
 
 /* Flags for gs_create. */
@@ -243,6 +244,26 @@ int gs_status(gs_ctx* c);
  * Returns GS_EINVAL for a NULL context, GS_ECUDA if the launch fails.
  */
 int gs_set_slm_amplitude(gs_ctx* c, const float* amplitude);
+
+/*
+ * gs_check_workspace -- verify the canary words of the context's workspace
+ * (a diagnostic; the paper has no counterpart).
+ *
+ * Every buffer of the workspace is followed by 256 bytes of a fixed pattern,
+ * written at creation; a kernel that wrote past the end of a buffer would
+ * overwrite one. Synchronises the context stream and compares every canary.
+ * Returns GS_OK, GS_ECORRUPT if one changed, GS_EINVAL for a NULL context,
+ * GS_ECUDA on a CUDA error.
+ */
+int gs_check_workspace(gs_ctx* c);
+
+/*
+ * gs_test_corrupt_workspace -- test hook: overwrite one byte of the first
+ * canary word from the host (a memset on the workspace; no kernel runs), so
+ * that a test can see gs_check_workspace report GS_ECORRUPT. Returns GS_OK,
+ * GS_EINVAL for a NULL context, GS_ECUDA on a CUDA error.
+ */
+int gs_test_corrupt_workspace(gs_ctx* c);
 
 /*
  * gs_set_trace -- record per-pass timestamps of later runs (a diagnostic; the

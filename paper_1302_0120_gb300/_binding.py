@@ -18,6 +18,7 @@ GS_ENOMEM = -2
 GS_ECUDA = -3
 GS_ETIMEOUT = -4
 GS_ENUMERIC = -5
+GS_ECORRUPT = -6
 
 GS_FINAL_RESIDUAL = 1
 GS_INIT_FROM_TARGET = 2
@@ -50,6 +51,8 @@ SIGNATURES = {
     "gs_run_mixed": (_c_int, [_vp, _vp, _vp, _vp, _c_int, _vp, _vp, _vp]),
     "gs_set_mask_group": (_c_int, [_vp, _c_int]),
     "gs_set_trace": (_c_int, [_vp, _c_int]),
+    "gs_check_workspace": (_c_int, [_vp]),
+    "gs_test_corrupt_workspace": (_c_int, [_vp]),
     "gs_get_trace": (_c_int, [_vp, _vp, _c_int, ctypes.POINTER(_c_int), ctypes.POINTER(_c_int)]),
     "gs_adam_step": (_c_int, [_vp, _vp, _vp, _vp, ctypes.c_longlong, _vp, ctypes.c_float, ctypes.c_float,
                               ctypes.c_float, ctypes.c_float, _vp]),
@@ -150,6 +153,16 @@ def gs_adam_step(phase: int, grad: int, m: int, v: int, n: int, state: int, lr: 
     """Enqueue one Adam update on device pointers; returns the status code."""
     return lib().gs_adam_step(_vp(phase), _vp(grad), _vp(m), _vp(v), int(n), _vp(state), float(lr), float(beta1),
                               float(beta2), float(eps), _vp(stream or 0))
+
+
+def gs_check_workspace(ctx: int) -> int:
+    """Compare the workspace's canary words (synchronises); returns the status code."""
+    return lib().gs_check_workspace(_vp(ctx))
+
+
+def gs_test_corrupt_workspace(ctx: int) -> int:
+    """Test hook: overwrite one canary byte from the host; returns the status code."""
+    return lib().gs_test_corrupt_workspace(_vp(ctx))
 
 
 def gs_set_trace(ctx: int, enable: bool) -> int:

@@ -72,7 +72,12 @@ constexpr int kTwiddleEntries = 31 * 32 + 31 * 1024;
 // Offsets of the sub-buffers of one workspace allocation.
 struct Layout {
   size_t B, mT, partials, twx, twy, ones, bar, status, abort_flag, mask_flags, energy, lossbuf, dI, dphi, trace, total;
+  size_t guard[16];  // canary words after each buffer (gs_check_workspace)
+  int nguard;
 };
+
+constexpr size_t kGuardBytes = 256;
+constexpr unsigned char kGuardByte = 0xA5;
 
 Layout make_layout(int nx, int ny, int max_batch) {
   const size_t n = static_cast<size_t>(nx) * ny;
@@ -80,21 +85,36 @@ Layout make_layout(int nx, int ny, int max_batch) {
   Layout L{};
   size_t o = 0;
   L.B = o;          o = align_up(o + nb * sizeof(float2));
+  L.guard[L.nguard++] = o; o += kGuardBytes;
   L.mT = o;         o = align_up(o + nb * sizeof(float));
+  L.guard[L.nguard++] = o; o += kGuardBytes;
   L.partials = o;
   o = align_up(o + static_cast<size_t>(gsk::kSlots) * max_batch * gsk::kMaxGrid * sizeof(double));
+  L.guard[L.nguard++] = o; o += kGuardBytes;
   L.twx = o;        o = align_up(o + static_cast<size_t>(kTwiddleEntries) * sizeof(float2));
+  L.guard[L.nguard++] = o; o += kGuardBytes;
   L.twy = o;        o = align_up(o + static_cast<size_t>(kTwiddleEntries) * sizeof(float2));
+  L.guard[L.nguard++] = o; o += kGuardBytes;
   L.ones = o;       o = align_up(o + 4096 * sizeof(float));
+  L.guard[L.nguard++] = o; o += kGuardBytes;
   L.bar = o;        o = align_up(o + sizeof(unsigned));
+  L.guard[L.nguard++] = o; o += kGuardBytes;
   L.status = o;     o = align_up(o + sizeof(int));
+  L.guard[L.nguard++] = o; o += kGuardBytes;
   L.abort_flag = o; o = align_up(o + sizeof(int));
+  L.guard[L.nguard++] = o; o += kGuardBytes;
   L.mask_flags = o; o = align_up(o + gsk::kMaxBatch * sizeof(int));
+  L.guard[L.nguard++] = o; o += kGuardBytes;
   L.energy = o;     o = align_up(o + sizeof(double));
+  L.guard[L.nguard++] = o; o += kGuardBytes;
   L.lossbuf = o;    o = align_up(o + sizeof(double));
+  L.guard[L.nguard++] = o; o += kGuardBytes;
   L.dI = o;         o = align_up(o + n * sizeof(float));
+  L.guard[L.nguard++] = o; o += kGuardBytes;
   L.dphi = o;       o = align_up(o + n * sizeof(float));
+  L.guard[L.nguard++] = o; o += kGuardBytes;
   L.trace = o;      o = align_up(o + static_cast<size_t>(gsk::kTraceRows) * gsk::kMaxGrid * 2 * sizeof(unsigned long long));
+  L.guard[L.nguard++] = o; o += kGuardBytes;
   L.total = o;
   return L;
 }
@@ -220,6 +240,26 @@ int group_size(const gs_ctx* c, int batch) {
   return g < batch ? g : batch;
 }
 
+// Fill (or check) the canary words of one workspace layout at ws.
+bool fill_guards(unsigned char* ws, const Layout& L) {
+  for (int g = 0; g < L.nguard; ++g)
+    if (cudaMemset(ws + L.guard[g], kGuardByte, kGuardBytes) != cudaSuccess) return false;
+  return true;
+}
+
+int check_guards(const unsigned char* ws, const Layout& L) {
+  unsigned char h[kGuardBytes];
+  for (int g = 0; g < L.nguard; ++g) {
+    if (cudaMemcpy(h, ws + L.guard[g], kGuardBytes, cudaMemcpyDeviceToHost) != cudaSuccess) {
+      cudaGetLastError();
+      return GS_ECUDA;
+    }
+    for (size_t k = 0; k < kGuardBytes; ++k)
+      if (h[k] != kGuardByte) return GS_ECORRUPT;
+  }
+  return GS_OK;
+}
+
 int choose_grid(const gs_ctx* c) {
   if (!c->mixed && gsk::uses_general(c->nx, c->ny) && c->grid_override <= 0) {
     // general sides: one row per team (four per block) and one 4-column
@@ -246,6 +286,7 @@ const char* gs_strerror(int code) {
     case GS_ECUDA: return "CUDA runtime error";
     case GS_ETIMEOUT: return "device-side wait timed out";
     case GS_ENUMERIC: return "target intensity is non-finite, negative or zero";
+    case GS_ECORRUPT: return "a canary word of the workspace was overwritten";
     default: return "unknown status";
   }
 }
@@ -297,7 +338,7 @@ int gs_create_batched(gs_ctx** out, int nx, int ny, int max_batch, unsigned flag
   bool ok = cudaMemcpy(c->ws + c->L.twx, wx.data(), wx.size() * sizeof(float2), cudaMemcpyHostToDevice) == cudaSuccess &&
             cudaMemcpy(c->ws + c->L.ones, ones.data(), ones.size() * sizeof(float), cudaMemcpyHostToDevice) == cudaSuccess &&
             cudaMemcpy(c->ws + c->L.twy, wy.data(), wy.size() * sizeof(float2), cudaMemcpyHostToDevice) == cudaSuccess &&
-            cudaMemset(c->ws + c->L.bar, 0, c->L.dI - c->L.bar) == cudaSuccess;
+            cudaMemset(c->ws + c->L.bar, 0, c->L.dI - c->L.bar) == cudaSuccess && fill_guards(c->ws, c->L);
   if (!ok) {
     cudaGetLastError();
     cudaFree(c->ws);
@@ -437,7 +478,7 @@ int gs_create_mixed(gs_ctx** out, const int* max_batch, unsigned flags, void* st
     const std::vector<float2> tw = twiddles(256 << k, false);
     ok = cudaMemcpy(w + L.twx, tw.data(), tw.size() * sizeof(float2), cudaMemcpyHostToDevice) == cudaSuccess &&
          cudaMemcpy(w + L.twy, tw.data(), tw.size() * sizeof(float2), cudaMemcpyHostToDevice) == cudaSuccess &&
-         cudaMemset(w + L.bar, 0, L.dI - L.bar) == cudaSuccess;
+         cudaMemset(w + L.bar, 0, L.dI - L.bar) == cudaSuccess && fill_guards(w, L);
   }
   if (!ok) {
     cudaGetLastError();
@@ -660,6 +701,32 @@ int gs_set_slm_amplitude(gs_ctx* c, const float* amplitude) {
 int gs_test_barrier_timeout(gs_ctx* c, int enable) {
   if (c == nullptr || enable < 0) return GS_EINVAL;
   c->extra_arrivals = enable ? 1u : 0u;
+  return GS_OK;
+}
+
+int gs_check_workspace(gs_ctx* c) {
+  if (c == nullptr) return GS_EINVAL;
+  if (cudaStreamSynchronize(c->stream) != cudaSuccess) {
+    cudaGetLastError();
+    return GS_ECUDA;
+  }
+  if (!c->mixed) return check_guards(c->ws, c->L);
+  for (int k = 0; k < 3; ++k) {
+    if (c->mixed_max[k] == 0) continue;
+    const int rc = check_guards(c->ws + c->mbase[k], c->Lm[k]);
+    if (rc != GS_OK) return rc;
+  }
+  return GS_OK;
+}
+
+int gs_test_corrupt_workspace(gs_ctx* c) {
+  if (c == nullptr) return GS_EINVAL;
+  const Layout& L = c->L;  // of a mixed context: its first class, at offset 0
+  if (cudaStreamSynchronize(c->stream) != cudaSuccess ||
+      cudaMemset(c->ws + L.guard[0] + kGuardBytes / 2, 0, 1) != cudaSuccess) {
+    cudaGetLastError();
+    return GS_ECUDA;
+  }
   return GS_OK;
 }
 

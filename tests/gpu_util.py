@@ -28,6 +28,9 @@ def gpu_gs(I, phi0, iters, grid=None, final_residual=True, aliased=False):
         Pt = torch.from_numpy(np.ascontiguousarray(phi0, np.float32)).cuda()
         out, r, g = gs.run(It, Pt, iters, phase_out=Pt if aliased else None)
         st = gs.status()
+        from paper_1302_0120_gb300 import _binding as B
+
+        assert B.gs_check_workspace(gs.handle) == B.GS_OK  # no write past a workspace buffer
         return out.cpu().numpy(), r.cpu().numpy(), g.cpu().numpy(), st
 
 

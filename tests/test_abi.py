@@ -49,7 +49,7 @@ def test_binding_covers_every_declared_symbol():
 
 def test_strerror(lib):
     assert B.gs_strerror(B.GS_OK) == "success"
-    for code in (B.GS_EINVAL, B.GS_ENOMEM, B.GS_ECUDA, B.GS_ETIMEOUT, B.GS_ENUMERIC, 12345):
+    for code in (B.GS_EINVAL, B.GS_ENOMEM, B.GS_ECUDA, B.GS_ETIMEOUT, B.GS_ENUMERIC, B.GS_ECORRUPT, 12345):
         assert len(B.gs_strerror(code)) > 0
 
 
@@ -100,6 +100,7 @@ def test_null_context_calls(lib):
     assert lib.gs_run_mixed(None, None, None, None, 1, None, None, None) == B.GS_EINVAL
     assert lib.gs_set_mask_group(None, 2) == B.GS_EINVAL
     assert lib.gs_set_trace(None, 1) == B.GS_EINVAL
+    assert lib.gs_check_workspace(None) == B.GS_EINVAL
     n = ctypes.c_int(0)
     assert lib.gs_get_trace(None, None, 0, ctypes.byref(n), ctypes.byref(n)) == B.GS_EINVAL
     assert B.gs_adam_step(0, 0, 0, 0, 16, 0, 0.05, 0.9, 0.999, 1e-8) == B.GS_EINVAL

@@ -37,6 +37,9 @@ def run_batched(I, P, iters, grid=None, final_residual=True):
             gs.set_grid(grid)
         ph, r, g = gs.run_batched(torch.from_numpy(I).cuda(), torch.from_numpy(P).cuda(), iters)
         st = gs.status()
+        from paper_1302_0120_gb300 import _binding as B
+
+        assert B.gs_check_workspace(gs.handle) == B.GS_OK
         return ph.cpu().numpy(), r.cpu().numpy(), g.cpu().numpy(), st
 
 

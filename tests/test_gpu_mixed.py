@@ -43,6 +43,9 @@ def test_mixed_matches_per_size_launches(tc, counts, iters, from_target):
     with MixedGerchbergSaxton(counts, tensor_core=tc, init_from_target=from_target) as gs:
         out = gs.run(T, P, iters)
         assert gs.status() == 0
+        from paper_1302_0120_gb300 import _binding as B
+
+        assert B.gs_check_workspace(gs.handle) == B.GS_OK
         out = {n: tuple(x.cpu().numpy() for x in v) for n, v in out.items()}
     for n in counts:
         with GerchbergSaxton(n, n, max_batch=counts[n], tensor_core=tc, init_from_target=from_target) as gs1:

@@ -38,6 +38,9 @@ def tc_run(I, phi0, iters, p=None):
             gs.set_slm_amplitude(pt)
         ph, r, g = gs.run(torch.from_numpy(I).cuda(), torch.from_numpy(phi0).cuda(), iters)
         st = gs.status()
+        from paper_1302_0120_gb300 import _binding as B
+
+        assert B.gs_check_workspace(gs.handle) == B.GS_OK
         return ph.cpu().numpy(), r.cpu().numpy(), g.cpu().numpy(), st
 
 

@@ -36,3 +36,28 @@ def test_trace_shape_order_and_results():
     assert np.all(np.diff(seq, axis=0) >= 0), "stamps must not go back in time"
     work, barrier = B.pass_times(tr)
     assert work.shape == (passes,) and np.all(work > 0) and np.all(barrier > -1.0)
+
+
+def test_workspace_canaries():
+    """The canary words survive runs of every kind on one context and
+    report an overwrite."""
+    import torch
+
+    from paper_1302_0120_gb300 import GerchbergSaxton, build_lib
+    from paper_1302_0120_gb300 import _binding as B
+    from paper_1302_0120_gb300.differentiable import LossContext
+
+    build_lib.build()
+    I, phi0, _ = S.workload("spots64")
+    It, Pt = torch.from_numpy(I).cuda(), torch.from_numpy(phi0).cuda()
+    with GerchbergSaxton(64, 64, max_batch=2) as gs:
+        gs.run(It, Pt, 7)
+        gs.run_batched(torch.stack([It, It]), torch.stack([Pt, Pt]), 3)
+        assert gs.status() == 0
+        assert B.gs_check_workspace(gs.handle) == B.GS_OK
+        assert B.gs_test_corrupt_workspace(gs.handle) == B.GS_OK
+        assert B.gs_check_workspace(gs.handle) == B.GS_ECORRUPT
+    lc = LossContext(64)
+    lc.loss_grad(It, Pt)
+    assert lc.status() == 0 and B.gs_check_workspace(lc.handle) == B.GS_OK
+    lc.close()
