@@ -298,10 +298,10 @@ int gs_get_trace(gs_ctx* c, unsigned long long* host_out, int capacity, int* pas
  * A batch runs group after group, each group through the whole iteration
  * schedule of the launch, so that a group's fields (12 bytes per pixel) can
  * stay in L2; results do not depend on it (phases bit-identical, gaps to
- * FP64 rounding). masks = 0 (the default) iterates the whole batch (of each
- * size) together; masks > 0 fixes the group size, capped by the batch. In a
- * mixed run the sizes always run one after the other. Returns GS_EINVAL for a
- * NULL context or masks < 0.
+ * FP64 rounding). masks = 0 (the default) takes, per grid size, the most
+ * masks whose fields fit 100 MiB (8 of 1024 x 1024); masks > 0 fixes the
+ * group size, capped by the batch. In a mixed run the sizes always run one
+ * after the other. Returns GS_EINVAL for a NULL context or masks < 0.
  */
 int gs_set_mask_group(gs_ctx* c, int masks);
 
