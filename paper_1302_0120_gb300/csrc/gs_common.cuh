@@ -46,9 +46,15 @@ __device__ __forceinline__ unsigned long long global_ns() {
   return t;
 }
 
+// Added once to the grid-barrier counter by the first failing thread of a
+// launch: it releases every waiting block, which sees the bit in the value its
+// spin ended on (no extra load after the barrier). Arrivals per launch stay far
+// below it (at most blocks x passes, < 2^20).
+constexpr unsigned kAbortBit = 1u << 30;
+
 __device__ __forceinline__ void fail(const Params& p, int code) {
   atomicCAS(p.status, 0, code);
-  atomicExch(p.abort_flag, 1);
+  if (atomicExch(p.abort_flag, 1) == 0) atomicAdd(p.bar, kAbortBit);
 }
 
 // sum p^2 of the SLM amplitude (N for p = 1): the energy of every field in S.
@@ -104,7 +110,8 @@ static __device__ bool grid_sync(const Params& p, unsigned& target, Shared& sh) 
     const unsigned want = target + p.extra_arrivals;
     unsigned spins = 0;
     unsigned long long t0 = 0;
-    while (static_cast<int>(ld_acquire_gpu(p.bar) - want) < 0) {
+    unsigned v;
+    while (static_cast<int>((v = ld_acquire_gpu(p.bar)) - want) < 0) {
       ++spins;
       if ((spins & 255u) == 0) {
         const unsigned long long now = global_ns();
@@ -120,7 +127,7 @@ static __device__ bool grid_sync(const Params& p, unsigned& target, Shared& sh) 
     // block's arrival; the proxy fence extends that to the bulk copies it
     // issues next, and the __syncthreads below to the rest of the block.
     asm volatile("fence.proxy.async.global;" ::: "memory");
-    if (ok && *reinterpret_cast<volatile int*>(p.abort_flag) != 0) ok = 0;  // another block failed
+    if (ok && (v & kAbortBit) != 0) ok = 0;  // a block failed in this launch
     sh.flag = ok;
   }
   __syncthreads();
