@@ -189,6 +189,7 @@ struct gs_ctx {
   Layout L{};
   unsigned char* ws = nullptr;
   double* dres = nullptr;  // device residual staging for gs_run_host
+  double* hres = nullptr;  // pinned host copy of it, plus a word for the status
   size_t dres_cap = 0;     // doubles
   // gs_create_mixed: one workspace per size class n = 256 << k (max_batch > 0),
   // at byte offset mbase[k]; L above is the first such class, at offset 0.
@@ -613,9 +614,12 @@ int gs_run_host(gs_ctx* c, const float* target_intensity, const float* phase_in,
       return GS_ECUDA;
     }
     cudaFree(c->dres);
+    cudaFreeHost(c->hres);
     c->dres = nullptr;
+    c->hres = nullptr;
     c->dres_cap = 0;
-    if (cudaMalloc(&c->dres, need * sizeof(double)) != cudaSuccess) {
+    if (cudaMalloc(&c->dres, need * sizeof(double)) != cudaSuccess ||
+        cudaMallocHost(&c->hres, (need + 1) * sizeof(double)) != cudaSuccess) {
       cudaGetLastError();
       return GS_ENOMEM;
     }
@@ -633,14 +637,24 @@ int gs_run_host(gs_ctx* c, const float* target_intensity, const float* phase_in,
   }
   int rc = gs_run(c, dI, dphi, iters, dphi, dr, dg);
   if (rc != GS_OK) return rc;
+  // The phase goes straight to the caller's buffer; the gaps and the status
+  // word go through the context's pinned staging, so that one synchronisation
+  // ends the call whatever kind of host memory the caller passed.
   const size_t nr = static_cast<size_t>(iters) + ((c->flags & GS_FINAL_RESIDUAL) ? 1 : 0);
+  int* dst = at<int>(c, c->L.status);
+  int* hst = reinterpret_cast<int*>(c->hres + need);
   if (cudaMemcpyAsync(phase_out, dphi, n * sizeof(float), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
-      (dr && nr && cudaMemcpyAsync(residual_out, dr, nr * sizeof(double), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess) ||
-      (dg && iters && cudaMemcpyAsync(object_gap_out, dg, iters * sizeof(double), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess)) {
+      ((dr || dg) &&
+       cudaMemcpyAsync(c->hres, c->dres, need * sizeof(double), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess) ||
+      cudaMemcpyAsync(hst, dst, sizeof(int), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
+      cudaMemsetAsync(dst, 0, sizeof(int), c->stream) != cudaSuccess ||
+      cudaStreamSynchronize(c->stream) != cudaSuccess) {
     cudaGetLastError();
     return GS_ECUDA;
   }
-  return gs_status(c);
+  if (dr && nr) std::memcpy(residual_out, c->hres, nr * sizeof(double));
+  if (dg && iters) std::memcpy(object_gap_out, c->hres + nres, static_cast<size_t>(iters) * sizeof(double));
+  return *hst;
 }
 
 namespace {
@@ -791,6 +805,7 @@ int gs_destroy(gs_ctx* c) {
   if (cudaStreamSynchronize(c->stream) != cudaSuccess) rc = GS_ECUDA;
   if (c->ws && cudaFree(c->ws) != cudaSuccess) rc = GS_ECUDA;
   if (c->dres && cudaFree(c->dres) != cudaSuccess) rc = GS_ECUDA;
+  if (c->hres && cudaFreeHost(c->hres) != cudaSuccess) rc = GS_ECUDA;
   cudaGetLastError();
   delete c;
   return rc;

@@ -239,3 +239,34 @@ def test_run_host_pinned_buffers(iters):
             if iters:
                 assert np.array_equal(g[:iters], dev[2])
             pO.fill_(7.0)
+
+
+def test_run_host_growing_runs_and_status():
+    """One context, runs of growing and shrinking length (the staging of the
+    gaps grows with them), then an invalid target: the status comes back as
+    the return value and is cleared for the next call."""
+    from paper_1302_0120_gb300 import GS_ENUMERIC, GerchbergSaxton
+    from paper_1302_0120_gb300 import _binding as B
+
+    I, phi0, _ = S.workload("spots64")
+    with GerchbergSaxton(64, 64) as gs:
+        for iters in (3, 140, 0, 7):
+            dev = gpu_gs(I, phi0, iters)
+            r = np.empty(iters + 1)
+            g = np.empty(max(iters, 1))
+            out = np.empty_like(phi0)
+            rc = B.gs_run_host(gs.handle, I.ctypes.data, phi0.ctypes.data, iters, out.ctypes.data, r.ctypes.data,
+                               g.ctypes.data)
+            assert rc == 0
+            assert np.array_equal(out, dev[0]) and np.array_equal(r, dev[1])
+            if iters:
+                assert np.array_equal(g[:iters], dev[2])
+        bad = I.copy()
+        bad[3, 5] = -1.0
+        r = np.empty(6)
+        out = np.empty_like(phi0)
+        assert B.gs_run_host(gs.handle, bad.ctypes.data, phi0.ctypes.data, 5, out.ctypes.data, r.ctypes.data,
+                             0) == GS_ENUMERIC
+        assert np.all(np.isnan(r))
+        rc = B.gs_run_host(gs.handle, I.ctypes.data, phi0.ctypes.data, 5, out.ctypes.data, r.ctypes.data, 0)
+        assert rc == 0 and np.all(np.isfinite(r))
