@@ -488,6 +488,51 @@ def run_gpu(args):
                          "speedup_vs_paper_e2e": round(45.0 / statistics.mean(host_ms), 1), "grid_ctas": gsp.grid}
         gsp.close()
 
+    # the small workload (64 x 64, 5 spots, 20 iterations plus r^K): one block
+    # per mask with the field in shared memory. Latency of one mask on the
+    # device and end to end through gs_run_host, the same mask on the
+    # persistent kernel (fixed grid), and a batch of 64 masks in one launch.
+    spots64 = None
+    if args.small_steps > 0 and ws == 1:
+        from paper_1302_0120_gb300 import _binding as B6
+
+        I6, P6, K6 = S.workload("spots64", seed=rank)
+        I6d, P6d = torch.from_numpy(I6).to(dev), torch.from_numpy(P6).to(dev)
+        o6 = torch.empty_like(P6d)
+        g6 = GerchbergSaxton(64, 64, stream=stream)
+        ms_small = timed(lambda: g6.run(I6d, P6d, K6, phase_out=o6), args.small_steps)
+        g6p = GerchbergSaxton(64, 64, stream=stream)
+        g6p.set_grid(g6.grid)
+        ms_pers = timed(lambda: g6p.run(I6d, P6d, K6, phase_out=o6), args.small_steps)
+        Ib = np.stack([S.workload("spots64", seed=100 + k)[0] for k in range(64)])
+        Pb = np.stack([S.workload("spots64", seed=100 + k)[1] for k in range(64)])
+        Ibd, Pbd = torch.from_numpy(Ib).to(dev), torch.from_numpy(Pb).to(dev)
+        ob = torch.empty_like(Pbd)
+        g6b = GerchbergSaxton(64, 64, stream=stream, max_batch=64)
+        ms_batch = timed(lambda: g6b.run_batched(Ibd, Pbd, K6, phase_out=ob), args.small_steps)
+        pin6, pinp6 = torch.from_numpy(I6).pin_memory(), torch.from_numpy(P6).pin_memory()
+        pout6 = torch.empty_like(pinp6).pin_memory()
+        r6 = torch.empty(K6 + 1, dtype=torch.float64).pin_memory()
+        host6 = []
+        for k in range(args.small_steps + 2):
+            flush.zero_()
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            rc = B6.gs_run_host(g6.handle, pin6.data_ptr(), pinp6.data_ptr(), K6, pout6.data_ptr(), r6.data_ptr(), 0)
+            if rc != 0:
+                raise RuntimeError(f"gs_run_host 64x64: {B6.gs_strerror(rc)}")
+            if k >= 2:
+                host6.append(1e3 * (time.perf_counter() - t0))
+        if g6.status() != 0 or g6p.status() != 0 or g6b.status() != 0:
+            raise RuntimeError("64x64 runs failed")
+        spots64 = {"iters": K6, "kernel": "one block per mask, field in shared memory",
+                   "device_ms": round(ms_small, 4), "e2e_ms": round(statistics.mean(host6), 4),
+                   "persistent_kernel_ms": round(ms_pers, 4), "persistent_grid_ctas": g6p.grid,
+                   "batch64_ms": round(ms_batch, 4), "batch64_masks_per_s": round(64e3 / ms_batch, 1),
+                   "final_residual": float(r6[K6])}
+        for g_ in (g6, g6p, g6b):
+            g_.close()
+
     # 64 masks of mixed size (256^2, 512^2, 1024^2 by seed, 10..200 spots), 50
     # iterations in one persistent launch (gs_run_mixed): FP32 and tensor-core forms
     mixed64 = None
@@ -613,6 +658,7 @@ def run_gpu(args):
         "pass_trace": pass_trace,
         "tensor_core": tensor_core,
         "paper_800x600": paper_800x600,
+        "spots64": spots64,
         "mixed64": mixed64,
         "wall_s": round(wall, 3),
     }
@@ -642,6 +688,7 @@ def main(argv=None):
     ap.add_argument("--tc-steps", type=int, default=20, help="timed runs of the tensor-core field (0: skip)")
     ap.add_argument("--paper-steps", type=int, default=20, help="timed runs of the 800x600 field (0: skip)")
     ap.add_argument("--mixed-steps", type=int, default=5, help="timed runs of the 64-mask mixed batch (0: skip)")
+    ap.add_argument("--small-steps", type=int, default=50, help="timed runs of the 64x64 field (0: skip)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget-s", type=float, default=12.0)
     ap.add_argument("--ref-sample-iters", type=int, default=2)

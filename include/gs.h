@@ -137,6 +137,12 @@ int gs_create_batched(gs_ctx** out, int nx, int ny, int max_batch, unsigned flag
  * arrays, iters < 0; GS_ECUDA if a launch fails. Device-side errors are
  * reported by gs_status; on GS_ENUMERIC the phase output is left untouched and
  * residuals are set to NaN.
+ * Execution: one persistent cooperative launch per 128 iterations; grids of
+ * power-of-two sides >= 32 with at most 8192 pixels (64 x 64, 32 x 256, ...)
+ * instead run the whole run in one launch of one block per mask with the
+ * field in shared memory (same iterates bit for bit), unless gs_set_grid
+ * fixed a grid, or the target start, a laser amplitude or pass timestamps
+ * are in use.
  */
 int gs_run(gs_ctx* c, const float* target_intensity, const float* phase_in, int iters,
            float* phase_out, double* residual_out, double* object_gap_out);
@@ -310,6 +316,7 @@ int gs_set_mask_group(gs_ctx* c, int masks);
  *
  * ctas = 0 restores the automatic choice. A value above what the device can
  * keep resident at once is clamped. Host-only; takes effect at the next run.
+ * A fixed grid also runs small grids on the persistent kernel (see gs_run).
  * Returns GS_EINVAL for a NULL context or ctas < 0.
  */
 int gs_set_grid(gs_ctx* c, int ctas);

@@ -327,7 +327,8 @@ int gs_create_batched(gs_ctx** out, int nx, int ny, int max_batch, unsigned flag
   c->L = make_layout(nx, ny, max_batch);
   if (cudaGetDevice(&c->device) != cudaSuccess ||
       cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess ||
-      gsk::iteration_occupancy(nx, ny, &c->blocks_per_sm, tc) != cudaSuccess || c->blocks_per_sm < 1) {
+      gsk::iteration_occupancy(nx, ny, &c->blocks_per_sm, tc) != cudaSuccess || c->blocks_per_sm < 1 ||
+      (gsk::small_grid(nx, ny) && gsk::small_prepare(nx, ny) != cudaSuccess)) {
     cudaGetLastError();
     delete c;
     return GS_ECUDA;
@@ -366,6 +367,12 @@ int gs_run_batched(gs_ctx* c, int batch, const float* target_intensity, const fl
   if (c == nullptr || c->mixed || target_intensity == nullptr || (phase_in == nullptr && !from_target) ||
       phase_out == nullptr || iters < 0 || batch < 1 || batch > c->max_batch)
     return GS_EINVAL;
+  // Small grids run one block per mask with the field in shared memory,
+  // unless a fixed grid, a variant the small kernel does not implement (the
+  // target start, a laser amplitude, tensor cores) or a diagnostic (pass
+  // timestamps, the barrier test hook) asks for the persistent kernel.
+  const bool small = gsk::small_grid(c->nx, c->ny) && c->grid_override == 0 && !from_target &&
+                     c->p_slm == nullptr && !(c->flags & GS_TENSOR_CORE) && !c->trace && c->extra_arrivals == 0;
   const int grid = choose_grid(c);
   gsk::Params p{};
   p.batch = batch;
@@ -405,6 +412,16 @@ int gs_run_batched(gs_ctx* c, int batch, const float* target_intensity, const fl
   const double n = static_cast<double>(c->nx) * c->ny;
   p.inv_sqrt_n = static_cast<float>(1.0 / std::sqrt(n));
   p.inv_n = 1.0 / n;
+  if (small) {  // one launch for the whole run, whatever K
+    p.it0 = 0;
+    p.it1 = iters;
+    p.do_init = p.do_final = 1;
+    if (gsk::launch_small(p, c->stream) != cudaSuccess) {
+      cudaGetLastError();
+      return GS_ECUDA;
+    }
+    return GS_OK;
+  }
   if (cudaMemsetAsync(p.abort_flag, 0, sizeof(int), c->stream) != cudaSuccess) {
     cudaGetLastError();
     return GS_ECUDA;

@@ -72,6 +72,14 @@ struct MixedParams {
   Params cls[3];
 };
 
+// Small grids (power-of-two sides >= 32, at most this many pixels) run one
+// block per mask with the whole field in shared memory (gs_small.cuh).
+constexpr int kSmallMaxPixels = 8192;
+inline __host__ __device__ bool small_grid(int nx, int ny) {
+  const bool px = nx > 0 && (nx & (nx - 1)) == 0, py = ny > 0 && (ny & (ny - 1)) == 0;
+  return px && py && nx >= 32 && ny >= 32 && static_cast<long long>(nx) * ny <= kSmallMaxPixels;
+}
+
 // The general kernel serves every grid with a side that is not a power of
 // two or is below 32 (the power-of-two kernels need 32 points per thread).
 inline __host__ __device__ bool uses_general(int nx, int ny) {
@@ -139,5 +147,9 @@ cudaError_t launch_iterations(const Params& p, int grid, cudaStream_t s);
 // sum p^2 of an SLM amplitude into *energy (NaN if p has a negative or non-finite value)
 cudaError_t launch_energy(const float* p, long long n, double* energy, cudaStream_t s);
 cudaError_t iteration_occupancy(int nx, int ny, int* blocks_per_sm, bool tensor_core = false);
+// Small grids (small_grid): allow the kernel its shared memory, and launch
+// one block per mask of p.batch (gs_small_inst.cu).
+cudaError_t small_prepare(int nx, int ny);
+cudaError_t launch_small(const Params& p, cudaStream_t s);
 
 }  // namespace gsk
