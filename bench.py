@@ -43,17 +43,30 @@ FLOPS_PROJ_PER_PX = 20
 
 
 def kernel_sources_sha() -> str:
-    """Hash of the device-code sources of the iteration kernels (the headers
-    and the instantiation units; host-only files do not change the kernel)."""
-    import glob
+    """Hash of the sources the FP32 iteration kernel is compiled from: its
+    instantiation unit and everything it includes from the package (other
+    kernels and host-only files do not change it)."""
     import hashlib
+    import re
 
     csrc = os.path.join(ROOT, "paper_1302_0120_gb300", "csrc")
+    inc = os.path.join(ROOT, "include")
+    seen, todo = [], ["gs_inst.cu"]
+    while todo:
+        name = todo.pop()
+        if name in seen:
+            continue
+        path = next((os.path.join(d, name) for d in (csrc, inc) if os.path.exists(os.path.join(d, name))), None)
+        if path is None:
+            continue  # a system header
+        seen.append(name)
+        with open(path) as fh:
+            todo.extend(re.findall(r'^\s*#\s*include\s+"([^"]+)"', fh.read(), flags=re.M))
     h = hashlib.sha256()
-    for f in sorted(glob.glob(os.path.join(csrc, "*.cuh")) + glob.glob(os.path.join(csrc, "*_inst.cu")) +
-                    [os.path.join(csrc, "gs_internal.h")]):
-        h.update(os.path.basename(f).encode())
-        with open(f, "rb") as fh:
+    for name in sorted(seen):
+        path = next(os.path.join(d, name) for d in (csrc, inc) if os.path.exists(os.path.join(d, name)))
+        h.update(name.encode())
+        with open(path, "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()
 
