@@ -71,7 +71,8 @@ __device__ __forceinline__ int split(int b, int G, int total) {
 }
 
 // Sum of one double per thread over the block, in a fixed order. The result
-// is returned to every thread.
+// is valid in thread 0 only (its one reader): FP64 issue is scarce on this
+// part, so the sum of the warps' totals runs on one thread, not on all 256.
 static __device__ double block_sum(double x, Shared& sh) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
@@ -79,8 +80,10 @@ static __device__ double block_sum(double x, Shared& sh) {
   if ((threadIdx.x & 31) == 0) sh.red[threadIdx.x >> 5] = x;
   __syncthreads();
   double s = 0.0;
+  if (threadIdx.x == 0) {
 #pragma unroll
-  for (int w = 0; w < kThreads / 32; ++w) s += sh.red[w];
+    for (int w = 0; w < kThreads / 32; ++w) s += sh.red[w];
+  }
   return s;
 }
 

@@ -49,7 +49,9 @@ struct SmallGeom {
   __device__ static int fo(int y, int x) { return y * NX + (x ^ rev4(y)); }
 };
 
-// Sum of one double per thread over a block of NT threads, in a fixed order.
+// Sum of one double per thread over a block of NT threads, in a fixed order,
+// valid in thread 0 only (FP64 issue is scarce: one thread adds the warps'
+// totals, not all of them).
 template <int NT>
 __device__ __forceinline__ double small_sum(double x, double* red) {
 #pragma unroll
@@ -58,8 +60,10 @@ __device__ __forceinline__ double small_sum(double x, double* red) {
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = x;
   __syncthreads();
   double s = 0.0;
+  if (threadIdx.x == 0) {
 #pragma unroll
-  for (int w = 0; w < NT / 32; ++w) s += red[w];
+    for (int w = 0; w < NT / 32; ++w) s += red[w];
+  }
   return s;
 }
 
@@ -68,15 +72,33 @@ __device__ __forceinline__ float small_phase(float2 u) {
   return (ph <= -3.14159274f) ? 3.14159274f : ph;
 }
 
+// The phase of row `line` to phase_out, once per run: through the group's
+// exchange buffer (free between transforms), so that a rolled loop holds the
+// only copy of atan2f and the registers are never indexed at run time.
+template <int LN>
+__device__ __forceinline__ void small_phase_out(const Params& p, size_t moff, int line, int t, const float2 (&v)[32],
+                                                const GroupT<LN>& grp) {
+  constexpr int T = GroupT<LN>::T;
+  float2* su = grp.sm + t;
+#pragma unroll
+  for (int i = 0; i < 32; ++i) su[T * i] = v[i];
+  float* po = p.phi_out + moff + static_cast<size_t>(line) * GroupT<LN>::N + t;
+#pragma unroll 1
+  for (int i = 0; i < 32; ++i) po[T * i] = small_phase(su[T * i]);
+  grp.sync();  // the next transform's exchange reuses the buffer
+}
+
 enum SmallPass { kSmallInit = 0, kSmallRow = 1, kSmallCol = 2, kSmallResid = 3 };
 
-// One pass over the rows (init, row) or columns (col, resid) of the block's
-// mask; returns this thread's FP64 share of the pass's gap sum.
+// The passes that run once per run: A1 (init, the rows of u0 = exp(i phi0))
+// and A4's final residual (the columns, forward transform only). Returns this
+// thread's FP64 share of the pass's gap sum.
 template <int LX, int LY, int KIND>
 __device__ __forceinline__ double small_pass(const Params& p, size_t moff, bool last, float2* F, const float* mT,
                                              float2* X, const StageTw<LX>& twr, const StageTw<LY>& twc) {
+  static_assert(KIND == kSmallInit || KIND == kSmallResid, "the iteration passes are small_pass_hot");
   using Gm = SmallGeom<LX, LY>;
-  constexpr bool kRows = (KIND == kSmallInit || KIND == kSmallRow);
+  constexpr bool kRows = (KIND == kSmallInit);
   constexpr int LN = kRows ? LX : LY;
   constexpr int T = kRows ? Gm::TX : Gm::TY;
   constexpr int NG = kRows ? Gm::NGR : Gm::NGC;
@@ -105,45 +127,15 @@ __device__ __forceinline__ double small_pass(const Params& p, size_t moff, bool 
         sincosf(ph[T * i], &s, &c);
         v[i] = make_float2(c, s);  // u0 = exp(i phi0)
       }
-      if (last) {  // zero iterations: the mask is arg exp(i phi0)
-        float* po = p.phi_out + moff + static_cast<size_t>(line) * Gm::NX + t;
-#pragma unroll
-        for (int i = 0; i < 32; ++i) po[T * i] = small_phase(v[i]);
-      }
+      if (last) small_phase_out(p, moff, line, t, v, grp);  // zero iterations: arg exp(i phi0)
       group_fft<LN>(v, grp, stw);
 #pragma unroll
       for (int i = 0; i < 32; ++i) F[Gm::fo(line, t + T * i)] = v[i];
-    } else if constexpr (KIND == kSmallRow) {
-#pragma unroll
-      for (int i = 0; i < 32; ++i) v[i] = F[Gm::fo(line, t + T * i)];
-      // v = swap(IDFT_x(B)) = swap(sqrt(N) P_M u^nu): gap to S and Eq. (e:PS)
-      group_fft<LN>(v, grp, stw);
-#pragma unroll
-      for (int i = 0; i < 32; ++i) {
-        const float vx = v[i].y;
-        const float vy = v[i].x;
-        const float a2 = vx * vx + vy * vy;
-        const float rs = rsqrtf(a2);
-        const float mag = a2 > 0.f ? a2 * rs : 0.f;
-        const float d = mag * inv_sqrt_n - 1.f;
-        part += d * d;
-        v[i] = a2 > 0.f ? make_float2(vx * rs, vy * rs) : make_float2(1.f, 0.f);
-      }
-      if (last) {
-        float* po = p.phi_out + moff + static_cast<size_t>(line) * Gm::NX + t;
-#pragma unroll
-        for (int i = 0; i < 32; ++i) po[T * i] = small_phase(v[i]);
-      }
-      if (!last || p.final_resid) {
-        group_fft<LN>(v, grp, stw);
-#pragma unroll
-        for (int i = 0; i < 32; ++i) F[Gm::fo(line, t + T * i)] = v[i];
-      }
     } else {
       const int c = line;
 #pragma unroll
       for (int i = 0; i < 32; ++i) v[i] = F[Gm::fo(t + T * i, c)];
-      // v = Y = F u^nu along this column: residual and Eq. (e:Mhat)
+      // v = Y = F u^K along this column: the final residual
       group_fft<LN>(v, grp, stw);
       const float* mcol = mT + c * Gm::MLD + t;
 #pragma unroll
@@ -155,17 +147,85 @@ __device__ __forceinline__ double small_pass(const Params& p, size_t moff, bool 
         const float mag = a2 > 0.f ? a2 * rs : 0.f;
         const float d = mag * inv_sqrt_n - m;
         part += d * d;
-        if constexpr (KIND == kSmallCol) {
+      }
+    }
+    acc += static_cast<double>(part);
+  }
+  __syncthreads();  // the pass's writes are seen by the next pass
+  return acc;
+}
+
+// The passes of the iteration loop, column (A2) or row (A3) by `kind` at run
+// time, lines of length 2^LN. The two transforms of a line go through one
+// rolled loop and a square grid serves both kinds with one instantiation, so
+// the loop body holds a single copy of the unrolled FFT: with one warp per
+// scheduler, a body with four copies spent most of its time waiting for
+// instructions. ROWS / COLS: the kinds this instantiation serves.
+template <int LX, int LY, int LN, bool ROWS, bool COLS>
+__device__ __forceinline__ double small_pass_hot(const Params& p, size_t moff, int kind, bool last, float2* F,
+                                                 const float* mT, float2* X, const StageTw<LN>& stw) {
+  using Gm = SmallGeom<LX, LY>;
+  static_assert(!ROWS || LN == LX, "row transforms have length nx");
+  static_assert(!COLS || LN == LY, "column transforms have length ny");
+  constexpr int T = 1 << (LN - 5);
+  constexpr int NG = Gm::NT / T;
+  constexpr int LINES = Gm::N >> LN;  // rows (length nx) or columns (length ny)
+  const bool rows = ROWS && (!COLS || kind == kSmallRow);
+  GroupT<LN> grp;
+  grp.t = threadIdx.x & (T - 1);
+  grp.bar_id = 0;  // T <= 8: groups sync by warp
+  grp.sm = X + (threadIdx.x / T) * GroupT<LN>::SMEM;
+  grp.tw = rows ? p.twx : p.twy;
+  const int t = grp.t;
+  const float inv_sqrt_n = p.inv_sqrt_n;
+  // a row pass that ends the run without the final residual stops after the projection
+  const int nh = (rows && last && !p.final_resid) ? 1 : 2;
+  double acc = 0.0;
+  for (int l0 = 0; l0 < LINES; l0 += NG) {
+    const int line = l0 + static_cast<int>(threadIdx.x) / T;
+    float2 v[32];
+    float part = 0.f;
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = F[rows ? Gm::fo(line, t + T * i) : Gm::fo(t + T * i, line)];
+#pragma unroll 1
+    for (int h = 0; h < nh; ++h) {
+      group_fft<LN>(v, grp, stw);
+      if (h != 0) continue;
+      if (rows) {
+        // v = swap(IDFT_x(B)) = swap(sqrt(N) P_M u^nu): gap to S and Eq. (e:PS)
+#pragma unroll
+        for (int i = 0; i < 32; ++i) {
+          const float vx = v[i].y;
+          const float vy = v[i].x;
+          const float a2 = vx * vx + vy * vy;
+          const float rs = rsqrtf(a2);
+          const float mag = a2 > 0.f ? a2 * rs : 0.f;
+          const float d = mag * inv_sqrt_n - 1.f;
+          part += d * d;
+          v[i] = a2 > 0.f ? make_float2(vx * rs, vy * rs) : make_float2(1.f, 0.f);
+        }
+        if (last) small_phase_out(p, moff, line, t, v, grp);
+      } else {
+        // v = Y = F u^nu along this column: residual and Eq. (e:Mhat)
+        const float* mcol = mT + line * Gm::MLD + t;
+#pragma unroll
+        for (int i = 0; i < 32; ++i) {
+          const float m = mcol[T * i];
+          const float2 Y = v[i];
+          const float a2 = Y.x * Y.x + Y.y * Y.y;
+          const float rs = rsqrtf(a2);
+          const float mag = a2 > 0.f ? a2 * rs : 0.f;
+          const float d = mag * inv_sqrt_n - m;
+          part += d * d;
           const float f = m * rs;
           const float2 Yh = a2 > 0.f ? make_float2(Y.x * f, Y.y * f) : make_float2(m, 0.f);
           v[i] = make_float2(Yh.y, Yh.x);  // swapped: the next forward DFT acts as the inverse
         }
       }
-      if constexpr (KIND == kSmallCol) {
-        group_fft<LN>(v, grp, stw);
+    }
+    if (nh == 2) {
 #pragma unroll
-        for (int i = 0; i < 32; ++i) F[Gm::fo(t + T * i, c)] = v[i];
-      }
+      for (int i = 0; i < 32; ++i) F[rows ? Gm::fo(line, t + T * i) : Gm::fo(t + T * i, line)] = v[i];
     }
     acc += static_cast<double>(part);
   }
@@ -198,7 +258,12 @@ __global__ void __launch_bounds__(SmallGeom<LX, LY>::NT) gs_small(const Params p
     acc += static_cast<double>(x);
   }
   if (__syncthreads_or(bad)) acc = __longlong_as_double(0x7ff8000000000000ll);
-  const double total = small_sum<NT>(acc, red);
+  {
+    const double t0 = small_sum<NT>(acc, red);
+    if (threadIdx.x == 0) red[0] = t0;  // to every thread
+    __syncthreads();
+  }
+  const double total = red[0];
   if (!(total > 0.0) || !(total <= DBL_MAX)) {
     // rejected: phase untouched, gaps NaN, GS_ENUMERIC
     if (threadIdx.x == 0) atomicCAS(p.status, 0, GS_ENUMERIC);
@@ -224,16 +289,37 @@ __global__ void __launch_bounds__(SmallGeom<LX, LY>::NT) gs_small(const Params p
 
   const int K = p.iters;
   small_pass<LX, LY, kSmallInit>(p, moff, K == 0, F, mT, X, twr, twc);
-  for (int nu = 0; nu < K; ++nu) {
-    const double rc = small_sum<NT>(small_pass<LX, LY, kSmallCol>(p, moff, false, F, mT, X, twr, twc), red);
-    if (r_out && threadIdx.x == 0) r_out[nu] = sqrt(rc / energy);
-    const double gr = small_sum<NT>(small_pass<LX, LY, kSmallRow>(p, moff, nu == K - 1, F, mT, X, twr, twc), red);
-    if (g_out && threadIdx.x == 0) g_out[nu] = sqrt(gr / energy);
+  // pass q: column pass of iteration q/2 (q even), row pass (q odd)
+#pragma unroll 1
+  for (int q = 0; q < 2 * K; ++q) {
+    const bool rows = (q & 1) != 0;
+    const int nu = q >> 1;
+    const bool last = rows && nu == K - 1;
+    double a;
+    if constexpr (LX == LY) {
+      a = small_pass_hot<LX, LY, LX, true, true>(p, moff, rows ? kSmallRow : kSmallCol, last, F, mT, X, twr);
+    } else {
+      a = rows ? small_pass_hot<LX, LY, LX, true, false>(p, moff, kSmallRow, last, F, mT, X, twr)
+               : small_pass_hot<LX, LY, LY, false, true>(p, moff, kSmallCol, false, F, mT, X, twc);
+    }
+    // the raw sum now, the normalisation after the loop (an FP64 division
+    // and square root on one thread would hold up the next pass)
+    const double sum = small_sum<NT>(a, red);
+    if (threadIdx.x == 0) {
+      double* const out = rows ? g_out : r_out;
+      if (out) out[nu] = sum;
+    }
   }
   if (p.final_resid) {
     const double rc = small_sum<NT>(small_pass<LX, LY, kSmallResid>(p, moff, false, F, mT, X, twr, twc), red);
-    if (r_out && threadIdx.x == 0) r_out[K] = sqrt(rc / energy);
+    if (r_out && threadIdx.x == 0) r_out[K] = rc;
   }
+  __syncthreads();  // thread 0's sums are visible to the block
+  const int nr = K + (p.final_resid ? 1 : 0);
+  if (r_out)
+    for (int e = threadIdx.x; e < nr; e += NT) r_out[e] = sqrt(r_out[e] / energy);
+  if (g_out)
+    for (int e = threadIdx.x; e < K; e += NT) g_out[e] = sqrt(g_out[e] / energy);
 }
 
 }  // namespace gsk
