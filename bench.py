@@ -198,21 +198,36 @@ def oracle_mask_ms(I, phi0, iters_total, sample_iters):
     return 1e3 * (t_zero + iters_total * per_iter), t_zero + t_k
 
 
-def cpu_baseline(I, phi0, iters, budget_s=12.0):
+def cpu_baseline(I, phi0, iters, budget_s=12.0, budget_1t_s=6.0):
+    """The oracle on the host cores: all of them (the FFT's threads), and one."""
     import oracle.gs_oracle as O
 
-    # estimate the cost of one iteration, then fill the budget
-    _, spent = oracle_mask_ms(I, phi0, iters, 1)
-    k = int(max(1, min(iters, budget_s / max(spent, 1e-3))))
-    ms, _ = oracle_mask_ms(I, phi0, iters, k)
-    return {
+    def sample(budget):
+        # estimate the cost of one iteration, then fill the budget
+        _, spent = oracle_mask_ms(I, phi0, iters, 1)
+        k = int(max(1, min(iters, budget / max(spent, 1e-3))))
+        ms, _ = oracle_mask_ms(I, phi0, iters, k)
+        return ms, k
+
+    ms, k = sample(budget_s)
+    cores = O.WORKERS
+    out = {
         "value": round(ms, 3),
         "unit": UNIT,
-        "cores": O.WORKERS,
+        "cores": cores,
         "kind": "oracle",
         "sample": f"FP64 oracle on the {WORKLOAD} target: 0 and {k} iterations timed, scaled to {iters} "
-                  f"iterations; FFT by scipy/pocketfft with {O.WORKERS} threads, elementwise numpy on 1",
+                  f"iterations; FFT by scipy/pocketfft with {cores} threads, elementwise numpy on 1",
     }
+    if budget_1t_s > 0 and cores > 1:
+        O.WORKERS = 1
+        try:
+            ms1, k1 = sample(budget_1t_s)
+        finally:
+            O.WORKERS = cores
+        out["one_thread"] = {"value": round(ms1, 3), "unit": UNIT, "cores": 1,
+                             "sample": f"the same, FFT on 1 thread: 0 and {k1} iterations, scaled to {iters}"}
+    return out
 
 
 def run_reference(args):
