@@ -71,9 +71,10 @@ def kernel_sources_sha() -> str:
     return h.hexdigest()
 
 
-def measured_traffic():
-    """DRAM bytes per launch of the iteration kernel from the committed ncu
-    capture, or None when the kernel sources changed since that capture."""
+def measured_traffic(key="dram_bytes_per_launch"):
+    """Bytes per launch of the iteration kernel from the committed ncu capture
+    (DRAM by default, or key="l2_bytes_per_launch"), or None when the kernel
+    sources changed since that capture."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as f:
@@ -82,7 +83,28 @@ def measured_traffic():
         return None
     if rec.get("csrc_sha256") != kernel_sources_sha():
         return None
-    return rec.get("dram_bytes_per_launch")
+    return rec.get(key)
+
+
+def l2_copy_gbs(dev, stream, mib=40, reps=100):
+    """Device-to-device copy bandwidth with both buffers resident in L2 (two
+    40 MiB buffers within the 126 MB L2), read + write bytes per second: the
+    L2 roof of a kernel whose working set stays in L2."""
+    import torch
+
+    n = mib * (1 << 20) // 4
+    a = torch.ones(n, dtype=torch.float32, device=dev)
+    b = torch.empty_like(a)
+    with torch.cuda.stream(stream):
+        for _ in range(5):
+            b.copy_(a)
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        for _ in range(reps):
+            b.copy_(a)
+        t1.record(stream)
+    torch.cuda.synchronize(dev)
+    return 2 * n * 4 * reps / (t0.elapsed_time(t1) * 1e-3) / 1e9
 
 
 def peaks():
@@ -638,6 +660,8 @@ def run_gpu(args):
     alu_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12  # FP32 FMA lanes x 2 flops x max clock
     achieved_tf = flops_alg / (mean_ms * 1e-3) / 1e12
     traffic = measured_traffic()
+    l2_traffic = measured_traffic("l2_bytes_per_launch")
+    l2_peak = l2_copy_gbs(dev, stream)
 
     out = {
         "metric": METRIC,
@@ -678,6 +702,9 @@ def run_gpu(args):
             "alu_achieved_tflops": round(achieved_tf, 2),
             "alu_peak_tflops": round(alu_peak, 1),
             "alu_frac": round(achieved_tf / alu_peak, 4),
+            "l2": {"achieved": round(achieved, 1), "peak": round(l2_peak, 1), "unit": "GB/s",
+                   "frac": round(achieved / l2_peak, 4), "traffic": l2_traffic,
+                   "peak_kind": "40 MiB device copy within L2, measured in this run"},
         },
         "clocks": clocks,
         "batched_throughput": batched,
