@@ -65,9 +65,14 @@ def kernel_sources_sha() -> str:
     h = hashlib.sha256()
     for name in sorted(seen):
         path = next(os.path.join(d, name) for d in (csrc, inc) if os.path.exists(os.path.join(d, name)))
+        with open(path) as fh:
+            text = fh.read()
+        # comments and blank lines do not change the kernel
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", "", text)
+        text = "\n".join(line.rstrip() for line in text.splitlines() if line.strip())
         h.update(name.encode())
-        with open(path, "rb") as fh:
-            h.update(fh.read())
+        h.update(text.encode())
     return h.hexdigest()
 
 

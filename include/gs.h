@@ -29,7 +29,8 @@
  *   - nx and ny are powers of two in [8, 4096] or 5-smooth numbers
  *     (2^a 3^b 5^c, such as the 800 x 600 SLM of Sec. V) in [8, 1536].
  *     Grids with both sides powers of two of at least 32 run on the
- *     register-resident kernels; every other grid on the general kernel.
+ *     register-resident kernels (one block per mask when the grid has at
+ *     most 8192 pixels, see gs_run); every other grid on the general kernel.
  *
  * Memory and ordering:
  *   - Pointers named "device" are CUDA device pointers owned by the caller;
