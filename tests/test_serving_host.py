@@ -99,3 +99,11 @@ def test_poisson_stream_recipe():
     for r in reqs:
         assert r.target.shape == (r.n, r.n) and r.target.dtype == np.float32 and r.target.max() > 0
         assert r.target[0, 0] == 0  # DC kept dark
+
+
+def test_plan_lanes_with_equal_weights_gives_every_lane_the_same_share():
+    # the service's default: one 512 lane and two 1024 lanes, 152 SMs
+    plans = SV.plan_lanes([512, 1024], [1, 2], sm_count=152, budget_bytes=2 << 30, iters=30,
+                          workspace_bytes=fake_workspace, max_batch_cap=16, weights=[1.0, 1.0])
+    grids = [p.grid for p in plans]
+    assert sum(grids) == 152 and max(grids) - min(grids) <= 1
