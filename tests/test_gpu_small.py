@@ -74,3 +74,19 @@ def test_small_kernel_batch_of_64():
     for k in (0, 17, 63):
         one = gpu_gs(I[k], P[k], 20)
         _same((ph[k], r[k], g[k], 0), one)
+
+
+def test_small_kernel_without_gap_outputs():
+    # null residual and gap pointers: the phase is unchanged and nothing is written
+    import torch
+
+    from paper_1302_0120_gb300 import GerchbergSaxton
+
+    I, phi0 = _inputs(64, 64, seed=13)
+    with GerchbergSaxton(64, 64) as gs:
+        It, Pt = torch.from_numpy(I).cuda(), torch.from_numpy(phi0).cuda()
+        ph, r, g = gs.run(It, Pt, 11, residuals=False, object_gap=False)
+        assert r is None and g is None
+        assert gs.status() == 0
+        ph = ph.cpu().numpy()
+    assert np.array_equal(ph, gpu_gs(I, phi0, 11)[0])
