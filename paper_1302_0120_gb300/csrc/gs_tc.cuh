@@ -15,11 +15,12 @@
 // [[Fr, -Fi], [Fi, Fr]] of the DFT matrix and the operand stacked as
 // [re; im], issued as mma.sync m16n8k16 tiles (row-major A = DFT matrix,
 // column-major B = data). The DFT-matrix fragments stay in registers for the
-// whole kernel; the data operands are staged in the warp's shared-memory
-// buffer as FP16 and read with ldmatrix, the stage-1 result is written back
-// with stmatrix, and the stage-2 result (FP32) returns to the thread layout
-// through the same buffer. The factor 1/32 before the FP16 rounding of Z and
-// the exact factor 32 after stage 2 are powers of two.
+// whole kernel; the stage-1 operand is staged in the warp's shared-memory
+// buffer as FP16 and read with ldmatrix; the stage-1 result, twiddled and
+// rounded to FP16, feeds stage 2 from registers (its accumulator tiles are
+// the transposed B operand of stage 2); the stage-2 result (FP32) returns to
+// the thread layout through the buffer. The factor 1/32 before the FP16
+// rounding of Z and the exact factor 32 after stage 2 are powers of two.
 //
 // Range: every FP16 value is at most max |x| in magnitude, so inputs must stay
 // below 65504 (the caller checks a bound). Rounding: unit roundoff 2^-11 per
@@ -60,19 +61,6 @@ __device__ __forceinline__ void ldsm_x4(uint32_t (&r)[4], const void* p) {
   asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
                : "r"(smem_u32(p))
-               : "memory");
-}
-
-__device__ __forceinline__ void ldsm_x2(uint32_t& r0, uint32_t& r1, const void* p) {
-  asm volatile("ldmatrix.sync.aligned.m8n8.x2.shared.b16 {%0,%1}, [%2];"
-               : "=r"(r0), "=r"(r1)
-               : "r"(smem_u32(p))
-               : "memory");
-}
-
-__device__ __forceinline__ void stsm_x4(void* p, uint32_t r0, uint32_t r1, uint32_t r2, uint32_t r3) {
-  asm volatile("stmatrix.sync.aligned.m8n8.x4.shared.b16 [%0], {%1,%2,%3,%4};" ::"r"(smem_u32(p)), "r"(r0),
-               "r"(r1), "r"(r2), "r"(r3)
                : "memory");
 }
 
@@ -180,10 +168,8 @@ struct TcFft {
   static constexpr int Q = 32 / R;       // transforms per warp
   static constexpr int KT = R / 8;       // 16-wide tiles along 2R
   static constexpr int XS = 72;          // halves per row of the stage-1 operand (144 bytes)
-  static constexpr int ZS = 2 * R + 8;   // halves per row of the stage-2 operand (odd multiple of 16 bytes)
-  static constexpr int ZG = 32 * ZS;     // halves per transform of the stage-2 operand
   static_assert(R == 8 || R == 16 || R == 32, "tensor-core transforms have length 256, 512 or 1024");
-  static_assert(Q * (N + 8) <= 32 * 33 && ZG * Q * 2 <= kTcWarpBytes, "buffers fit the warp slice");
+  static_assert(Q * (N + 8) <= 32 * 33 && 32 * XS * 2 <= kTcWarpBytes, "buffers fit the warp slice");
 
   const TcStage1& s1;
   const TcStage2<R>& s2;
@@ -238,14 +224,15 @@ struct TcFft {
 #pragma unroll
         for (int kt = 0; kt < 4; ++kt) s1.mma32(acc[mt][nt], mt, kt, b[kt >> 1][2 * (kt & 1)], b[kt >> 1][2 * (kt & 1) + 1]);
     }
-    __syncwarp();  // every lane's operand reads are done before the buffer is rewritten
-
-    // Twiddle, 1/32, FP16; stage-2 operand B of transform gamma: row k1,
-    // re Z at column t, im at R + t.
-    __half* zs = xs;
+    // Twiddle, 1/32, FP16. The stage-2 operand B of transform gamma (K = t,
+    // re then im; N = k1) is the transpose of the stage-1 accumulator (rows
+    // k1, re then im; columns gamma R + t), so this lane's pair of adjacent
+    // columns of an 8-column accumulator tile is exactly a B register: the
+    // packed values stay in registers. z[part][nt][mp][h]: part 0 re, 1 im;
+    // rows k1 = 16 mp + 8 h + g, columns 8 nt + 2c, 8 nt + 2c + 1.
+    uint32_t z[2][4][2][2];
 #pragma unroll
-    for (int nt = 0; nt < 4; ++nt) {
-      uint32_t re[4], im[4];
+    for (int nt = 0; nt < 4; ++nt)
 #pragma unroll
       for (int mp = 0; mp < 2; ++mp)
 #pragma unroll
@@ -255,20 +242,14 @@ struct TcFft {
           const float2 w1 = tw[(slot + 1) * 32 + lane];
           const float2 y0 = cmul(make_float2(acc[mp][nt][2 * h], acc[mp + 2][nt][2 * h]), w0);
           const float2 y1 = cmul(make_float2(acc[mp][nt][2 * h + 1], acc[mp + 2][nt][2 * h + 1]), w1);
-          re[2 * mp + h] = pack_h2(y0.x, y1.x);
-          im[2 * mp + h] = pack_h2(y0.y, y1.y);
+          z[0][nt][mp][h] = pack_h2(y0.x, y1.x);
+          z[1][nt][mp][h] = pack_h2(y0.y, y1.y);
         }
-      const int gamma = (8 * nt) / R;
-      const int t0 = (8 * nt) % R;
-      const int mj = lane >> 3;  // matrix whose row this lane addresses: (mp, h) = (mj / 2, mj % 2)
-      __half* dst = zs + gamma * ZG + (16 * (mj >> 1) + 8 * (mj & 1) + (lane & 7)) * ZS + t0;
-      stsm_x4(dst, re[0], re[1], re[2], re[3]);
-      stsm_x4(dst + R, im[0], im[1], im[2], im[3]);
-    }
-    __syncwarp();
 
     // Stage 2 per transform: tiles [gamma][mt][nt], mt < KT (R = 32: mt 0, 1
-    // real rows, 2, 3 imaginary rows).
+    // real rows, 2, 3 imaginary rows). B tile (kt, nt) holds rows k = 16 kt
+    // + 2c (+1) in b0 and k + 8 in b1, row k being re Z[.][k] for k < R and
+    // im Z[.][k - R] otherwise, at columns k1 = 8 nt + g.
     float out[Q][KT][4][4];
 #pragma unroll
     for (int gamma = 0; gamma < Q; ++gamma)
@@ -282,25 +263,14 @@ struct TcFft {
     for (int gamma = 0; gamma < Q; ++gamma) {
 #pragma unroll
       for (int nt = 0; nt < 4; ++nt) {
-        uint32_t b[KT][2];
-        const __half* src = zs + gamma * ZG + (8 * nt + (lane & 7)) * ZS;
-        if constexpr (KT == 4) {
-          uint32_t r0[4], r1[4];
-          ldsm_x4(r0, src + 8 * (lane >> 3));
-          ldsm_x4(r1, src + 32 + 8 * (lane >> 3));
-          b[0][0] = r0[0]; b[0][1] = r0[1]; b[1][0] = r0[2]; b[1][1] = r0[3];
-          b[2][0] = r1[0]; b[2][1] = r1[1]; b[3][0] = r1[2]; b[3][1] = r1[3];
-        } else if constexpr (KT == 2) {
-          uint32_t r0[4];
-          ldsm_x4(r0, src + 8 * (lane >> 3));
-          b[0][0] = r0[0]; b[0][1] = r0[1]; b[1][0] = r0[2]; b[1][1] = r0[3];
-        } else {
-          ldsm_x2(b[0][0], b[0][1], src + 8 * ((lane >> 3) & 1));
+#pragma unroll
+        for (int kt = 0; kt < KT; ++kt) {
+          const int ka = 16 * kt, kb = 16 * kt + 8;  // first rows of b0 and b1
+          const uint32_t b0 = z[ka < R ? 0 : 1][(gamma * R + ka % R) >> 3][nt >> 1][nt & 1];
+          const uint32_t b1 = z[kb < R ? 0 : 1][(gamma * R + kb % R) >> 3][nt >> 1][nt & 1];
+#pragma unroll
+          for (int mt = 0; mt < KT; ++mt) mma2(out[gamma][mt][nt], mt, kt, b0, b1);
         }
-#pragma unroll
-        for (int mt = 0; mt < KT; ++mt)
-#pragma unroll
-          for (int kt = 0; kt < KT; ++kt) mma2(out[gamma][mt][nt], mt, kt, b[kt][0], b[kt][1]);
       }
     }
     __syncwarp();  // operand reads done before the return buffer overwrites them
