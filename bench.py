@@ -225,35 +225,58 @@ def oracle_mask_ms(I, phi0, iters_total, sample_iters):
     return 1e3 * (t_zero + iters_total * per_iter), t_zero + t_k
 
 
-def cpu_baseline(I, phi0, iters, budget_s=12.0, budget_1t_s=6.0):
-    """The oracle on the host cores: all of them (the FFT's threads), and one."""
-    import oracle.gs_oracle as O
+def blas_threads_env(threads: int) -> dict:
+    """Environment that fixes the oracle's BLAS thread count (read when numpy
+    first loads its BLAS, so it must be set before numpy is imported)."""
+    t = str(int(threads))
+    return {"OPENBLAS_NUM_THREADS": t, "OMP_NUM_THREADS": t, "MKL_NUM_THREADS": t}
 
-    def sample(budget):
+
+def run_oracle_sample(args):
+    """Subprocess leg of the CPU baseline: one timed oracle sample, as JSON."""
+    from paper_1302_0120_gb300 import synthetic as S
+
+    I, phi0, iters = S.workload(WORKLOAD, seed=0)
+    ms, spent = oracle_mask_ms(I, phi0, iters, args.oracle_sample)
+    print(json.dumps({"ms": ms, "spent_s": spent, "iters": iters}))
+    return 0
+
+
+def oracle_sample(sample_iters: int, threads: int) -> dict:
+    """The oracle timed in a fresh process whose BLAS runs `threads` threads."""
+    env = dict(os.environ, **blas_threads_env(threads))
+    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-sample", str(sample_iters)],
+                       env=env, capture_output=True, text=True, timeout=900, cwd=ROOT)
+    if r.returncode != 0:
+        raise RuntimeError(f"oracle sample failed: {r.stderr[-2000:]}")
+    return json.loads([ln for ln in r.stdout.splitlines() if ln.startswith("{")][-1])
+
+
+def cpu_baseline(iters, budget_s=12.0, budget_1t_s=6.0):
+    """The oracle on the host cores: BLAS on all of them, and on one."""
+    cores = os.cpu_count() or 1
+
+    def sample(threads, budget):
         # estimate the cost of one iteration, then fill the budget
-        _, spent = oracle_mask_ms(I, phi0, iters, 1)
-        k = int(max(1, min(iters, budget / max(spent, 1e-3))))
-        ms, _ = oracle_mask_ms(I, phi0, iters, k)
-        return ms, k
+        first = oracle_sample(1, threads)
+        k = int(max(1, min(iters, budget / max(first["spent_s"], 1e-3))))
+        return oracle_sample(k, threads)["ms"], k
 
-    ms, k = sample(budget_s)
-    cores = O.WORKERS
+    ms, k = sample(cores, budget_s)
     out = {
         "value": round(ms, 3),
         "unit": UNIT,
         "cores": cores,
         "kind": "oracle",
+        "extrapolated": True,
         "sample": f"FP64 oracle on the {WORKLOAD} target: 0 and {k} iterations timed, scaled to {iters} "
-                  f"iterations; FFT by scipy/pocketfft with {cores} threads, elementwise numpy on 1",
+                  f"iterations; its own FFT (DFT-matrix products on {cores} BLAS threads), elementwise numpy "
+                  f"on one thread",
     }
     if budget_1t_s > 0 and cores > 1:
-        O.WORKERS = 1
-        try:
-            ms1, k1 = sample(budget_1t_s)
-        finally:
-            O.WORKERS = cores
-        out["one_thread"] = {"value": round(ms1, 3), "unit": UNIT, "cores": 1,
-                             "sample": f"the same, FFT on 1 thread: 0 and {k1} iterations, scaled to {iters}"}
+        ms1, k1 = sample(1, budget_1t_s)
+        out["one_thread"] = {"value": round(ms1, 3), "unit": UNIT, "cores": 1, "extrapolated": True,
+                             "sample": f"the same on one BLAS thread: 0 and {k1} iterations, scaled to {iters}"}
     return out
 
 
@@ -263,8 +286,8 @@ def run_reference(args):
     if rank != 0:
         return 0
     from paper_1302_0120_gb300 import synthetic as S
-    import oracle.gs_oracle as O
 
+    cores = int(os.environ.get("OPENBLAS_NUM_THREADS", "0")) or (os.cpu_count() or 1)
     I, phi0, iters = S.workload(WORKLOAD, seed=0)
     sample = max(1, args.ref_sample_iters)
     for _ in range(args.warmup):
@@ -290,10 +313,16 @@ def run_reference(args):
         "vs_baseline": None,
         "dtype": "f64",
         "data": "synthetic",
+        # each step times 0 and `sample` iterations and scales them to a whole
+        # mask of `iters` iterations: ms_per_step is a per-mask estimate, not
+        # the wall time of the step
+        "extrapolated": True,
         "config": {"workload": f"{WORKLOAD}: 1024x1024, 50 Gaussian spots, 100 GS iterations, final residual",
                    "flush_l2": "n/a (CPU)"},
-        "cpu_baseline": {"value": round(value, 3), "unit": UNIT, "cores": O.WORKERS, "kind": "oracle",
-                         "sample": f"per step: 0 and {sample} oracle iterations timed, scaled to {iters}"},
+        "cpu_baseline": {"value": round(value, 3), "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "extrapolated": True,
+                         "sample": f"per step: 0 and {sample} oracle iterations timed, scaled to {iters}; "
+                                   f"its own FFT on {cores} BLAS threads"},
         "e2e": {"value": round(value, 3), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
         "wall_s": round(wall, 3),
     }
@@ -662,7 +691,7 @@ def run_gpu(args):
     bytes_alg = (BYTES_PER_PX_FIXED + BYTES_PER_PX_ITER * iters) * n
     achieved = bytes_alg / (mean_ms * 1e-3) / 1e9
     flops_alg = iters * (2 * 5 * n * math.log2(n) + FLOPS_PROJ_PER_PX * n)
-    alu_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12  # FP32 FMA lanes x 2 flops x max clock
+    alu_peak = B.gs_fp32_peak(stream.cuda_stream)  # measured FMA throughput of this GPU
     achieved_tf = flops_alg / (mean_ms * 1e-3) / 1e12
     traffic = measured_traffic()
     l2_traffic = measured_traffic("l2_bytes_per_launch")
@@ -706,6 +735,7 @@ def run_gpu(args):
             "peak_kind": peak_kind,
             "alu_achieved_tflops": round(achieved_tf, 2),
             "alu_peak_tflops": round(alu_peak, 1),
+            "alu_peak_kind": "FMA chains on every SM, measured in this run (gs_fp32_peak)",
             "alu_frac": round(achieved_tf / alu_peak, 4),
             "l2": {"achieved": round(achieved, 1), "peak": round(l2_peak, 1), "unit": "GB/s",
                    "frac": round(achieved / l2_peak, 4), "traffic": l2_traffic,
@@ -723,7 +753,7 @@ def run_gpu(args):
         "wall_s": round(wall, 3),
     }
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline(I_np, phi_np, iters, budget_s=args.cpu_budget_s)
+        out["cpu_baseline"] = cpu_baseline(iters, budget_s=args.cpu_budget_s)
     if rank == 0:
         print(json.dumps(out))
     gs.close()
@@ -752,10 +782,16 @@ def main(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget-s", type=float, default=12.0)
     ap.add_argument("--ref-sample-iters", type=int, default=2)
+    ap.add_argument("--oracle-sample", type=int, default=0, help=argparse.SUPPRESS)
     args = ap.parse_args(argv)
+    if args.oracle_sample > 0:
+        return run_oracle_sample(args)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
+        if "numpy" not in sys.modules:  # BLAS on every host core, stated in the line
+            for k, v in blas_threads_env(os.environ.get("OPENBLAS_NUM_THREADS") or os.cpu_count() or 1).items():
+                os.environ.setdefault(k, v)
         return run_reference(args)
     return run_gpu(args)
 

@@ -422,6 +422,10 @@ int gs_adam_step(float* phase, const float* grad, float* m, float* v, long long 
  * This call performs the same operation as gs_run (same argument meaning,
  * layout and results) with the library's own static scratch instead of a
  * context workspace, and calls no cudaMalloc, cudaFree or allocating routine.
+ * It always runs the persistent kernel with gs_run's automatic grid (one
+ * block per 4096 pixels, small grids up to 32 blocks), also for the grids of
+ * at most 8192 pixels that gs_run hands to its one-block-per-mask kernel:
+ * the iterates are the same, such a small grid only runs slower here.
  *   nx, ny          powers of two in [32, 4096] with nx * ny <= 262144
  *                   (512 x 512): the static scratch holds one such grid.
  *                   Larger grids return GS_EINVAL (use gs_create/gs_run).
@@ -445,6 +449,20 @@ int gs_adam_step(float* phase, const float* grad, float* m, float* v, long long 
 int gs_run_noalloc(int nx, int ny, unsigned flags, void* stream, const float* target_intensity,
                    const float* phase_in, int iters, float* phase_out, double* residual_out,
                    double* object_gap_out, int* device_status);
+
+/*
+ * gs_fp32_peak -- measured FP32 fused multiply-add throughput of the current
+ * device (a diagnostic; the paper has no counterpart).
+ *
+ * Launches a kernel of independent FMA chains on every SM (as many blocks
+ * as stay resident), times it with CUDA events on `stream` (a cudaStream_t,
+ * or NULL for the legacy default stream) and writes 2 x FMAs / second in
+ * TFLOP/s to *tflops_out (host), the best of three timed launches after one
+ * warm-up. The denominator of the FP32 roofline of the iteration kernels.
+ * Synchronous (waits for the timed launches). Returns GS_EINVAL for a NULL
+ * tflops_out, GS_ECUDA if a CUDA call fails.
+ */
+int gs_fp32_peak(double* tflops_out, void* stream);
 
 /* gs_strerror -- static English text for a status code (never NULL). */
 const char* gs_strerror(int code);

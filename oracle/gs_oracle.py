@@ -5,8 +5,9 @@ benchmark's CPU-baseline leg, never by the product path.
 
 Every function cites the passage of the paper it restates (Kramer, Hagemann,
 Luke, "Real-Time Phase Masks for Interactive Stimulation of Optogenetic
-Neurons"). The code follows the paper's steps in its order and notation; the
-only library primitive used as a step is the FFT (scipy.fft, pocketfft).
+Neurons"). The code follows the paper's steps in its order and notation. The
+Fourier transform is the oracle's own (oracle/dft.py: direct DFT sums and the
+mixed-radix Cooley-Tukey factorisation), with no FFT library behind it.
 
 Conventions (the paper fixes none of them; these are the readings used):
   * A grid is stored as an array ``[ny, nx]`` (row-major, element ``(j, k)``
@@ -26,12 +27,13 @@ Conventions (the paper fixes none of them; these are the readings used):
     ``u0 = P_S(F^{-1} m)``; the default start is ``u0 = p exp(i phi0)``.
 
 Parity status:
-  fft2u / ifft2u, target_amplitude, proj_S, proj_M, gap_to_M, gap_to_S,
+  fft2u / ifft2u (oracle/dft.py), target_amplitude, proj_S, proj_M, gap_to_M, gap_to_S,
   gs_step, gs_run, consistent_target, intensity_loss, intensity_loss_grad:
       pinned by the tests in tests/test_oracle_pins.py (brute-force DFT,
       Parseval, idempotence, nearest-point property, the interleaved gap chain,
       fixed points of consistent targets, scale invariance, finite
-      differences).
+      differences, closed-form values of the loss for constant and
+      plane-wave phases).
   physical_error: parity unpinned. The paper prints no value of E; its printed
       formula is restated under the reading documented on the function, and
       only special cases that follow from its definition are tested.
@@ -39,19 +41,14 @@ Parity status:
 
 from __future__ import annotations
 
-import os
-
 import numpy as np
-import scipy.fft as _sfft
+
+from . import dft as _dft
 
 # Tolerances of the physical error, Sec. II (relative on lit pixels, absolute
 # on dark pixels).
 TL_LIT = 0.1
 TD_DARK = 3e-4
-
-# Threads handed to the library FFT. The oracle is never tuned; this only lets
-# large parity cases finish in seconds.
-WORKERS = int(os.environ.get("ORACLE_WORKERS", "0")) or (os.cpu_count() or 1)
 
 
 def _complex_dtype(real_dtype):
@@ -64,12 +61,14 @@ def fft2u(x: np.ndarray) -> np.ndarray:
     The Fourier transform F of Sec. II that maps the SLM field to the
     stimulation pattern (Fraunhofer diffraction), with numpy's sign convention.
     """
-    return _sfft.fft2(x, norm="ortho", workers=WORKERS)
+    x = np.asarray(x)
+    return _dft.dft2(x) / float(np.sqrt(x.shape[-1] * x.shape[-2]))  # a Python float keeps FP32 runs in FP32
 
 
 def ifft2u(X: np.ndarray) -> np.ndarray:
     """Unitary inverse 2D DFT ``F_u^{-1} X`` (the ``F^{-1}`` of Eq. e:PM)."""
-    return _sfft.ifft2(X, norm="ortho", workers=WORKERS)
+    X = np.asarray(X)
+    return _dft.idft2(X) / float(np.sqrt(X.shape[-1] * X.shape[-2]))
 
 
 def target_amplitude(I: np.ndarray, dtype=np.float64, energy: float | None = None) -> np.ndarray:
@@ -224,7 +223,7 @@ def consistent_target(phi_true) -> np.ndarray:
     gives the same problem).
     """
     x = np.exp(1j * np.asarray(phi_true, dtype=np.float32).astype(np.float64))
-    return np.abs(_sfft.fft2(x, workers=WORKERS)) ** 2
+    return np.abs(_dft.dft2(x)) ** 2
 
 
 def physical_error(I, u, t_l: float = TL_LIT, t_d: float = TD_DARK):
@@ -268,7 +267,7 @@ def intensity_loss(phi, I, p=None) -> float:
     phi = np.asarray(phi, dtype=np.float64)
     I = np.asarray(I, dtype=np.float64)
     pw = 1.0 if p is None else np.asarray(p, dtype=np.float64)
-    y = _sfft.fft2(pw * np.exp(1j * phi), workers=WORKERS)
+    y = _dft.dft2(pw * np.exp(1j * phi))
     r = np.abs(y) ** 2 / phi.size - I
     return float(np.sum(r * r))
 
@@ -284,7 +283,7 @@ def intensity_loss_grad(phi, I, p=None) -> np.ndarray:
     I = np.asarray(I, dtype=np.float64)
     pw = 1.0 if p is None else np.asarray(p, dtype=np.float64)
     x = pw * np.exp(1j * phi)
-    y = _sfft.fft2(x, workers=WORKERS)
+    y = _dft.dft2(x)
     r = np.abs(y) ** 2 / phi.size - I
-    z = _sfft.ifft2(r * y, workers=WORKERS)
+    z = _dft.idft2(r * y) / phi.size
     return 4.0 * np.imag(np.conj(x) * z)

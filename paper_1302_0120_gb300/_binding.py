@@ -54,6 +54,7 @@ SIGNATURES = {
     "gs_check_workspace": (_c_int, [_vp]),
     "gs_test_corrupt_workspace": (_c_int, [_vp]),
     "gs_get_trace": (_c_int, [_vp, _vp, _c_int, ctypes.POINTER(_c_int), ctypes.POINTER(_c_int)]),
+    "gs_fp32_peak": (_c_int, [ctypes.POINTER(ctypes.c_double), _vp]),
     "gs_adam_step": (_c_int, [_vp, _vp, _vp, _vp, ctypes.c_longlong, _vp, ctypes.c_float, ctypes.c_float,
                               ctypes.c_float, ctypes.c_float, _vp]),
 }
@@ -269,6 +270,15 @@ def gs_run_noalloc(nx: int, ny: int, flags: int, stream: int, target_intensity: 
     return lib().gs_run_noalloc(int(nx), int(ny), int(flags), _vp(stream or 0), _vp(target_intensity),
                                 _vp(phase_in), int(iters), _vp(phase_out), _vp(residual_out or 0),
                                 _vp(object_gap_out or 0), _vp(device_status or 0))
+
+
+def gs_fp32_peak(stream: int | None = None) -> float:
+    """Measured FP32 FMA throughput of the current device in TFLOP/s (synchronous). Raises GSError."""
+    out = ctypes.c_double(0.0)
+    rc = lib().gs_fp32_peak(ctypes.byref(out), _vp(stream or 0))
+    if rc != GS_OK:
+        raise GSError(rc, "gs_fp32_peak")
+    return out.value
 
 
 def gs_destroy(ctx: int) -> int:

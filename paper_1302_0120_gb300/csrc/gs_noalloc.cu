@@ -132,7 +132,12 @@ extern "C" int gs_run_noalloc(int nx, int ny, unsigned flags, void* stream, cons
     cudaGetLastError();
     return GS_ECUDA;
   }
-  int grid = static_cast<int>((static_cast<long long>(nx) * ny) / 4096);
+  // the context path's rule: one block per 4096 pixels, and small grids up
+  // to 32 blocks (one per 2048 pixels)
+  const long long npx = static_cast<long long>(nx) * ny;
+  int grid = static_cast<int>(npx / 4096);
+  const int small = static_cast<int>(npx / 2048 < 32 ? npx / 2048 : 32);
+  if (grid < small) grid = small;
   if (grid > num_sms * per_sm) grid = num_sms * per_sm;
   if (grid > kMaxGrid) grid = kMaxGrid;
   if (grid < 1) grid = 1;

@@ -36,11 +36,17 @@ class LossContext:
         for x, nm in ((target, "target"), (phase, "phase")):
             if not (x.is_cuda and x.dtype == torch.float32 and x.is_contiguous() and tuple(x.shape) == (self.n, self.n)):
                 raise ValueError(f"{nm} must be a contiguous float32 CUDA tensor of shape ({self.n}, {self.n})")
-        with torch.cuda.stream(self.stream):
-            loss = torch.empty(1, dtype=torch.float64, device=phase.device)
-            grad = torch.empty_like(phase) if want_grad else None
+        # The launch runs on the context's stream: it waits for the work the
+        # caller queued on its current stream (the writes of target and
+        # phase), and the caller's stream waits for the launch before it
+        # touches loss and grad (or overwrites phase, as an optimiser step does).
+        cur = torch.cuda.current_stream(phase.device)
+        loss = torch.empty(1, dtype=torch.float64, device=phase.device)
+        grad = torch.empty_like(phase) if want_grad else None
+        self.stream.wait_stream(cur)
         rc = B.gs_loss_grad(self.handle, target.data_ptr(), phase.data_ptr(), loss.data_ptr(),
                             grad.data_ptr() if grad is not None else 0)
+        cur.wait_stream(self.stream)
         if rc != B.GS_OK:
             raise B.GSError(rc, "gs_loss_grad")
         return loss, grad

@@ -16,8 +16,9 @@ module serves a stream of such requests on one GPU:
   other lanes keep working: requests that arrive while others are on the GPU
   join as soon as a lane frees up.
 * Warm starts: every mask of a launch starts from the most recent mask of its
-  class (kept on the device); the last mask of a launch becomes the next warm
-  start.
+  lane (kept on the device, one warm-start buffer per lane); the last mask of
+  a launch becomes that lane's next warm start. A class with several lanes
+  therefore keeps one warm start per lane, not one for the class.
 * The per-launch sequence (target upload from pinned host memory, warm-start
   copies, the batched run, the warm-start update) is captured once per lane
   and batch size as a CUDA graph and replayed.

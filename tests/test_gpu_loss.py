@@ -121,6 +121,36 @@ def test_graph_adam_matches_eager():
     lc_e.close()
 
 
+def test_side_stream_eager_steps_match_current_stream():
+    """optimize_phase with its defaults and fewer than four steps runs the
+    eager path on a context with its own stream while torch's Adam writes the
+    phase on the current stream: the two are ordered, so the result equals an
+    eager run whose context uses the current stream. A user-built context on
+    a side stream gives the same loss as one on the current stream."""
+    import torch
+
+    from paper_1302_0120_gb300.differentiable import LossContext, intensity_loss, optimize_phase
+
+    n = 256
+    I = torch.from_numpy(normalized_target(17, n, 30)).cuda()
+    phi0 = torch.from_numpy(S.random_phase(18, n, n)).cuda()
+    ph_side, loss_side = optimize_phase(I, phi0, steps=3, lr=0.05)  # graph=True, lctx=None
+    lc_cur = LossContext(n)
+    ph_cur, loss_cur = optimize_phase(I, phi0, steps=3, lr=0.05, lctx=lc_cur, graph=False)
+    assert lc_cur.status() == 0
+    assert np.array_equal(loss_side, loss_cur)
+    assert torch.equal(ph_side, ph_cur)
+    lc_side = LossContext(n, stream=torch.cuda.Stream())
+    for _ in range(3):
+        phi = phi0 * 1.01  # written on the current stream just before the call
+        a = intensity_loss(phi, I, lc_side)
+        b = intensity_loss(phi, I, lc_cur)
+        assert float(a) == float(b)
+    assert lc_side.status() == 0
+    lc_side.close()
+    lc_cur.close()
+
+
 def gpu_physical_error(I, phi, p=None):
     import torch
 

@@ -11,18 +11,24 @@ from tests.gpu_util import aligned_rel_err
 pytestmark = pytest.mark.gpu
 
 
-def test_each_result_same_alone_and_in_the_mix():
+@pytest.mark.parametrize("sizes,rate,seconds,budget", [((128, 256), 4000.0, 0.08, 256 << 20),
+                                                        ((512, 1024), 2000.0, 0.15, None)])
+def test_each_result_same_alone_and_in_the_mix(sizes, rate, seconds, budget):
+    """Small sizes at a high rate (many shared launches), and the 512^2 /
+    1024^2 sizes the service runs at."""
     import torch
 
     from paper_1302_0120_gb300 import GerchbergSaxton
     from paper_1302_0120_gb300 import serving as SV
 
-    summ, sch, ex = SV.run_service(rate_hz=4000.0, seconds=0.08, sizes=(128, 256), lanes=(1, 2), iters=30,
-                                   budget_bytes=256 << 20, record=True, warmup_s=0.0, max_batch_cap=6)
+    kw = {} if budget is None else {"budget_bytes": budget}
+    summ, sch, ex = SV.run_service(rate_hz=rate, seconds=seconds, sizes=sizes, lanes=(1, 2), iters=30,
+                                   record=True, warmup_s=0.0, max_batch_cap=6, **kw)
     try:
         done = sorted(sch.done, key=lambda r: r.rid)
         assert len(done) == summ["requests"] > 50
         assert max(r.slot for r in done) > 0  # some requests shared a launch
+        assert {r.n for r in done} == set(sizes)
         picks = done[:: max(1, len(done) // 12)]
         for r in picks:
             with GerchbergSaxton(r.n, r.n) as gs:

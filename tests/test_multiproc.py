@@ -46,7 +46,7 @@ def run_torchrun(args, timeout=300):
     port = free_port()
     cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node=2",
            "--master-addr", "127.0.0.1", "--master-port", str(port)] + args
-    env = dict(os.environ, OMP_NUM_THREADS="1", ORACLE_WORKERS="2")
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="2")
     return subprocess.run(cmd, capture_output=True, text=True, timeout=timeout, cwd=ROOT, env=env)
 
 

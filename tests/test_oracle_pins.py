@@ -49,9 +49,42 @@ def check_fft_direct(shape, seed=0):
     assert err2 <= 1e-12, err2
 
 
-@pytest.mark.parametrize("shape", [(8, 8), (16, 16), (32, 32), (8, 32), (32, 8), (6, 10), (15, 12), (24, 20), (45, 8)])
+@pytest.mark.parametrize("shape", [(8, 8), (16, 16), (32, 32), (8, 32), (32, 8), (6, 10), (15, 12), (24, 20), (45, 8),
+                                   (72, 80), (96, 67)])
 def test_fft_matches_direct_dft(shape):
     check_fft_direct(shape)
+
+
+def direct_dft1(x):
+    """Unnormalised DFT along the last axis by the defining sum, one output
+    frequency at a time (angles reduced exactly in integers)."""
+    n = x.shape[-1]
+    j = np.arange(n)
+    out = np.empty(x.shape, dtype=np.complex128)
+    for k in range(n):
+        a = 2 * np.pi * ((j * k) % n) / n
+        out[..., k] = np.sum(x * (np.cos(a) - 1j * np.sin(a)), axis=-1)
+    return out
+
+
+def check_fft_long(n, seed=2):
+    """Lengths above the direct-sum limit, which the oracle's FFT computes by
+    the Cooley-Tukey factorisation (powers of two, 5-smooth SLM sides of
+    Sec. V, a prime factor): against the defining sum."""
+    from oracle import dft as D
+
+    rng = np.random.default_rng(seed + n)
+    x = rand_complex(rng, (2, n))
+    ref = direct_dft1(x)
+    err = np.linalg.norm(D.dft_last(x) - ref) / np.linalg.norm(ref)
+    assert err <= 1e-12, (n, err)
+    back = D.idft_last(ref) / n
+    assert np.linalg.norm(back - x) / np.linalg.norm(x) <= 1e-12
+
+
+@pytest.mark.parametrize("n", [96, 128, 134, 600, 800, 1024, 1536, 4096])
+def test_fft_long_lengths_match_direct_dft(n):
+    check_fft_long(n)
 
 
 def check_fft_identities(ny=32, nx=16, seed=1):
@@ -161,11 +194,17 @@ def check_proj_M(seed=4):
     for eps in (1e-3, -1e-3):
         y = O.ifft2u(Fv * np.exp(1j * eps * rng.standard_normal(m.shape)))
         assert d0 <= np.linalg.norm(u - y) + 1e-12
-    # zero rule: where F u vanishes the result takes amplitude m with phase 0
-    u0 = np.ones((8, 8), complex)  # F u is a delta at DC, zero elsewhere
-    mm = np.full((8, 8), 1.0)
-    w = O.fft2u(O.proj_M(u0, mm))
-    assert np.allclose(w.ravel()[1:], 1.0, atol=1e-12)
+    # zero rule of Eq. (e:Mhat): where F u vanishes any phase is allowed; the
+    # selection must still have amplitude m there (reading C1: phase 0). Exact
+    # zeros are planted in the Fourier data: a transform of rounded inputs
+    # leaves residues of order 1e-16 instead of exact zeros.
+    Fz = rand_complex(rng, (8, 8))
+    Fz[0, 1] = 0.0
+    Fz[3, 5] = 0.0
+    mm = rng.uniform(0.5, 2.0, (8, 8))
+    sel = O._mhat(Fz, mm)
+    assert np.allclose(np.abs(sel), mm, rtol=0, atol=1e-14)
+    assert sel[0, 1] == mm[0, 1] and sel[3, 5] == mm[3, 5]
 
 
 def test_proj_M():
@@ -389,6 +428,39 @@ def test_gradient_finite_differences():
 
 def test_gradient_finite_differences_with_laser_amplitude():
     check_gradient_fd(p=laser_profile(32, 32, 9).astype(np.float64))
+
+
+def check_intensity_loss_closed_forms(seed=12):
+    """The value of the intensity loss where the field's transform is known.
+
+    A constant phase c gives x = e^{ic}, so y = F x = N e^{ic} at zero
+    frequency and 0 elsewhere, |y|^2/N = N delta_0 and
+    L = (N - I_0)^2 + sum_{k != 0} I_k^2. A plane-wave phase
+    2 pi (a j/nx + b k/ny) moves the delta to frequency (a, b) (row b,
+    column a). A constant laser amplitude p0 scales it to N p0^2."""
+    rng = np.random.default_rng(seed)
+    ny, nx = 8, 16
+    n = nx * ny
+    I = rng.uniform(0.0, 3.0, (ny, nx))
+    c = 0.7
+    want = (n - I[0, 0]) ** 2 + np.sum(I**2) - I[0, 0] ** 2
+    got = O.intensity_loss(np.full((ny, nx), c), I)
+    assert abs(got - want) <= 1e-10 * want, (got, want)
+    a, b = 5, 3
+    jj = np.arange(nx)[None, :]
+    kk = np.arange(ny)[:, None]
+    ramp = 2 * np.pi * (a * jj / nx + b * kk / ny) + c
+    want = (n - I[b, a]) ** 2 + np.sum(I**2) - I[b, a] ** 2
+    got = O.intensity_loss(ramp, I)
+    assert abs(got - want) <= 1e-10 * want, (got, want)
+    p0 = 1.5
+    want = (n * p0**2 - I[0, 0]) ** 2 + np.sum(I**2) - I[0, 0] ** 2
+    got = O.intensity_loss(np.full((ny, nx), c), I, np.full((ny, nx), p0))
+    assert abs(got - want) <= 1e-10 * want, (got, want)
+
+
+def test_intensity_loss_closed_forms():
+    check_intensity_loss_closed_forms()
 
 
 def test_gradient_single_pixel_is_zero():

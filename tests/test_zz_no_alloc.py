@@ -21,7 +21,10 @@ from tests.gpu_util import aligned_rel_err, gpu_gs
 pytestmark = pytest.mark.gpu
 
 
-def noalloc_run(I, phi0, iters):
+def noalloc_run(I, phi0, iters, from_target=False, free_check=None):
+    """One gs_run_noalloc call. With ``free_check`` (a list), the device's free
+    memory just before and just after the call is appended to it: every
+    buffer this helper passes exists before the first reading."""
     import torch
 
     from paper_1302_0120_gb300 import _binding as B
@@ -36,10 +39,41 @@ def noalloc_run(I, phi0, iters):
     g = torch.full((max(iters, 1),), float("nan"), dtype=torch.float64, device="cuda")
     st = torch.full((1,), 12345, dtype=torch.int32, device="cuda")
     stream = torch.cuda.current_stream().cuda_stream
-    rc = B.gs_run_noalloc(nx, ny, B.GS_FINAL_RESIDUAL, stream, It.data_ptr(), Pt.data_ptr(), iters,
+    flags = B.GS_FINAL_RESIDUAL | (B.GS_INIT_FROM_TARGET if from_target else 0)
+    torch.cuda.synchronize()
+    if free_check is not None:
+        free_check.append(torch.cuda.mem_get_info()[0])
+    rc = B.gs_run_noalloc(nx, ny, flags, stream, It.data_ptr(), 0 if from_target else Pt.data_ptr(), iters,
                           out.data_ptr(), r.data_ptr(), g.data_ptr(), st.data_ptr())
     torch.cuda.synchronize()
+    if free_check is not None:
+        free_check.append(torch.cuda.mem_get_info()[0])
     return rc, out.cpu().numpy(), r.cpu().numpy(), g[:iters].cpu().numpy(), int(st.item())
+
+
+def context_run(I, phi0, iters, from_target=False):
+    """The same run through gs_create / gs_run (a context workspace)."""
+    import torch
+
+    from paper_1302_0120_gb300 import GerchbergSaxton
+
+    ny, nx = I.shape
+    with GerchbergSaxton(nx, ny, init_from_target=from_target) as gs:
+        It = torch.from_numpy(np.ascontiguousarray(I, np.float32)).cuda()
+        Pt = None if from_target else torch.from_numpy(np.ascontiguousarray(phi0, np.float32)).cuda()
+        out, r, g = gs.run(It, Pt, iters)
+        assert gs.status() == 0
+        return out.cpu().numpy(), r.cpu().numpy(), g.cpu().numpy()
+
+
+def check_against_context(I, phi0, iters, from_target=False, free_check=None):
+    rc, ph, r, g, st = noalloc_run(I, phi0, iters, from_target, free_check)
+    assert rc == 0 and st == 0
+    ref_ph, ref_r, ref_g = context_run(I, phi0, iters, from_target)
+    assert aligned_rel_err(ph, np.exp(1j * ref_ph.astype(np.float64))) <= 1e-5
+    assert np.max(np.abs(r - ref_r) / ref_r) <= 1e-3
+    if iters:
+        assert np.max(np.abs(g - ref_g) / ref_g) <= 1e-3
 
 
 def test_noalloc_two_calls_match_context_runs():
@@ -55,3 +89,41 @@ def test_noalloc_two_calls_match_context_runs():
         assert aligned_rel_err(ph, np.exp(1j * ref_ph.astype(np.float64))) <= 1e-5
         assert np.max(np.abs(r - ref_r) / ref_r) <= 1e-3
         assert np.max(np.abs(g - ref_g) / ref_g) <= 1e-3
+
+
+@pytest.mark.parametrize("case", ["150-iterations", "target-start", "4096x32", "32x4096", "64x64"])
+def test_noalloc_paths_match_context_runs(case):
+    """The paths one call can take: more iterations than one launch holds
+    (chunks reuse the barrier, abort word and mask flags of the scratch), the
+    target start, the extreme shapes the size check accepts, and a grid that
+    gs_run would give to its one-block-per-mask kernel. Each is called twice in
+    a row and compared with a context run both times."""
+    if case == "150-iterations":
+        I, phi0, iters, ft = S.spot_target(23, 256, 256, 20, (0.5, 1.0)), S.random_phase(23, 256, 256), 150, False
+    elif case == "target-start":
+        # the target start is an unstable invariant subspace: gated over the
+        # first iterations only, as in the parity tests
+        I, phi0, iters, ft = S.spot_target(24, 512, 512, 40, (0.5, 1.0)), None, 1, True
+    elif case == "4096x32":
+        I, phi0, iters, ft = S.spot_target(25, 32, 4096, 12, (0.5, 1.0)), S.random_phase(25, 32, 4096), 5, False
+    elif case == "32x4096":
+        I, phi0, iters, ft = S.spot_target(26, 4096, 32, 12, (0.5, 1.0)), S.random_phase(26, 4096, 32), 5, False
+    else:
+        I, phi0, iters, ft = S.spot_target(27, 64, 64, 5), S.random_phase(27, 64, 64), 20, False
+    if phi0 is None:
+        phi0 = np.zeros(I.shape, np.float32)
+    for _ in range(2):
+        check_against_context(I, phi0, iters, ft)
+
+
+def test_noalloc_allocates_nothing():
+    """After a first call on the device (which may load the library's device
+    code and with it the static array), further calls leave the device's free
+    memory unchanged."""
+    I, phi0 = S.spot_target(28, 512, 512, 30, (0.5, 1.0)), S.random_phase(28, 512, 512)
+    noalloc_run(I, phi0, 5)
+    free = []
+    for _ in range(2):
+        rc, ph, r, g, st = noalloc_run(I, phi0, 5, free_check=free)
+        assert rc == 0 and st == 0
+    assert free[0] == free[1] and free[2] == free[3], free
