@@ -106,9 +106,10 @@ def idft_last(X: np.ndarray) -> np.ndarray:
 
 
 def dft2(x: np.ndarray) -> np.ndarray:
-    """Unnormalised 2D DFT over the last two axes ([ny, nx]): rows, then columns."""
+    """Unnormalised 2D DFT over the last two axes ([ny, nx]): rows, then
+    columns. Returned C-contiguous (row-major), like its input layout."""
     rows = dft_last(x)
-    return np.swapaxes(dft_last(np.swapaxes(rows, -1, -2)), -1, -2)
+    return np.ascontiguousarray(np.swapaxes(dft_last(np.swapaxes(rows, -1, -2)), -1, -2))
 
 
 def idft2(X: np.ndarray) -> np.ndarray:
