@@ -112,6 +112,19 @@ def l2_copy_gbs(dev, stream, mib=40, reps=100):
     return 2 * n * 4 * reps / (t0.elapsed_time(t1) * 1e-3) / 1e9
 
 
+def tensor_peak():
+    """Dense 16-bit tensor throughput in TFLOP/s: the sustained cuBLAS bf16
+    figure of MEASURED_PEAKS.json (FP16 runs at the same dense rate), else the
+    fallback; and which it is."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["bf16_tflops_sustained"]), "measured (bf16 sustained, MEASURED_PEAKS.json)"
+    except Exception:
+        return 1700.0, "fallback (sustained bf16)"
+
+
 def peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -515,27 +528,43 @@ def run_gpu(args):
                       "barrier_us": round(float(np.median(barrier_us[1:2 * iters + 1])), 2),
                       "passes": int(work_us.shape[0])}
 
-    # tensor-core form (FP16 DFT-matrix products, FP32 accumulation) on the
-    # same workload: time per mask and the final residual against the FP32 one
+    # tensor-core form (FP16 / BF16 DFT-matrix products, FP32 accumulation) on
+    # the same workload: time per mask and the final residual against the FP32
+    # one, for the tcgen05 engine with FP16 and BF16 operands and for the
+    # warp-level mma.sync products. Tensor work per mask: every 1024-point
+    # transform is two products of 32 rows x 64 x 64 (real form), 2 x 32 x 64 x
+    # 64 flop each; a mask of K iterations runs 4 K + 3 transforms per line
+    # (init row pass, two per pass, the final residual pass), 1024 lines each.
     tensor_core = None
     if args.tc_steps > 0 and ws == 1:
-        gst = GerchbergSaxton(nx, ny, final_residual=True, stream=stream, tensor_core=True)
-        out_t = torch.empty_like(phi0)
-        res_t = {}
+        tc_flops = (4 * iters + 3) * 1024 * 2 * (2 * 32 * 64 * 64)
+        tensor_core = {"tensor_flops_per_mask": tc_flops, "fp32_ms_per_mask": round(mean_ms, 4), "steps": args.tc_steps}
+        tc_peak = tensor_peak()
+        for name, kw in (("tcgen05_f16", {}), ("tcgen05_bf16", {"bf16": True}), ("mma_sync_f16", {"mma_sync": True})):
+            gst = GerchbergSaxton(nx, ny, final_residual=True, stream=stream, tensor_core=True, **kw)
+            out_t = torch.empty_like(phi0)
+            res_t = {}
 
-        def tc_step():
-            res_t["r"] = gst.run(I, phi0, iters, phase_out=out_t)[1]
+            def tc_step():
+                res_t["r"] = gst.run(I, phi0, iters, phase_out=out_t)[1]
 
-        ms_t = timed(tc_step, args.tc_steps)
-        if gst.status() != 0:
-            raise RuntimeError("tensor-core run failed")
-        r_t = float(res_t["r"][-1].item())
-        tensor_core = {"ms_per_mask": round(ms_t, 4), "fp32_ms_per_mask": round(mean_ms, 4),
-                       "achieved_gbs": round((BYTES_PER_PX_FIXED + BYTES_PER_PX_ITER * iters) * n / (ms_t * 1e6), 1),
-                       "speedup_vs_fp32": round(mean_ms / ms_t, 4), "final_residual": r_t,
-                       "final_residual_rel_diff_vs_fp32": round(abs(r_t - r_final) / r_final, 6),
-                       "matched_within_2pct": abs(r_t - r_final) <= 0.02 * r_final, "steps": args.tc_steps}
-        gst.close()
+            ms_t = timed(tc_step, args.tc_steps)
+            if gst.status() != 0:
+                raise RuntimeError(f"tensor-core run failed ({name})")
+            r_t = float(res_t["r"][-1].item())
+            tf = tc_flops / (ms_t * 1e-3) / 1e12
+            tensor_core[name] = {
+                "ms_per_mask": round(ms_t, 4),
+                "achieved_gbs": round((BYTES_PER_PX_FIXED + BYTES_PER_PX_ITER * iters) * n / (ms_t * 1e6), 1),
+                "speedup_vs_fp32": round(mean_ms / ms_t, 4), "final_residual": r_t,
+                "final_residual_rel_diff_vs_fp32": round(abs(r_t - r_final) / r_final, 6),
+                "matched_within_2pct": abs(r_t - r_final) <= 0.02 * r_final,
+                "tensor_tflops": round(tf, 2), "tensor_peak_tflops": tc_peak[0],
+                "tensor_frac": round(tf / tc_peak[0], 4), "tensor_peak_kind": tc_peak[1]}
+            gst.close()
+        # the headline of the form: the tcgen05 FP16 engine
+        tensor_core.update({k: tensor_core["tcgen05_f16"][k] for k in ("ms_per_mask", "speedup_vs_fp32",
+                                                                         "final_residual", "matched_within_2pct")})
 
     # the paper's own timing experiment (Sec. V): an 800 x 600 SLM, 25
     # iterations in single precision from the start P_S(F^-1 m), reported

@@ -81,10 +81,22 @@ enum {
    * gaps and reductions are unchanged (FP32 field, FP64 sums). The paper
    * computes in single or double precision only (Sec. V); this reduced
    * precision form has no counterpart there. One iteration differs from the
-   * FP32 one by about 1e-3 (relative L2). The transforms' inputs must stay in
-   * the FP16 range: a mask whose n * sum p^2 exceeds 2^31 is rejected like an
-   * invalid target (GS_ENUMERIC); p = 1 always qualifies. */
-  GS_TENSOR_CORE = 4u
+   * FP32 one by about 1e-3 (relative L2). The operands are kept in the FP16
+   * range by a power-of-two scale per mask (inputs below 2^15 from the bound
+   * sqrt(n sum p^2) of every transform input; the scale is undone in FP32),
+   * so any laser amplitude is accepted. On 1024 x 1024 grids the products run
+   * on the fifth-generation tensor cores (tcgen05: operands in shared memory,
+   * FP32 accumulators in tensor memory, each stage one M = 128 product over
+   * four lines); on 256 and 512 as warp-level mma.sync products. */
+  GS_TENSOR_CORE = 4u,
+  /* With GS_TENSOR_CORE on a 1024 x 1024 grid (tcgen05): BF16 operands
+   * instead of FP16 (8 bits of significand instead of 11, FP32's range). Not
+   * accepted without GS_TENSOR_CORE, on other sizes or with GS_TC_MMA_SYNC. */
+  GS_BF16 = 8u,
+  /* With GS_TENSOR_CORE on a 1024 x 1024 grid: run the products as
+   * warp-level mma.sync tiles (the form used at 256 and 512) instead of
+   * tcgen05, for comparison. Not accepted without GS_TENSOR_CORE. */
+  GS_TC_MMA_SYNC = 16u
 };
 
 typedef struct gs_ctx gs_ctx;
@@ -97,14 +109,15 @@ typedef struct gs_ctx gs_ctx;
  *   out     host pointer that receives the context (set to NULL on failure).
  *   nx, ny  grid sides: powers of two in [8, 4096], or 5-smooth in [8, 1536].
  *   flags   GS_* flags (GS_FINAL_RESIDUAL, GS_INIT_FROM_TARGET,
- *           GS_TENSOR_CORE).
+ *           GS_TENSOR_CORE, GS_BF16, GS_TC_MMA_SYNC).
  *   stream  a cudaStream_t, or NULL for the legacy default stream. All later
  *           work of this context is enqueued on it.
  * The context owns its device workspace (gs_workspace_bytes bytes): the field,
  * the scaled amplitude, per-block FP64 partial sums, twiddle tables, a
  * barrier counter and a status word. Synchronous (allocates and uploads).
  * Returns GS_EINVAL for bad sizes, an unknown flag, GS_TENSOR_CORE with a grid
- * other than 256, 512 or 1024 square, or a NULL out; GS_ENOMEM, GS_ECUDA.
+ * other than 256, 512 or 1024 square, GS_BF16 or GS_TC_MMA_SYNC where they do
+ * not apply, or a NULL out; GS_ENOMEM, GS_ECUDA.
  */
 int gs_create(gs_ctx** out, int nx, int ny, unsigned flags, void* stream);
 

@@ -23,6 +23,8 @@ GS_ECORRUPT = -6
 GS_FINAL_RESIDUAL = 1
 GS_INIT_FROM_TARGET = 2
 GS_TENSOR_CORE = 4
+GS_BF16 = 8
+GS_TC_MMA_SYNC = 16
 
 _c_int = ctypes.c_int
 _c_uint = ctypes.c_uint

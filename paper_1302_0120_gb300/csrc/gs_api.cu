@@ -181,6 +181,7 @@ struct gs_ctx {
   int num_sms = 0;
   int blocks_per_sm = 0;
   int grid_override = 0;
+  int tc_mode = 0;               // gsk::TcMode of the iteration kernel
   const float* p_slm = nullptr;  // caller-owned SLM amplitude, or null (p = 1)
   unsigned extra_arrivals = 0;
   int group_override = 0;  // masks per group of a batched run (0: the whole batch)
@@ -313,12 +314,20 @@ int gs_create_batched(gs_ctx** out, int nx, int ny, int max_batch, unsigned flag
   if (out == nullptr) return GS_EINVAL;
   *out = nullptr;
   if (!valid_dim(nx) || !valid_dim(ny) || max_batch < 1 || max_batch > gsk::kMaxBatch) return GS_EINVAL;
-  if ((flags & ~static_cast<unsigned>(GS_FINAL_RESIDUAL | GS_INIT_FROM_TARGET | GS_TENSOR_CORE)) != 0)
+  if ((flags & ~static_cast<unsigned>(GS_FINAL_RESIDUAL | GS_INIT_FROM_TARGET | GS_TENSOR_CORE | GS_BF16 |
+                                      GS_TC_MMA_SYNC)) != 0)
     return GS_EINVAL;
   const bool tc = (flags & GS_TENSOR_CORE) != 0;
   if (tc && !(nx == ny && is_pow2(nx) && nx >= 256 && nx <= 1024)) return GS_EINVAL;
+  if ((flags & (GS_BF16 | GS_TC_MMA_SYNC)) != 0 && !tc) return GS_EINVAL;
+  // 1024 x 1024 runs its transforms through tcgen05 unless mma.sync is asked
+  // for; the other sizes use mma.sync, with FP16 operands only
+  const bool tc5 = tc && nx == 1024 && !(flags & GS_TC_MMA_SYNC);
+  if ((flags & GS_BF16) != 0 && !tc5) return GS_EINVAL;
+  const int tc_mode = !tc ? gsk::kTcNone : !tc5 ? gsk::kTcMmaSync : (flags & GS_BF16) ? gsk::kTcGen05Bf16 : gsk::kTcGen05F16;
   gs_ctx* c = new (std::nothrow) gs_ctx();
   if (c == nullptr) return GS_ENOMEM;
+  c->tc_mode = tc_mode;
   c->nx = nx;
   c->ny = ny;
   c->max_batch = max_batch;
@@ -327,7 +336,7 @@ int gs_create_batched(gs_ctx** out, int nx, int ny, int max_batch, unsigned flag
   c->L = make_layout(nx, ny, max_batch);
   if (cudaGetDevice(&c->device) != cudaSuccess ||
       cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess ||
-      gsk::iteration_occupancy(nx, ny, &c->blocks_per_sm, tc) != cudaSuccess || c->blocks_per_sm < 1 ||
+      gsk::iteration_occupancy(nx, ny, &c->blocks_per_sm, tc_mode) != cudaSuccess || c->blocks_per_sm < 1 ||
       (gsk::small_grid(nx, ny) && gsk::small_prepare(nx, ny) != cudaSuccess)) {
     cudaGetLastError();
     delete c;
@@ -406,7 +415,7 @@ int gs_run_batched(gs_ctx* c, int batch, const float* target_intensity, const fl
   p.iters = iters;
   p.final_resid = (c->flags & GS_FINAL_RESIDUAL) ? 1 : 0;
   p.extra_arrivals = c->extra_arrivals;
-  p.tensor_core = (c->flags & GS_TENSOR_CORE) ? 1 : 0;
+  p.tensor_core = c->tc_mode;
   p.group = group_size(c, static_cast<long long>(c->nx) * c->ny, batch);
   p.trace = c->trace ? at<unsigned long long>(c, c->L.trace) : nullptr;
   const double n = static_cast<double>(c->nx) * c->ny;

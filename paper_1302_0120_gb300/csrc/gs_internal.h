@@ -17,8 +17,11 @@ constexpr int kTraceRows = 2 * kMaxIterPerLaunch + 4;
 // which is 256 * 33 complex whatever n is.
 constexpr int kGroupSmemBytes = kThreads * 33 * 8;
 // Extra shared memory of the tensor-core kernels: stage twiddles [32][32]
-// complex and a 32-entry cos/sin table.
+// complex and a 32-entry cos/sin table (mma.sync); the DFT matrix (hi and lo
+// parts, 8 KiB each) and an 8 KiB twiddle table (tcgen05, whose operands
+// share the exchange buffers).
 constexpr int kTcExtraSmemBytes = 32 * 32 * 8 + 32 * 8;
+constexpr int kTc5ExtraSmemBytes = 2 * 64 * 64 * 2 + 32 * 32 * 8;
 
 struct Params {
   int nx, ny;          // grid, powers of two in [32, 4096]
@@ -53,7 +56,8 @@ struct Params {
   unsigned extra_arrivals;  // test hook: arrivals a barrier waits for beyond the grid (0 in use)
   float inv_sqrt_n;    // 1/sqrt(N)
   double inv_n;        // 1/N
-  int tensor_core;     // host side: launch the tensor-core kernel (square 256, 512, 1024)
+  int tensor_core;     // host side: transforms on the FP32 ALUs (0) or the tensor cores: mma.sync (1,
+                       // square 256, 512, 1024), tcgen05 with FP16 (2) or BF16 (3) operands (1024 x 1024)
   unsigned long long* trace;  // [kTraceRows][grid][2] globaltimer stamps of block 0's thread 0 per block, or null
   int group;           // masks iterated together, 1..batch: the batch runs group after group
                        // through the whole schedule, so that a group's fields stay in L2
@@ -120,7 +124,9 @@ size_t mixed_smem_bytes(bool tensor_core);
 cudaError_t mixed_occupancy(bool tensor_core, int* blocks_per_sm);
 cudaError_t launch_mixed(const MixedParams& mp, int grid, bool tensor_core, cudaStream_t s);
 
-size_t iteration_smem_bytes(int nx, int ny, bool tensor_core = false);
+// Tensor-core modes of Params::tensor_core.
+enum TcMode { kTcNone = 0, kTcMmaSync = 1, kTcGen05F16 = 2, kTcGen05Bf16 = 3 };
+size_t iteration_smem_bytes(int nx, int ny, int tc_mode = kTcNone);
 
 // Intensity loss and gradient (square grids), see gs_loss.cuh.
 struct LossParams {
@@ -146,7 +152,9 @@ cudaError_t launch_loss(const LossParams& p, int grid, cudaStream_t s);
 cudaError_t launch_iterations(const Params& p, int grid, cudaStream_t s);
 // sum p^2 of an SLM amplitude into *energy (NaN if p has a negative or non-finite value)
 cudaError_t launch_energy(const float* p, long long n, double* energy, cudaStream_t s);
-cudaError_t iteration_occupancy(int nx, int ny, int* blocks_per_sm, bool tensor_core = false);
+cudaError_t iteration_occupancy(int nx, int ny, int* blocks_per_sm, int tc_mode = kTcNone);
+// The tcgen05 kernel of 1024 x 1024 masks (gs_tc5_inst.cu); FP16 or BF16 operands.
+const void* iterate_kernel_tc5(bool bf16);
 // Small grids (small_grid): allow the kernel its shared memory, and launch
 // one block per mask of p.batch (gs_small_inst.cu).
 cudaError_t small_prepare(int nx, int ny);

@@ -42,6 +42,7 @@
 #include "gs_general.cuh"
 #include "gs_internal.h"
 #include "gs_tc.cuh"
+#include "gs_tc5.cuh"
 #include "gs_tma.cuh"
 
 namespace gsk {
@@ -54,6 +55,7 @@ static_assert(kTcTwBytes + kTcCsBytes == kTcExtraSmemBytes, "tensor-core tables 
 // Stands in for TcFft in the kernels whose transforms run on the FP32 ALUs.
 struct NoTc {
   static constexpr bool kEnabled = false;
+  static constexpr bool kTcgen05 = false;
 };
 
 // Storage of the field B between passes: column blocks of W adjacent columns,
@@ -124,11 +126,17 @@ __device__ __forceinline__ double run_pass(const Params& p, int mb, int kind, bo
   const int nfft = (kind == kCol || (kind == kRow && !(last && !p.final_resid))) ? 2 : 1;
   const float inv_sqrt_n = p.inv_sqrt_n;
   double acc = 0.0;
-  // One forward transform of the group's vector: on the FP32 ALUs, or on the
-  // tensor cores through the warp's slice of the exchange buffers.
+  // Tensor-core transforms: this mask's power-of-two operand scales.
+  float tc_in = 1.f, tc_out = 32.f;
+  if constexpr (TCF::kEnabled) tc_scales(p.nx > p.ny ? p.nx : p.ny, energy_of(p), tc_in, tc_out);
+  // One forward transform of the group's vector: on the FP32 ALUs, on the
+  // tensor cores through the warp's slice of the exchange buffers (mma.sync),
+  // or on the tensor cores of the block's half (tcgen05, all warps at once).
   auto fft = [&](float2(&x)[32]) {
-    if constexpr (TCF::kEnabled) {
-      tcf.run(x, smem + (threadIdx.x >> 5) * kTcWarpBytes);
+    if constexpr (TCF::kTcgen05) {
+      tcf.run(x, tc_in, tc_out);
+    } else if constexpr (TCF::kEnabled) {
+      tcf.run(x, smem + (threadIdx.x >> 5) * kTcWarpBytes, tc_in, tc_out);
     } else {
       group_fft<LOGN>(x, grp, stw);
     }
@@ -423,18 +431,17 @@ static __device__ __forceinline__ void a0_partials(const Params& p, Shared& sh) 
 // A0, part 2 (after a grid barrier): validity and scale sqrt(sum p^2 / sum I)
 // of every mask, the same in every block (each reduces the same partials in
 // the same order). Rejected masks get NaN gaps and GS_ENUMERIC; they are
-// skipped from then on. With FP16 operands every transform input is below
-// sqrt(n sum p^2) (Cauchy-Schwarz on a row or column), which must stay in
-// the FP16 range. Returns the number of rejected masks.
-static __device__ __forceinline__ int a0_scales(const Params& p, Shared& sh, int base, bool tc) {
+// skipped from then on. (The tensor-core forms keep their FP16 operands in
+// range with a power-of-two scale per mask, tc_scales, so no energy is too
+// large for them.) Returns the number of rejected masks.
+static __device__ __forceinline__ int a0_scales(const Params& p, Shared& sh, int base) {
   const int b = blockIdx.x;
   if (threadIdx.x < 32) {
     for (int mb = 0; mb < p.batch; ++mb) {
       const double total = warp_slot_sum(p, mb);
       if (threadIdx.x == 0) {
         const double ep = energy_of(p);
-        const bool range = !tc || (ep * static_cast<double>(p.nx) <= 2147483648.0);
-        const bool bad = !(total > 0.0) || !(total <= DBL_MAX) || !(ep > 0.0) || !(ep <= DBL_MAX) || !range;
+        const bool bad = !(total > 0.0) || !(total <= DBL_MAX) || !(ep > 0.0) || !(ep <= DBL_MAX);
         sh.bad[base + mb] = bad ? 1 : 0;
         if (b == 0) p.mask_flags[mb] = bad ? 1 : 0;  // for later launches of the run
         sh.scale[base + mb] = bad ? 0.f : static_cast<float>(sqrt(ep / total));
@@ -602,41 +609,21 @@ static __device__ __forceinline__ void block_setup(Shared& sh) {
   __syncthreads();
 }
 
-// One size class per launch (every grid).
-template <int LX, int LY, bool TC = false>
-__global__ void __launch_bounds__(kThreads, 1) gs_iterate(const Params p) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ Shared sh;
-  if (*reinterpret_cast<volatile int*>(p.abort_flag) != 0) return;  // an earlier chunk failed
+// The schedule of one size class (every grid): A0, then the passes, then the
+// gaps. Returns early (in every thread of the block) when a grid barrier gave
+// up or every mask was rejected.
+template <int LX, int LY, bool kHold, class TCF>
+__device__ __forceinline__ void iterate_class(const Params& p, Shared& sh, unsigned char* smem,
+                                              const StageTw<LX>& tw_rows, const TCF& tcf) {
   unsigned target = 0;
   unsigned mphase = 0;
-  constexpr bool kHold = LX > 0 && LX == LY && !TC;
-  StageTw<LX> tw_rows;  // square grids: stage twiddles held for the whole run
-  if constexpr (kHold) tw_rows.load(p.twx, threadIdx.x & ((1 << (LX - 5)) - 1));
-  // Tensor-core transforms: the block's tables, then the DFT-matrix fragments
-  // held in registers for the whole run.
-  static_assert(!TC || LX == LY, "tensor-core kernels are square");
-  constexpr int kR = TC ? (1 << (LX > 5 ? LX - 5 : 0)) : 32;
-  TcStage1 s1;
-  TcStage2<kR> s2;
-  const float2* tctw = reinterpret_cast<const float2*>(smem + kTcTwOffset);
-  if constexpr (TC) {
-    tc_build_tables<LX>(reinterpret_cast<float2*>(smem + kTcTwOffset), reinterpret_cast<float2*>(smem + kTcCsOffset));
-    __syncthreads();
-    s1.load(reinterpret_cast<const float2*>(smem + kTcCsOffset));
-    s2.load(reinterpret_cast<const float2*>(smem + kTcCsOffset));
-  }
-  const auto tcf = [&]() {
-    if constexpr (TC) return TcFft<LX>{s1, s2, tctw};
-    else return NoTc{};
-  }();
   block_setup(sh);
   if constexpr (LX == 0) gen_load_twiddles(p, smem);  // sides that are not powers of two
 
   if (p.do_init) {
     a0_partials(p, sh);
     if (!grid_sync(p, target, sh)) return;
-    const int nbad = a0_scales(p, sh, 0, TC);
+    const int nbad = a0_scales(p, sh, 0);
     if (nbad == p.batch) {
       if (blockIdx.x == 0 && threadIdx.x == 0) atomicExch(p.abort_flag, 1);  // later launches of the run
       return;
@@ -666,6 +653,72 @@ __global__ void __launch_bounds__(kThreads, 1) gs_iterate(const Params p) {
     }
   }
   final_gaps(p, sh, 0);
+}
+
+// One size class per launch (every grid).
+template <int LX, int LY, bool TC = false>
+__global__ void __launch_bounds__(kThreads, 1) gs_iterate(const Params p) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ Shared sh;
+  if (*reinterpret_cast<volatile int*>(p.abort_flag) != 0) return;  // an earlier chunk failed
+  constexpr bool kHold = LX > 0 && LX == LY && !TC;
+  StageTw<LX> tw_rows;  // square grids: stage twiddles held for the whole run
+  if constexpr (kHold) tw_rows.load(p.twx, threadIdx.x & ((1 << (LX - 5)) - 1));
+  // Tensor-core transforms: the block's tables, then the DFT-matrix fragments
+  // held in registers for the whole run.
+  static_assert(!TC || LX == LY, "tensor-core kernels are square");
+  constexpr int kR = TC ? (1 << (LX > 5 ? LX - 5 : 0)) : 32;
+  TcStage1 s1;
+  TcStage2<kR> s2;
+  const float2* tctw = reinterpret_cast<const float2*>(smem + kTcTwOffset);
+  if constexpr (TC) {
+    tc_build_tables<LX>(reinterpret_cast<float2*>(smem + kTcTwOffset), reinterpret_cast<float2*>(smem + kTcCsOffset));
+    __syncthreads();
+    s1.load(reinterpret_cast<const float2*>(smem + kTcCsOffset));
+    s2.load(reinterpret_cast<const float2*>(smem + kTcCsOffset));
+  }
+  const auto tcf = [&]() {
+    if constexpr (TC) return TcFft<LX>{s1, s2, tctw};
+    else return NoTc{};
+  }();
+  iterate_class<LX, LY, kHold>(p, sh, smem, tw_rows, tcf);
+}
+
+// The tensor-core form on tcgen05 (1024 x 1024 masks): the same schedule with
+// every 1024-point transform issued by the block's halves as products on the
+// tensor cores (gs_tc5.cuh). Warp 0 holds the block's TMEM columns from the
+// start of the launch to its end, on every exit path.
+constexpr int kTc5Offset = kBlockSmemOffset + kBlockSmemBytes;  // after the amplitude and field blocks
+
+template <bool BF16>
+__global__ void __launch_bounds__(kThreads, 1) gs_iterate_tc5(const Params p) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ Shared sh;
+  __shared__ uint64_t tc_mbar[2];
+  __shared__ unsigned tc_tmem;
+  if (*reinterpret_cast<volatile int*>(p.abort_flag) != 0) return;  // an earlier chunk failed
+  static_assert(2 * kTc5HalfStride == kGroupSmemBytes, "the A operands fill the exchange area");
+  unsigned char* abuf = smem;  // the exchange area (gs_tc5.cuh)
+  unsigned char* bmat = smem + kTc5Offset;
+  float2* tw = reinterpret_cast<float2*>(bmat + 2 * kTc5BBytes);
+  tc5_build_tables<BF16>(bmat, tw);
+  if (threadIdx.x == 0) {
+    mbar_init(&tc_mbar[0], 1);
+    mbar_init(&tc_mbar[1], 1);
+    fence_barrier_init();
+  }
+  if ((threadIdx.x >> 5) == 0) tc5_alloc(&tc_tmem);
+  fence_proxy_async_smem();  // the DFT matrix is read by the tensor cores
+  tc5_fence_before();
+  __syncthreads();
+  tc5_fence_after();
+  unsigned phase = 0;
+  const Tc5Fft<BF16> tcf{abuf, smem_u32(bmat), tw, tc_mbar, tc_tmem, &phase, &p};
+  const StageTw<10> none{};
+  iterate_class<10, 10, false>(p, sh, smem, none, tcf);
+  tc5_fence_before();
+  __syncthreads();
+  if ((threadIdx.x >> 5) == 0) tc5_dealloc(tc_tmem);
 }
 
 template <int C, bool TC>
@@ -713,8 +766,7 @@ __global__ void __launch_bounds__(kThreads, 1) gs_iterate_mixed(const MixedParam
   if (p0.do_init) {
     for (int c = 0; c < 3; ++c) a0_partials(mp.cls[c], sh);
     if (!grid_sync(p0, target, sh)) return;
-    const int nbad = a0_scales(mp.cls[0], sh, 0, TC) + a0_scales(mp.cls[1], sh, base1, TC) +
-                     a0_scales(mp.cls[2], sh, base2, TC);
+    const int nbad = a0_scales(mp.cls[0], sh, 0) + a0_scales(mp.cls[1], sh, base1) + a0_scales(mp.cls[2], sh, base2);
     if (nbad == total) {
       if (blockIdx.x == 0 && threadIdx.x == 0) atomicExch(p0.abort_flag, 1);
       return;

@@ -48,10 +48,12 @@ static int log2_exact(int n) {
   return l;
 }
 
-static const void* kernel_for(int nx, int ny, bool tc) {
-  if (uses_general(nx, ny)) return tc ? nullptr : iterate_kernel_general();
+static const void* kernel_for(int nx, int ny, int tc_mode) {
+  if (uses_general(nx, ny)) return tc_mode != kTcNone ? nullptr : iterate_kernel_general();
   const int ly = log2_exact(ny);
-  if (tc) return nx == ny ? iterate_kernel_tc(ly) : nullptr;
+  if (tc_mode == kTcGen05F16 || tc_mode == kTcGen05Bf16)
+    return (nx == 1024 && ny == 1024) ? iterate_kernel_tc5(tc_mode == kTcGen05Bf16) : nullptr;
+  if (tc_mode == kTcMmaSync) return nx == ny ? iterate_kernel_tc(ly) : nullptr;
   switch (log2_exact(nx)) {
     case 5: return iterate_kernel_lx<5>(ly);
     case 6: return iterate_kernel_lx<6>(ly);
@@ -65,17 +67,20 @@ static const void* kernel_for(int nx, int ny, bool tc) {
   }
 }
 
-size_t iteration_smem_bytes(int nx, int ny, bool tensor_core) {
+size_t iteration_smem_bytes(int nx, int ny, int tc_mode) {
   if (uses_general(nx, ny)) return gen_smem_bytes(nx, ny);
   // group exchange buffers, one column block of the amplitude, one of the
-  // field; then the tensor-core tables
-  return kGroupSmemBytes + 8192 * 4 + 8192 * 8 + (tensor_core ? kTcExtraSmemBytes : 0);
+  // field; then the tensor-core tables (and, for tcgen05, operands)
+  const size_t extra = tc_mode == kTcMmaSync ? kTcExtraSmemBytes
+                       : (tc_mode == kTcGen05F16 || tc_mode == kTcGen05Bf16) ? kTc5ExtraSmemBytes
+                                                                               : 0;
+  return kGroupSmemBytes + 8192 * 4 + 8192 * 8 + extra;
 }
 
-cudaError_t iteration_occupancy(int nx, int ny, int* blocks_per_sm, bool tensor_core) {
-  const void* k = kernel_for(nx, ny, tensor_core);
+cudaError_t iteration_occupancy(int nx, int ny, int* blocks_per_sm, int tc_mode) {
+  const void* k = kernel_for(nx, ny, tc_mode);
   if (k == nullptr) return cudaErrorInvalidValue;
-  const size_t smem = iteration_smem_bytes(nx, ny, tensor_core);
+  const size_t smem = iteration_smem_bytes(nx, ny, tc_mode);
   // The general kernel serves every size: allow its largest request, so that
   // contexts of different sizes do not undo each other's setting.
   const size_t allow = uses_general(nx, ny) ? gen_smem_bytes(kMaxGeneralSide, kMaxGeneralSide) : smem;
@@ -104,9 +109,9 @@ cudaError_t launch_mixed(const MixedParams& mp, int grid, bool tensor_core, cuda
 }
 
 cudaError_t launch_iterations(const Params& p, int grid, cudaStream_t s) {
-  const void* k = kernel_for(p.nx, p.ny, p.tensor_core != 0);
+  const void* k = kernel_for(p.nx, p.ny, p.tensor_core);
   if (k == nullptr) return cudaErrorInvalidValue;
-  const size_t smem = iteration_smem_bytes(p.nx, p.ny, p.tensor_core != 0);
+  const size_t smem = iteration_smem_bytes(p.nx, p.ny, p.tensor_core);
   void* args[] = {const_cast<Params*>(&p)};
   return cudaLaunchCooperativeKernel(k, dim3(grid), dim3(kThreads), args, smem, s);
 }

@@ -22,9 +22,10 @@
 // the thread layout through the buffer. The factor 1/32 before the FP16
 // rounding of Z and the exact factor 32 after stage 2 are powers of two.
 //
-// Range: every FP16 value is at most max |x| in magnitude, so inputs must stay
-// below 65504 (the caller checks a bound). Rounding: unit roundoff 2^-11 per
-// FP16 operand; the relative L2 error of one transform is about 3e-4.
+// Range: every FP16 value is at most max |x| in magnitude; the caller scales
+// the inputs by a power of two that keeps them below 2^15 (and the outputs
+// back). Rounding: unit roundoff 2^-11 per FP16 operand; the relative L2
+// error of one transform is about 3e-4.
 #pragma once
 
 #include <cuda_fp16.h>
@@ -163,6 +164,7 @@ struct TcStage2<32> {
 template <int LOGN>
 struct TcFft {
   static constexpr bool kEnabled = true;
+  static constexpr bool kTcgen05 = false;
   static constexpr int N = 1 << LOGN;
   static constexpr int R = N >> 5;
   static constexpr int Q = 32 / R;       // transforms per warp
@@ -190,13 +192,17 @@ struct TcFft {
   }
 
   // The transform. `buf` is the warp's 16-byte aligned slice (kTcWarpBytes).
-  // Every lane of the warp must call it.
-  __device__ __forceinline__ void run(float2 (&v)[32], unsigned char* buf) const {
+  // Every lane of the warp must call it. The inputs are multiplied by the
+  // power of two `in_scale` before the FP16 rounding and the outputs by
+  // `out_scale` (32 / in_scale: the 1/32 in the twiddles is undone as well).
+  __device__ __forceinline__ void run(float2 (&v)[32], unsigned char* buf, float in_scale, float out_scale) const {
     const int lane = threadIdx.x & 31;
     __half* xs = reinterpret_cast<__half*>(buf);
     // Stage-1 operand B: row n = lane holds re x[.. i ..] at column i, im at 32 + i.
     {
       uint4* row = reinterpret_cast<uint4*>(xs + lane * XS);
+#pragma unroll
+      for (int i = 0; i < 32; ++i) v[i] = make_float2(v[i].x * in_scale, v[i].y * in_scale);
 #pragma unroll
       for (int c = 0; c < 4; ++c) {
         row[c] = make_uint4(pack_h2(v[8 * c].x, v[8 * c + 1].x), pack_h2(v[8 * c + 2].x, v[8 * c + 3].x),
@@ -291,14 +297,15 @@ struct TcFft {
 #pragma unroll
               for (int h = 0; h < 2; ++h)
                 ret[pos(0, k1 + 32 * (16 * mp + 8 * h + g))] =
-                    make_float2(32.f * out[0][mp][nt][2 * h + e], 32.f * out[0][mp + 2][nt][2 * h + e]);
+                    make_float2(out_scale * out[0][mp][nt][2 * h + e], out_scale * out[0][mp + 2][nt][2 * h + e]);
           } else if constexpr (R == 16) {
 #pragma unroll
             for (int h = 0; h < 2; ++h)
               ret[pos(gamma, k1 + 32 * (8 * h + g))] =
-                  make_float2(32.f * out[gamma][0][nt][2 * h + e], 32.f * out[gamma][1][nt][2 * h + e]);
+                  make_float2(out_scale * out[gamma][0][nt][2 * h + e], out_scale * out[gamma][1][nt][2 * h + e]);
           } else {
-            ret[pos(gamma, k1 + 32 * g)] = make_float2(32.f * out[gamma][0][nt][e], 32.f * out[gamma][0][nt][2 + e]);
+            ret[pos(gamma, k1 + 32 * g)] =
+                make_float2(out_scale * out[gamma][0][nt][e], out_scale * out[gamma][0][nt][2 + e]);
           }
         }
     __syncwarp();

@@ -19,7 +19,10 @@ class GerchbergSaxton:
     """
 
     def __init__(self, nx: int, ny: int, final_residual: bool = True, stream=None, max_batch: int = 1,
-                 init_from_target: bool = False, tensor_core: bool = False):
+                 init_from_target: bool = False, tensor_core: bool = False, bf16: bool = False,
+                 mma_sync: bool = False):
+        """``tensor_core`` runs the DFTs as FP16 tensor-core products (1024 x
+        1024 on tcgen05 unless ``mma_sync``; ``bf16`` for BF16 operands there)."""
         import torch
 
         if stream is None:
@@ -29,7 +32,8 @@ class GerchbergSaxton:
         self.stream = stream
         self.max_batch = int(max_batch)
         flags = ((B.GS_FINAL_RESIDUAL if final_residual else 0) | (B.GS_INIT_FROM_TARGET if init_from_target else 0)
-                 | (B.GS_TENSOR_CORE if tensor_core else 0))
+                 | (B.GS_TENSOR_CORE if tensor_core else 0) | (B.GS_BF16 if bf16 else 0)
+                 | (B.GS_TC_MMA_SYNC if mma_sync else 0))
         self.tensor_core = bool(tensor_core)
         self.init_from_target = bool(init_from_target)
         self._p = None

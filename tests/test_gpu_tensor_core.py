@@ -24,14 +24,20 @@ FINAL_TOL = 0.02
 CHAIN_SLACK = 5e-3
 
 
-def tc_run(I, phi0, iters, p=None):
+# Engines of the tensor-core form: at 1024 x 1024, tcgen05 with FP16 or BF16
+# operands and the warp-level mma.sync products; at 256 and 512, mma.sync.
+ENGINES = {"tcgen05-f16": {}, "tcgen05-bf16": {"bf16": True}, "mma-sync": {"mma_sync": True}}
+
+
+def tc_run(I, phi0, iters, p=None, engine="tcgen05-f16"):
     import torch
 
     from paper_1302_0120_gb300 import GerchbergSaxton, build_lib
 
     build_lib.build()
     ny, nx = I.shape
-    with GerchbergSaxton(nx, ny, tensor_core=True) as gs:
+    kw = ENGINES[engine] if nx == 1024 else {}
+    with GerchbergSaxton(nx, ny, tensor_core=True, **kw) as gs:
         pt = None
         if p is not None:
             pt = torch.from_numpy(p).cuda()
@@ -49,11 +55,16 @@ def check_chain(r, g):
     assert np.all(r[1:] <= g * (1 + CHAIN_SLACK)), np.max(r[1:] / g)
 
 
-@pytest.mark.parametrize("n,nspots,iters", [(256, 20, 50), (512, 40, 50), (1024, 50, 100)])
-def test_final_residual(n, nspots, iters):
+CASES = [(256, 20, "mma-sync"), (512, 40, "mma-sync"), (1024, 50, "tcgen05-f16"), (1024, 50, "tcgen05-bf16"),
+         (1024, 50, "mma-sync")]
+
+
+@pytest.mark.parametrize("n,nspots,engine", CASES)
+def test_final_residual(n, nspots, engine):
+    iters = 100 if n == 1024 else 50
     I = S.spot_target(70 + n, n, n, nspots, (0.5, 1.0))
     phi0 = S.random_phase(71 + n, n, n)
-    ph, r, g, st = tc_run(I, phi0, iters)
+    ph, r, g, st = tc_run(I, phi0, iters, engine=engine)
     assert st == 0 and np.all(np.isfinite(ph)) and np.all(np.abs(ph) <= np.float32(np.pi))
     ref = O.gs_run(I, phi0, iters)
     assert abs(r[0] - ref["r"][0]) <= STEP_TOL * ref["r"][0], (r[0], ref["r"][0])
@@ -61,12 +72,12 @@ def test_final_residual(n, nspots, iters):
     check_chain(r, g)
 
 
-@pytest.mark.parametrize("n,nspots", [(256, 20), (512, 40), (1024, 50)])
-def test_one_step(n, nspots):
+@pytest.mark.parametrize("n,nspots,engine", CASES)
+def test_one_step(n, nspots, engine):
     I = S.spot_target(80 + n, n, n, nspots, (0.5, 1.0))
     phi0 = S.random_phase(81 + n, n, n)
     start = O.gs_run(I, phi0, 5)["phase"].astype(np.float32)
-    nxt, r, g, st = tc_run(I, start, 1)
+    nxt, r, g, st = tc_run(I, start, 1, engine=engine)
     assert st == 0
     u_ref, r_ref, g_ref = O.gs_step(np.exp(1j * start.astype(np.float64)), O.target_amplitude(I))
     err = aligned_rel_err(nxt, u_ref)
@@ -74,15 +85,17 @@ def test_one_step(n, nspots):
     assert abs(r[0] - r_ref) <= STEP_TOL * r_ref and abs(g[0] - g_ref) <= STEP_TOL * g_ref
 
 
-def test_batch_matches_single_runs():
+@pytest.mark.parametrize("n", [512, 1024])
+def test_batch_matches_single_runs(n):
     """Each mask of a batched launch has the single-mask run's phase, bit for
-    bit, and its gaps to FP64 rounding."""
+    bit, and its gaps to FP64 rounding (at 1024: tcgen05, whose products mix
+    the lines of different masks in one M = 128 product)."""
     import torch
 
     from paper_1302_0120_gb300 import GerchbergSaxton, build_lib
 
     build_lib.build()
-    n, nb, iters = 512, 4, 12
+    nb, iters = 4, 12
     masks = [(S.spot_target(90 + k, n, n, 30, (0.5, 1.0)), S.random_phase(90 + k, n, n)) for k in range(nb)]
     It = torch.from_numpy(np.stack([m[0] for m in masks])).cuda()
     Pt = torch.from_numpy(np.stack([m[1] for m in masks])).cuda()
@@ -142,12 +155,25 @@ def test_laser_amplitude():
     check_chain(r, g)
 
 
-def test_out_of_fp16_range_is_rejected():
-    """n sum p^2 > 2^31: a transform input could leave the FP16 range."""
-    from paper_1302_0120_gb300 import GS_ENUMERIC
-
-    n = 256
-    I = S.spot_target(96, n, n, 10, (0.5, 1.0))
-    p = np.full((n, n), 100.0, np.float32)  # n sum p^2 = 2^8 * 2^16 * 1e4
-    ph, r, g, st = tc_run(I, S.random_phase(96, n, n), 3, p=p)
-    assert st == GS_ENUMERIC and np.all(np.isnan(r)) and np.all(np.isnan(g))
+@pytest.mark.parametrize("n,engine", [(256, "mma-sync"), (512, "mma-sync"), (1024, "tcgen05-f16"),
+                                      (1024, "tcgen05-bf16"), (1024, "mma-sync")])
+def test_large_laser_amplitude_is_rescaled(n, engine):
+    """p = 100 everywhere: n sum p^2 = n^3 1e4 puts the raw transform inputs far
+    beyond the FP16 range (65504); the per-mask power-of-two scale keeps the
+    operands in range, and the run meets the one-step and final gates."""
+    iters = 20
+    I = S.spot_target(96, n, n, 20, (0.5, 1.0))
+    phi0 = S.random_phase(96, n, n)
+    p = np.full((n, n), 100.0, np.float32)
+    ph, r, g, st = tc_run(I, phi0, iters, p=p, engine=engine)
+    assert st == 0 and np.all(np.isfinite(r)) and np.all(np.isfinite(g))
+    ref = O.gs_run(I, phi0, iters, p=p)
+    assert abs(r[0] - ref["r"][0]) <= STEP_TOL * ref["r"][0], (r[0], ref["r"][0])
+    assert abs(r[-1] - ref["r"][-1]) <= FINAL_TOL * ref["r"][-1], (r[-1], ref["r"][-1])
+    check_chain(r, g)
+    start = ref["phase"].astype(np.float32)
+    nxt, _, _, st = tc_run(I, start, 1, p=p, engine=engine)
+    assert st == 0
+    u_ref, _, _ = O.gs_step(100.0 * np.exp(1j * start.astype(np.float64)), O.target_amplitude(I, energy=float(n * n) * 1e4),
+                            p.astype(np.float64))
+    assert aligned_rel_err(nxt, u_ref / 100.0) <= STEP_TOL
