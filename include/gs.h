@@ -382,6 +382,35 @@ int gs_destroy(gs_ctx* c);
 int gs_loss_grad(gs_ctx* c, const float* target_intensity, const float* phase, double* loss_out, float* grad_out);
 
 /*
+ * gs_loss_prepare -- stage a target for repeated gs_loss_grad_prepared calls
+ * (an optimisation over many steps with the same target).
+ *
+ * Operation: the target half of gs_loss_grad, once: checks that every value
+ * is finite, reduces sum I and max I in FP64 and stores the target
+ * transposed in the context's workspace, where the loss passes read it
+ * column block by column block.
+ *   target_intensity  device, float [n][n]; may be freed once the context's
+ *                     stream has passed this call (the context keeps a copy).
+ * Square grids only. Asynchronous. A non-finite target makes gs_status report
+ * GS_ENUMERIC and later gs_loss_grad_prepared calls write NaN losses. The
+ * staged target is overwritten (and later prepared calls refused) by any
+ * gs_run / gs_run_batched, gs_loss_grad or gs_physical_error on the same
+ * context. Returns GS_EINVAL for NULL arguments or a non-square context,
+ * GS_ECUDA if the launch fails.
+ */
+int gs_loss_prepare(gs_ctx* c, const float* target_intensity);
+
+/*
+ * gs_loss_grad_prepared -- gs_loss_grad on the target of the last
+ * gs_loss_prepare of this context: the same loss L(phi) and gradient, from
+ * the three transform passes only (no validation or transposition of the
+ * target per call). Arguments and layouts as gs_loss_grad. Returns GS_EINVAL
+ * for NULL arguments, a non-square context or a context without a staged
+ * target; GS_ECUDA if the launch fails.
+ */
+int gs_loss_grad_prepared(gs_ctx* c, const float* phase, double* loss_out, float* grad_out);
+
+/*
  * gs_physical_error -- the physical error of a phase mask, Eq. (phys-error).
  *
  * Operation: for the field u = p exp(i phase) on the SLM (p from

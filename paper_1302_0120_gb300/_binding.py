@@ -46,6 +46,8 @@ SIGNATURES = {
     "gs_run_batched": (_c_int, [_vp, _c_int, _vp, _vp, _c_int, _vp, _vp, _vp]),
     "gs_workspace_bytes_batched": (ctypes.c_size_t, [_c_int, _c_int, _c_int, _c_uint]),
     "gs_loss_grad": (_c_int, [_vp, _vp, _vp, _vp, _vp]),
+    "gs_loss_prepare": (_c_int, [_vp, _vp]),
+    "gs_loss_grad_prepared": (_c_int, [_vp, _vp, _vp, _vp]),
     "gs_set_slm_amplitude": (_c_int, [_vp, _vp]),
     "gs_test_barrier_timeout": (_c_int, [_vp, _c_int]),
     "gs_physical_error": (_c_int, [_vp, _vp, _vp, _vp]),
@@ -233,6 +235,16 @@ def gs_run_host(ctx: int, target_intensity: int, phase_in: int, iters: int, phas
 def gs_loss_grad(ctx: int, target_intensity: int, phase: int, loss_out: int, grad_out: int = 0) -> int:
     """Enqueue the intensity loss (and its gradient when grad_out != 0); returns the status code."""
     return lib().gs_loss_grad(_vp(ctx), _vp(target_intensity), _vp(phase), _vp(loss_out), _vp(grad_out or 0))
+
+
+def gs_loss_prepare(ctx: int, target_intensity: int) -> int:
+    """Enqueue the staging of a target for gs_loss_grad_prepared; returns the status code."""
+    return lib().gs_loss_prepare(_vp(ctx), _vp(target_intensity))
+
+
+def gs_loss_grad_prepared(ctx: int, phase: int, loss_out: int, grad_out: int = 0) -> int:
+    """Enqueue the loss (and gradient) on the staged target; returns the status code."""
+    return lib().gs_loss_grad_prepared(_vp(ctx), _vp(phase), _vp(loss_out), _vp(grad_out or 0))
 
 
 def gs_physical_error(ctx: int, target_intensity: int, phase: int, error_out: int) -> int:

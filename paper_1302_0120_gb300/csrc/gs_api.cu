@@ -182,6 +182,7 @@ struct gs_ctx {
   int blocks_per_sm = 0;
   int grid_override = 0;
   int tc_mode = 0;               // gsk::TcMode of the iteration kernel
+  bool loss_prepared = false;    // the workspace holds a target staged by gs_loss_prepare
   const float* p_slm = nullptr;  // caller-owned SLM amplitude, or null (p = 1)
   unsigned extra_arrivals = 0;
   int group_override = 0;  // masks per group of a batched run (0: the whole batch)
@@ -383,6 +384,7 @@ int gs_run_batched(gs_ctx* c, int batch, const float* target_intensity, const fl
   const bool small = gsk::small_grid(c->nx, c->ny) && c->grid_override == 0 && !from_target &&
                      c->p_slm == nullptr && !(c->flags & GS_TENSOR_CORE) && !c->trace && c->extra_arrivals == 0;
   const int grid = choose_grid(c);
+  c->loss_prepared = false;  // the run's amplitude overwrites a staged loss target
   gsk::Params p{};
   p.batch = batch;
   p.mstride = static_cast<long long>(c->nx) * c->ny;
@@ -686,8 +688,11 @@ int gs_run_host(gs_ctx* c, const float* target_intensity, const float* phase_in,
 namespace {
 
 int enqueue_loss(gs_ctx* c, const float* target_intensity, const float* phase, double* loss_out, float* grad_out,
-                 double* phys_out) {
+                 double* phys_out, int mode = gsk::kLossFused) {
   gsk::LossParams p{};
+  p.mode = mode;
+  // the fused and prepare launches stage their target over the previous one
+  c->loss_prepared = (mode == gsk::kLossPrepare) || (mode == gsk::kLossStep && c->loss_prepared);
   p.n = c->nx;
   p.logn = ilog2i(c->nx);
   p.B = at<float2>(c, c->L.B);
@@ -721,6 +726,19 @@ int gs_loss_grad(gs_ctx* c, const float* target_intensity, const float* phase, d
       c->nx != c->ny || gsk::uses_general(c->nx, c->ny))
     return GS_EINVAL;
   return enqueue_loss(c, target_intensity, phase, loss_out, grad_out, nullptr);
+}
+
+int gs_loss_prepare(gs_ctx* c, const float* target_intensity) {
+  if (c == nullptr || c->mixed || target_intensity == nullptr || c->nx != c->ny || gsk::uses_general(c->nx, c->ny))
+    return GS_EINVAL;
+  return enqueue_loss(c, target_intensity, nullptr, nullptr, nullptr, nullptr, gsk::kLossPrepare);
+}
+
+int gs_loss_grad_prepared(gs_ctx* c, const float* phase, double* loss_out, float* grad_out) {
+  if (c == nullptr || c->mixed || phase == nullptr || loss_out == nullptr || c->nx != c->ny ||
+      gsk::uses_general(c->nx, c->ny) || !c->loss_prepared)
+    return GS_EINVAL;
+  return enqueue_loss(c, nullptr, phase, loss_out, grad_out, nullptr, gsk::kLossStep);
 }
 
 int gs_physical_error(gs_ctx* c, const float* target_intensity, const float* phase, double* error_out) {

@@ -23,6 +23,7 @@ struct Shared {
   const float* m_block;  // global address of the amplitude block in shared memory (null: none)
   unsigned pending_phase;  // the mbarrier phase that copy completes
   double red[kThreads / 32];
+  float redf[kThreads / 32];
   float scale[kMaxBatch];  // sqrt(N / sum I) per mask
   int bad[kMaxBatch];      // mask with a non-finite, negative or zero target
 };
@@ -83,6 +84,27 @@ static __device__ double block_sum(double x, Shared& sh) {
   if (threadIdx.x == 0) {
 #pragma unroll
     for (int w = 0; w < kThreads / 32; ++w) s += sh.red[w];
+  }
+  return s;
+}
+
+// Sum of one float per thread over the block: FP32 within the block (warp
+// shuffles, then the warps' totals on one thread), widened to FP64 for the
+// grid-wide reduction, which runs in FP64 (warp_slot_sum). A warp's FP64
+// shuffles would run on the FP64 pipe (1/64 of the FP32 rate on this part)
+// and cost more than the pass's projection. The result is valid in thread 0.
+static __device__ double block_sum_f(float x, Shared& sh) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) sh.redf[threadIdx.x >> 5] = x;
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x == 0) {
+    float t = 0.f;
+#pragma unroll
+    for (int w = 0; w < kThreads / 32; ++w) t += sh.redf[w];
+    s = static_cast<double>(t);
   }
   return s;
 }

@@ -193,7 +193,7 @@ __device__ __forceinline__ float gen_phase(float2 u) {
 // One pass over rows [lo, hi) (kInit, kRow) or 8-column groups [lo, hi)
 // (kCol, kResid, kInitM) of mask mb. Returns this thread's FP64 contribution
 // to the pass's gap sum.
-static __device__ __forceinline__ double run_pass_gen(const Params& p, int mb, int kind, bool last, int lo, int hi,
+static __device__ __forceinline__ float run_pass_gen(const Params& p, int mb, int kind, bool last, int lo, int hi,
                                                       unsigned char* smem) {
   const size_t moff = static_cast<size_t>(mb) * static_cast<size_t>(p.mstride);
   float2* const Bm = p.B + moff;
@@ -208,7 +208,7 @@ static __device__ __forceinline__ double run_pass_gen(const Params& p, int mb, i
   float2* const Bf = A + nmax + 1;
   const float inv_sqrt_n = p.inv_sqrt_n;
   const bool two = (kind == kCol || (kind == kRow && !(last && !p.final_resid)));
-  double acc = 0.0;
+  float acc = 0.f;
 
   if (kind == kInit || kind == kRow) {
     for (int row = lo + tm; row < hi; row += kGenTeams) {
@@ -268,7 +268,7 @@ static __device__ __forceinline__ double run_pass_gen(const Params& p, int mb, i
             }
           }
         }
-        acc += static_cast<double>(part);
+        acc += part;
         team_sync(tm);
         if (last) {
           float* po = p.phi_out + moff + static_cast<size_t>(row) * nx;
@@ -339,7 +339,7 @@ static __device__ __forceinline__ double run_pass_gen(const Params& p, int mb, i
             }
           }
         }
-        acc += static_cast<double>(part);
+        acc += part;
         team_sync(tm);
         if (kind == kCol) res = gen_fft(res, res == A ? Bf : A, ny, p.plany, p.nsty, twy, tm);
       }

@@ -128,7 +128,10 @@ cudaError_t launch_mixed(const MixedParams& mp, int grid, bool tensor_core, cuda
 enum TcMode { kTcNone = 0, kTcMmaSync = 1, kTcGen05F16 = 2, kTcGen05Bf16 = 3 };
 size_t iteration_smem_bytes(int nx, int ny, int tc_mode = kTcNone);
 
-// Intensity loss and gradient (square grids), see gs_loss.cuh.
+// Intensity loss and gradient (square grids), see gs_loss.cuh. A launch
+// either does everything (fused), or stages the target once (prepare) for
+// later launches that run only the transform passes on it (step).
+enum LossMode { kLossFused = 0, kLossPrepare = 1, kLossStep = 2 };
 struct LossParams {
   int n, logn;             // square grid n x n
   float2* B;               // workspace field (column-blocked layout)
@@ -146,6 +149,7 @@ struct LossParams {
   int* status;
   int* abort_flag;
   float inv_n;             // 1/N
+  int mode;                // LossMode: fused, prepare the target, or a step on the prepared target
 };
 
 cudaError_t launch_loss(const LossParams& p, int grid, cudaStream_t s);

@@ -88,9 +88,9 @@ struct FieldLayout {
 
 // One pass over rows [lo, hi) (kInit, kRow; LOGN = log2 nx) or column blocks
 // [lo, hi) (kCol, kResid, kInitM; LOGN = log2 ny) of mask mb. Returns this
-// thread's FP64 contribution to the pass's gap sum.
+// thread's contribution to the pass's gap sum (FP32: the lines it holds).
 template <int LOGN, int LX, int LY, bool HOLD, class TCF>
-__device__ __forceinline__ double run_pass(const Params& p, int mb, int kind, bool last, int lo, int hi,
+__device__ __forceinline__ float run_pass(const Params& p, int mb, int kind, bool last, int lo, int hi,
                                            unsigned char* smem, Shared& sh, unsigned& mphase,
                                            const StageTw<LOGN>& tw_rows, const TCF& tcf) {
   // this mask's arrays
@@ -125,7 +125,7 @@ __device__ __forceinline__ double run_pass(const Params& p, int mb, int kind, bo
   float2* blk = reinterpret_cast<float2*>(smem + kBlockSmemOffset);
   const int nfft = (kind == kCol || (kind == kRow && !(last && !p.final_resid))) ? 2 : 1;
   const float inv_sqrt_n = p.inv_sqrt_n;
-  double acc = 0.0;
+  float acc = 0.f;
   // Tensor-core transforms: this mask's power-of-two operand scales.
   float tc_in = 1.f, tc_out = 32.f;
   if constexpr (TCF::kEnabled) tc_scales(p.nx > p.ny ? p.nx : p.ny, energy_of(p), tc_in, tc_out);
@@ -260,7 +260,7 @@ __device__ __forceinline__ double run_pass(const Params& p, int mb, int kind, bo
           grp.sync();
         }
       }
-      if (valid) acc += static_cast<double>(part);
+      if (valid) acc += part;
       if (valid && (kind == kInit || nfft == 2)) {
 #pragma unroll
         for (int i = 0; i < 32; ++i) Bm[L::off(idx, t + T * i)] = v[i];
@@ -341,7 +341,7 @@ __device__ __forceinline__ double run_pass(const Params& p, int mb, int kind, bo
           }
         }
       }
-      if (gact) acc += static_cast<double>(part);
+      if (gact) acc += part;
       if ((kind == kCol || from_m) && gact) {
 #pragma unroll
         for (int i = 0; i < 32; ++i) blk[L::boff(t + T * i, g)] = v[i];
@@ -551,7 +551,7 @@ __device__ __forceinline__ void class_pass(const Params& p, Shared& sh, int base
     if (sh.bad[base + mb]) continue;
     const int slo = max(lo, (mb - w0) * per) - (mb - w0) * per;
     const int shi = min(hi, (mb - w0 + 1) * per) - (mb - w0) * per;
-    double a;
+    float a;
     if constexpr (LX == 0) {
       a = run_pass_gen(p, mb, f.kind, f.last, slo, shi, smem);
     } else if constexpr (LX == LY) {
@@ -562,7 +562,7 @@ __device__ __forceinline__ void class_pass(const Params& p, Shared& sh, int base
                : run_pass<LY, LX, LY, false>(p, mb, f.kind, f.last, slo, shi, smem, sh, mphase, none, tcf);
     }
     if (f.slot >= 0) {
-      const double tot = block_sum(a, sh);
+      const double tot = block_sum_f(a, sh);
       if (threadIdx.x == 0) p.partials[(static_cast<size_t>(f.slot) * p.batch + mb) * G + blockIdx.x] = tot;
     }
   }

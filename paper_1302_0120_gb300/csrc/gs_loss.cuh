@@ -29,8 +29,9 @@ namespace gsk {
 constexpr float kTolLit = 0.1f;    // t_l, Sec. II
 constexpr float kTolDark = 3e-4f;  // t_d, Sec. II
 
-// partial-sum rows of the loss kernel (each [grid])
-enum LossRow { kRowFlag = 0, kRowSumI = 1, kRowMaxI = 2, kRowLoss = 3, kRowEl = 4, kRowEd = 5 };
+// partial-sum rows of the loss kernel (each [grid]); row kRowStaged holds the
+// reduced target statistics of a prepared target (flag, sum I, max I).
+enum LossRow { kRowFlag = 0, kRowSumI = 1, kRowMaxI = 2, kRowLoss = 3, kRowEl = 4, kRowEd = 5, kRowStaged = 6 };
 
 // Grid barrier for the loss kernel (same protocol as grid_sync).
 static __device__ bool loss_sync(const LossParams& p, unsigned& target, Shared& sh) {
@@ -62,7 +63,13 @@ static __device__ bool loss_sync(const LossParams& p, unsigned& target, Shared& 
   return sh.flag != 0;
 }
 
-template <int LN>
+// MODE (LossMode, gs_internal.h) kLossFused: validate and stage the target,
+// then the three passes (one call does everything). kLossPrepare: validate
+// and stage the target only, and reduce its statistics into row kRowStaged.
+// kLossStep: the three passes on the staged target (the target of the last
+// kLossPrepare launch).
+
+template <int LN, int MODE>
 __global__ void __launch_bounds__(kThreads, 1) gs_loss_kernel(const LossParams p) {
   using G = GroupT<LN>;
   using L = FieldLayout<LN, LN>;
@@ -95,7 +102,7 @@ __global__ void __launch_bounds__(kThreads, 1) gs_loss_kernel(const LossParams p
   __syncthreads();
 
   // Target: validate this block's rows, and stage its columns transposed.
-  {
+  if constexpr (MODE != kLossStep) {
     const int r0 = split(b, gridDim.x, N);
     const int r1 = split(b + 1, gridDim.x, N);
     bool bad = false;
@@ -150,6 +157,25 @@ __global__ void __launch_bounds__(kThreads, 1) gs_loss_kernel(const LossParams p
       }
     }
   }
+  if constexpr (MODE == kLossPrepare) {
+    // the staged target's statistics, reduced once (FP64, fixed order)
+    if (!loss_sync(p, target, sh)) return;
+    if (b == 0 && threadIdx.x == 0) {
+      const int G = gridDim.x;
+      double flag = 0.0, sum_i = 0.0, max_i = 0.0;
+      for (int c = 0; c < G; ++c) {
+        flag += p.partials[kRowFlag * G + c];
+        sum_i += p.partials[kRowSumI * G + c];
+        max_i = fmax(max_i, p.partials[kRowMaxI * G + c]);
+      }
+      double* st = p.partials + kRowStaged * kMaxGrid;  // a fixed place: the step may use another grid
+      st[0] = flag;
+      st[1] = sum_i;
+      st[2] = max_i;
+      if (!(flag == 0.0)) atomicCAS(p.status, 0, GS_ENUMERIC);
+    }
+    return;
+  }
 
   // Pass 1 (rows): x = exp(i phi), B = DFT_x(x).
   {
@@ -196,10 +222,17 @@ __global__ void __launch_bounds__(kThreads, 1) gs_loss_kernel(const LossParams p
   {
     double tot = 0.0, sum_i = 0.0, max_i = 0.0;
     const int G = gridDim.x;
-    for (int c = 0; c < G; ++c) {
-      tot += p.partials[kRowFlag * G + c];
-      sum_i += p.partials[kRowSumI * G + c];
-      max_i = fmax(max_i, p.partials[kRowMaxI * G + c]);
+    if constexpr (MODE == kLossStep) {
+      const double* st = p.partials + kRowStaged * kMaxGrid;  // written by the prepare launch
+      tot = st[0];
+      sum_i = st[1];
+      max_i = st[2];
+    } else {
+      for (int c = 0; c < G; ++c) {
+        tot += p.partials[kRowFlag * G + c];
+        sum_i += p.partials[kRowSumI * G + c];
+        max_i = fmax(max_i, p.partials[kRowMaxI * G + c]);
+      }
     }
     const double ep = p.p_slm ? *p.energy : static_cast<double>(N) * N;
     if (max_i > 0.0 && ep > 0.0) {
@@ -221,7 +254,7 @@ __global__ void __launch_bounds__(kThreads, 1) gs_loss_kernel(const LossParams p
   // B = swap(IDFT_y(r y)) for the adjoint.
   const bool want_grad = p.grad != nullptr;
   const bool want_phys = p.phys != nullptr;
-  double acc = 0.0, acc_l = 0.0, acc_d = 0.0;
+  float acc = 0.f, acc_l = 0.f, acc_d = 0.f;  // this thread's lines, FP32
   {
     const int lo = split(b, gridDim.x, L::NBLK);
     const int hi = split(b + 1, gridDim.x, L::NBLK);
@@ -264,7 +297,7 @@ __global__ void __launch_bounds__(kThreads, 1) gs_loss_kernel(const LossParams p
           if (want_phys) sa2[T * i] = a2;
           v[i] = make_float2(r * y.y, r * y.x);  // swapped: the next forward DFT acts as the inverse
         }
-        if (gact) acc += static_cast<double>(part);
+        if (gact) acc += part;
         if (want_phys) {  // Eq. (phys-error), once per call: a rolled loop
           float el = 0.f, ed = 0.f;
 #pragma unroll 1
@@ -280,8 +313,8 @@ __global__ void __launch_bounds__(kThreads, 1) gs_loss_kernel(const LossParams p
             }
           }
           if (gact) {
-            acc_l += static_cast<double>(el);
-            acc_d += static_cast<double>(ed);
+            acc_l += el;
+            acc_d += ed;
           }
           grp.sync();
         }
@@ -306,12 +339,13 @@ __global__ void __launch_bounds__(kThreads, 1) gs_loss_kernel(const LossParams p
   }
   {
     const int G = gridDim.x;
-    const double tot = block_sum(acc, sh);
+    // FP32 within the block, FP64 across blocks (below)
+    const double tot = block_sum_f(acc, sh);
     if (threadIdx.x == 0) p.partials[kRowLoss * G + b] = tot;
     if (want_phys) {
-      const double tl = block_sum(acc_l, sh);
+      const double tl = block_sum_f(acc_l, sh);
       if (threadIdx.x == 0) p.partials[kRowEl * G + b] = tl;
-      const double td = block_sum(acc_d, sh);
+      const double td = block_sum_f(acc_d, sh);
       if (threadIdx.x == 0) p.partials[kRowEd * G + b] = td;
     }
   }

@@ -67,6 +67,26 @@ __device__ __forceinline__ double small_sum(double x, double* red) {
   return s;
 }
 
+// The same for one float per thread, in FP32 (the gaps of a pass: a warp's
+// FP64 shuffles would run on the FP64 pipe, 1/64 of the FP32 rate here),
+// widened to FP64 for the normalisation.
+template <int NT>
+__device__ __forceinline__ double small_sum_f(float x, float* red) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+  __syncthreads();  // red is free
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = x;
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x == 0) {
+    float t = 0.f;
+#pragma unroll
+    for (int w = 0; w < NT / 32; ++w) t += red[w];
+    s = static_cast<double>(t);
+  }
+  return s;
+}
+
 __device__ __forceinline__ float small_phase(float2 u) {
   const float ph = atan2f(u.y, u.x);
   return (ph <= -3.14159274f) ? 3.14159274f : ph;
@@ -94,7 +114,7 @@ enum SmallPass { kSmallInit = 0, kSmallRow = 1, kSmallCol = 2, kSmallResid = 3 }
 // and A4's final residual (the columns, forward transform only). Returns this
 // thread's FP64 share of the pass's gap sum.
 template <int LX, int LY, int KIND>
-__device__ __forceinline__ double small_pass(const Params& p, size_t moff, bool last, float2* F, const float* mT,
+__device__ __forceinline__ float small_pass(const Params& p, size_t moff, bool last, float2* F, const float* mT,
                                              float2* X, const StageTw<LX>& twr, const StageTw<LY>& twc) {
   static_assert(KIND == kSmallInit || KIND == kSmallResid, "the iteration passes are small_pass_hot");
   using Gm = SmallGeom<LX, LY>;
@@ -110,7 +130,7 @@ __device__ __forceinline__ double small_pass(const Params& p, size_t moff, bool 
   grp.tw = kRows ? p.twx : p.twy;
   const int t = grp.t;
   const float inv_sqrt_n = p.inv_sqrt_n;
-  double acc = 0.0;
+  float acc = 0.f;
   const StageTw<LN>& stw = [&]() -> const StageTw<LN>& {
     if constexpr (kRows) return twr;
     else return twc;
@@ -149,7 +169,7 @@ __device__ __forceinline__ double small_pass(const Params& p, size_t moff, bool 
         part += d * d;
       }
     }
-    acc += static_cast<double>(part);
+    acc += part;
   }
   __syncthreads();  // the pass's writes are seen by the next pass
   return acc;
@@ -162,7 +182,7 @@ __device__ __forceinline__ double small_pass(const Params& p, size_t moff, bool 
 // scheduler, a body with four copies spent most of its time waiting for
 // instructions. ROWS / COLS: the kinds this instantiation serves.
 template <int LX, int LY, int LN, bool ROWS, bool COLS>
-__device__ __forceinline__ double small_pass_hot(const Params& p, size_t moff, int kind, bool last, float2* F,
+__device__ __forceinline__ float small_pass_hot(const Params& p, size_t moff, int kind, bool last, float2* F,
                                                  const float* mT, float2* X, const StageTw<LN>& stw) {
   using Gm = SmallGeom<LX, LY>;
   static_assert(!ROWS || LN == LX, "row transforms have length nx");
@@ -180,7 +200,7 @@ __device__ __forceinline__ double small_pass_hot(const Params& p, size_t moff, i
   const float inv_sqrt_n = p.inv_sqrt_n;
   // a row pass that ends the run without the final residual stops after the projection
   const int nh = (rows && last && !p.final_resid) ? 1 : 2;
-  double acc = 0.0;
+  float acc = 0.f;
   for (int l0 = 0; l0 < LINES; l0 += NG) {
     const int line = l0 + static_cast<int>(threadIdx.x) / T;
     float2 v[32];
@@ -227,7 +247,7 @@ __device__ __forceinline__ double small_pass_hot(const Params& p, size_t moff, i
 #pragma unroll
       for (int i = 0; i < 32; ++i) F[rows ? Gm::fo(line, t + T * i) : Gm::fo(t + T * i, line)] = v[i];
     }
-    acc += static_cast<double>(part);
+    acc += part;
   }
   __syncthreads();  // the pass's writes are seen by the next pass
   return acc;
@@ -239,6 +259,7 @@ __global__ void __launch_bounds__(SmallGeom<LX, LY>::NT) gs_small(const Params p
   constexpr int NT = Gm::NT;
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ double red[NT / 32];
+  __shared__ float redf[NT / 32];
   float2* F = reinterpret_cast<float2*>(smem);
   float* mT = reinterpret_cast<float*>(smem + Gm::F_BYTES);
   float2* X = reinterpret_cast<float2*>(smem + Gm::F_BYTES + Gm::M_BYTES);
@@ -295,7 +316,7 @@ __global__ void __launch_bounds__(SmallGeom<LX, LY>::NT) gs_small(const Params p
     const bool rows = (q & 1) != 0;
     const int nu = q >> 1;
     const bool last = rows && nu == K - 1;
-    double a;
+    float a;
     if constexpr (LX == LY) {
       a = small_pass_hot<LX, LY, LX, true, true>(p, moff, rows ? kSmallRow : kSmallCol, last, F, mT, X, twr);
     } else {
@@ -304,14 +325,14 @@ __global__ void __launch_bounds__(SmallGeom<LX, LY>::NT) gs_small(const Params p
     }
     // the raw sum now, the normalisation after the loop (an FP64 division
     // and square root on one thread would hold up the next pass)
-    const double sum = small_sum<NT>(a, red);
+    const double sum = small_sum_f<NT>(a, redf);
     if (threadIdx.x == 0) {
       double* const out = rows ? g_out : r_out;
       if (out) out[nu] = sum;
     }
   }
   if (p.final_resid) {
-    const double rc = small_sum<NT>(small_pass<LX, LY, kSmallResid>(p, moff, false, F, mT, X, twr, twc), red);
+    const double rc = small_sum_f<NT>(small_pass<LX, LY, kSmallResid>(p, moff, false, F, mT, X, twr, twc), redf);
     if (r_out && threadIdx.x == 0) r_out[K] = rc;
   }
   __syncthreads();  // thread 0's sums are visible to the block

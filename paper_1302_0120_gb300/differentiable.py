@@ -51,6 +51,36 @@ class LossContext:
             raise B.GSError(rc, "gs_loss_grad")
         return loss, grad
 
+    def prepare(self, target):
+        """Stage ``target`` once (C: gs_loss_prepare) for ``loss_grad_prepared``."""
+        import torch
+
+        if not (target.is_cuda and target.dtype == torch.float32 and target.is_contiguous()
+                and tuple(target.shape) == (self.n, self.n)):
+            raise ValueError(f"target must be a contiguous float32 CUDA tensor of shape ({self.n}, {self.n})")
+        self.stream.wait_stream(torch.cuda.current_stream(target.device))
+        rc = B.gs_loss_prepare(self.handle, target.data_ptr())
+        if rc != B.GS_OK:
+            raise B.GSError(rc, "gs_loss_prepare")
+
+    def loss_grad_prepared(self, phase, want_grad: bool = True):
+        """The loss and gradient on the staged target (C: gs_loss_grad_prepared)."""
+        import torch
+
+        if not (phase.is_cuda and phase.dtype == torch.float32 and phase.is_contiguous()
+                and tuple(phase.shape) == (self.n, self.n)):
+            raise ValueError(f"phase must be a contiguous float32 CUDA tensor of shape ({self.n}, {self.n})")
+        cur = torch.cuda.current_stream(phase.device)
+        loss = torch.empty(1, dtype=torch.float64, device=phase.device)
+        grad = torch.empty_like(phase) if want_grad else None
+        self.stream.wait_stream(cur)
+        rc = B.gs_loss_grad_prepared(self.handle, phase.data_ptr(), loss.data_ptr(),
+                                     grad.data_ptr() if grad is not None else 0)
+        cur.wait_stream(self.stream)
+        if rc != B.GS_OK:
+            raise B.GSError(rc, "gs_loss_grad_prepared")
+        return loss, grad
+
     def status(self) -> int:
         return B.gs_status(self.handle)
 
@@ -100,9 +130,10 @@ def optimize_phase(target, phase0, steps: int = 200, lr: float = 0.05, betas=(0.
     """Adam on the phase. Returns (phase, losses) with losses[k] the loss
     before step k (and the final loss last).
 
-    With ``graph`` (the default) one step -- the loss-and-gradient launch and
-    the library's Adam update (gs_adam_step) -- is captured once as a CUDA
-    graph and replayed after three eager steps; the context then needs its own
+    With ``graph`` (the default) the target is staged once (gs_loss_prepare)
+    and one step -- the loss-and-gradient launch on the staged target and the
+    library's Adam update (gs_adam_step) -- is captured once as a CUDA graph
+    and replayed after three eager steps; the context then needs its own
     (non-default) stream, and one is created when ``lctx`` is None. Otherwise
     every step goes through the autograd function above and torch's Adam."""
     import torch
@@ -121,11 +152,16 @@ def optimize_phase(target, phase0, steps: int = 200, lr: float = 0.05, betas=(0.
         state = torch.zeros(2, dtype=torch.int32, device=phase.device)
         loss = torch.zeros(1, dtype=torch.float64, device=phase.device)
         record = torch.zeros(steps + 1, dtype=torch.float64, device=phase.device)
+        # the target is validated and staged once; every step runs only the
+        # three transform passes on it
+        rc = B.gs_loss_prepare(lctx.handle, target.data_ptr())
+        if rc != B.GS_OK:
+            raise B.GSError(rc, "gs_loss_prepare")
 
         def step():
-            rc = B.gs_loss_grad(lctx.handle, target.data_ptr(), phase.data_ptr(), loss.data_ptr(), grad.data_ptr())
+            rc = B.gs_loss_grad_prepared(lctx.handle, phase.data_ptr(), loss.data_ptr(), grad.data_ptr())
             if rc != B.GS_OK:
-                raise B.GSError(rc, "gs_loss_grad")
+                raise B.GSError(rc, "gs_loss_grad_prepared")
             rc = B.gs_adam_step(phase.data_ptr(), grad.data_ptr(), m.data_ptr(), v.data_ptr(), phase.numel(),
                                 state.data_ptr(), lr, betas[0], betas[1], eps, s.cuda_stream)
             if rc != B.GS_OK:
@@ -141,9 +177,9 @@ def optimize_phase(target, phase0, steps: int = 200, lr: float = 0.05, betas=(0.
         for k in range(warm, steps):
             g.replay()
             record[k].copy_(loss[0])
-        rc = B.gs_loss_grad(lctx.handle, target.data_ptr(), phase.data_ptr(), loss.data_ptr(), 0)
+        rc = B.gs_loss_grad_prepared(lctx.handle, phase.data_ptr(), loss.data_ptr(), 0)
         if rc != B.GS_OK:
-            raise B.GSError(rc, "gs_loss_grad")
+            raise B.GSError(rc, "gs_loss_grad_prepared")
         record[steps].copy_(loss[0])
     torch.cuda.current_stream().wait_stream(s)
     keep = list(range(0, steps, record_every)) + [steps]

@@ -8,7 +8,7 @@ import pytest
 
 import oracle.gs_oracle as O
 from paper_1302_0120_gb300 import synthetic as S
-from tests.gpu_util import aligned_rel_err
+from tests.gpu_util import aligned_rel_err, GROUPING_RTOL
 from tests.test_gpu_parity import check_run
 
 pytestmark = pytest.mark.gpu
@@ -99,7 +99,7 @@ def test_batch_matches_single_runs():
         ph, r = ph.cpu().numpy(), r.cpu().numpy()
     for k, (I, phi0) in enumerate(masks):
         ph1, r1, _, st = gpu_gs(I, phi0, iters)
-        assert st == 0 and np.array_equal(ph[k], ph1) and np.allclose(r[k], r1, rtol=1e-12, atol=0)
+        assert st == 0 and np.array_equal(ph[k], ph1) and np.allclose(r[k], r1, rtol=GROUPING_RTOL, atol=0)
 
 
 def test_loss_rejects_general_grids():

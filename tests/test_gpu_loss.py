@@ -49,6 +49,65 @@ def test_loss_and_gradient_match_oracle(n, nspots):
     assert st == 0 and none is None and loss_only == loss
 
 
+@pytest.mark.parametrize("n,nspots", [(64, 6), (1024, 100)])
+def test_prepared_target_matches_fused_call(n, nspots):
+    """gs_loss_prepare + gs_loss_grad_prepared give the fused call's loss and
+    gradient bit for bit (the same passes on the same staged target), call
+    after call, and both match the oracle; a new phase needs no new prepare."""
+    import torch
+
+    from paper_1302_0120_gb300 import _binding as B
+    from paper_1302_0120_gb300.differentiable import LossContext
+
+    I = normalized_target(40 + n, n, nspots)
+    It = torch.from_numpy(I).cuda()
+    lc = LossContext(n)
+    lc.prepare(It)
+    for k in range(3):
+        phi = S.random_phase(41 + n + k, n, n)
+        Pt = torch.from_numpy(phi).cuda()
+        l_p, g_p = lc.loss_grad_prepared(Pt)
+        l_p, g_p = float(l_p.item()), g_p.cpu().numpy()
+        assert lc.status() == 0
+        lc2 = LossContext(n)
+        l_f, g_f = lc2.loss_grad(It, Pt)
+        assert lc2.status() == 0
+        assert l_p == float(l_f.item()) and np.array_equal(g_p, g_f.cpu().numpy())
+        lc2.close()
+        ref_l = O.intensity_loss(phi, I)
+        assert abs(l_p - ref_l) <= 1e-4 * ref_l
+        if n <= 64:
+            ref_g = O.intensity_loss_grad(phi, I)
+            assert np.linalg.norm(g_p - ref_g) / np.linalg.norm(ref_g) <= 1e-3
+    # an iteration run on the same context overwrites the staged target
+    from paper_1302_0120_gb300 import GerchbergSaxton  # noqa: F401
+
+    loss = torch.empty(1, dtype=torch.float64, device="cuda")
+    out = torch.empty_like(It)
+    r = torch.empty(3, dtype=torch.float64, device="cuda")
+    assert B.gs_run(lc.handle, It.data_ptr(), Pt.data_ptr(), 2, out.data_ptr(), r.data_ptr(), 0) == 0
+    assert lc.status() == 0
+    assert B.gs_loss_grad_prepared(lc.handle, Pt.data_ptr(), loss.data_ptr(), 0) == B.GS_EINVAL
+    lc.close()
+
+
+def test_prepared_nonfinite_target():
+    import torch
+
+    from paper_1302_0120_gb300 import GS_ENUMERIC
+    from paper_1302_0120_gb300.differentiable import LossContext
+
+    n = 64
+    I = normalized_target(44, n, 6)
+    I[5, 7] = np.nan
+    lc = LossContext(n)
+    lc.prepare(torch.from_numpy(I).cuda())
+    assert lc.status() == GS_ENUMERIC
+    loss, _ = lc.loss_grad_prepared(torch.from_numpy(S.random_phase(45, n, n)).cuda())
+    assert lc.status() == GS_ENUMERIC and np.isnan(loss.item())
+    lc.close()
+
+
 def test_autograd_and_adam():
     import torch
 

@@ -7,6 +7,7 @@ import numpy as np
 import pytest
 
 from paper_1302_0120_gb300 import synthetic as S
+from tests.gpu_util import GROUPING_RTOL
 
 pytestmark = pytest.mark.gpu
 
@@ -58,7 +59,7 @@ def test_mixed_matches_per_size_launches(tc, counts, iters, from_target):
             assert gs1.status() == 0
             ph, r, g = ph.cpu().numpy(), r.cpu().numpy(), g.cpu().numpy()
         assert np.array_equal(out[n][0], ph), n
-        assert np.allclose(out[n][1], r, rtol=1e-12, atol=0) and np.allclose(out[n][2], g, rtol=1e-12, atol=0), n
+        assert np.allclose(out[n][1], r, rtol=GROUPING_RTOL, atol=0) and np.allclose(out[n][2], g, rtol=GROUPING_RTOL, atol=0), n
 
 
 def test_mixed_rejects_one_mask():
@@ -102,6 +103,6 @@ def test_mask_groups_do_not_change_results(group):
             res[("single", g)] = (ph.cpu().numpy(), r.cpu().numpy())
     for n in counts:
         assert np.array_equal(res[0][n][0], res[group][n][0])
-        assert np.allclose(res[0][n][1], res[group][n][1], rtol=1e-12, atol=0)
+        assert np.allclose(res[0][n][1], res[group][n][1], rtol=GROUPING_RTOL, atol=0)
     assert np.array_equal(res[("single", 0)][0], res[("single", group)][0])
-    assert np.allclose(res[("single", 0)][1], res[("single", group)][1], rtol=1e-12, atol=0)
+    assert np.allclose(res[("single", 0)][1], res[("single", group)][1], rtol=GROUPING_RTOL, atol=0)

@@ -10,7 +10,7 @@ import numpy as np
 import pytest
 
 from paper_1302_0120_gb300 import synthetic as S
-from tests.gpu_util import gpu_gs
+from tests.gpu_util import gpu_gs, GROUPING_RTOL
 from tests.test_gpu_parity import check_run
 
 pytestmark = pytest.mark.gpu
@@ -27,8 +27,8 @@ def _inputs(ny, nx, seed=0):
 
 def _same(a, b):
     assert np.array_equal(a[0], b[0]), np.max(np.abs(a[0] - b[0]))
-    np.testing.assert_allclose(a[1], b[1], rtol=1e-12, atol=0)
-    np.testing.assert_allclose(a[2], b[2], rtol=1e-12, atol=0)
+    np.testing.assert_allclose(a[1], b[1], rtol=GROUPING_RTOL, atol=0)
+    np.testing.assert_allclose(a[2], b[2], rtol=GROUPING_RTOL, atol=0)
     assert a[3] == 0 and b[3] == 0
 
 

@@ -15,7 +15,7 @@ import pytest
 
 import oracle.gs_oracle as O
 from paper_1302_0120_gb300 import synthetic as S
-from tests.gpu_util import aligned_rel_err
+from tests.gpu_util import aligned_rel_err, GROUPING_RTOL
 
 pytestmark = pytest.mark.gpu
 
@@ -107,7 +107,7 @@ def test_batch_matches_single_runs(n):
         ph1, r1, g1, st = tc_run(I, phi0, iters)
         assert st == 0
         assert np.array_equal(ph[k], ph1)
-        assert np.allclose(r[k], r1, rtol=1e-12, atol=0) and np.allclose(g[k], g1, rtol=1e-12, atol=0)
+        assert np.allclose(r[k], r1, rtol=GROUPING_RTOL, atol=0) and np.allclose(g[k], g1, rtol=GROUPING_RTOL, atol=0)
 
 
 def test_mixed_sizes_64_masks():
