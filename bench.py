@@ -488,12 +488,25 @@ def run_gpu(args):
     if args.serve_seconds > 0 and ws == 1:
         from paper_1302_0120_gb300 import serving as SV
 
-        summ, sch, ex = SV.run_service(rate_hz=args.serve_rate, seconds=args.serve_seconds, sizes=(512, 1024),
-                                       lanes=(1, 2), iters=30, warmup_s=0.3)
-        ex.close()
-        del sch, ex  # the finished requests hold their targets
-        serving = {k: (round(v, 4) if isinstance(v, float) else v) for k, v in summ.items() if k != "lanes"}
-        serving["lanes"] = [f"{p['name']} batch<={p['max_batch']} grid={p['grid']}" for p in summ["lanes"]]
+        def stream(rate, seconds, **kw):
+            summ, sch, ex = SV.run_service(rate_hz=rate, seconds=seconds, sizes=(512, 1024), lanes=(1, 2), iters=30,
+                                           warmup_s=0.3, **kw)
+            ex.close()
+            del sch, ex  # the finished requests hold their targets
+            out = {k: (round(v, 4) if isinstance(v, float) else v) for k, v in summ.items() if k != "lanes"}
+            out["lanes"] = [f"{p['name']} batch<={p['max_batch']} grid={p['grid']}" for p in summ["lanes"]]
+            return out
+
+        serving = stream(args.serve_rate, args.serve_seconds)
+        half = max(1.0, args.serve_seconds / 2)
+        # twice the rate; the same rate with a loop that sleeps between events;
+        # the same rate on disjoint shares of the SMs
+        serving["at_2x_rate"] = {k: v for k, v in stream(2 * args.serve_rate, half).items()
+                                 if k in ("requests", "p50_ms", "p99_ms", "max_ms", "rate_hz", "by_size")}
+        serving["event_driven"] = {k: v for k, v in stream(args.serve_rate, half, wait="event").items()
+                                   if k in ("requests", "p50_ms", "p99_ms", "max_ms", "rate_hz", "wait")}
+        serving["disjoint_sm_shares"] = {k: v for k, v in stream(args.serve_rate, half, share_sms=False).items()
+                                         if k in ("requests", "p50_ms", "p99_ms", "max_ms", "lanes")}
 
     def timed(fn, steps):
         """Mean device ms of fn() over `steps` launches, L2 flushed before each."""

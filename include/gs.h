@@ -506,6 +506,22 @@ int gs_run_noalloc(int nx, int ny, unsigned flags, void* stream, const float* ta
  */
 int gs_fp32_peak(double* tflops_out, void* stream);
 
+/*
+ * gs_stream_notify -- wake a host thread when a stream reaches this point
+ * (serving utility; the paper has no counterpart).
+ *
+ * Enqueues on `stream` (a cudaStream_t, or NULL for the legacy default
+ * stream) a host function that writes the 8-byte value 1 to the file
+ * descriptor `fd` (an eventfd or a pipe owned by the caller) once all work
+ * enqueued before it on that stream has finished. A request loop can then
+ * sleep in select/poll on `fd` until a launch completes or the next request
+ * arrives, instead of spinning on events. The write happens on a thread of the
+ * CUDA driver; the descriptor must stay open until it has run. Asynchronous.
+ * Returns GS_EINVAL for fd < 0, GS_ECUDA if the host function cannot be
+ * enqueued.
+ */
+int gs_stream_notify(void* stream, int fd);
+
 /* gs_strerror -- static English text for a status code (never NULL). */
 const char* gs_strerror(int code);
 

@@ -59,6 +59,7 @@ SIGNATURES = {
     "gs_test_corrupt_workspace": (_c_int, [_vp]),
     "gs_get_trace": (_c_int, [_vp, _vp, _c_int, ctypes.POINTER(_c_int), ctypes.POINTER(_c_int)]),
     "gs_fp32_peak": (_c_int, [ctypes.POINTER(ctypes.c_double), _vp]),
+    "gs_stream_notify": (_c_int, [_vp, _c_int]),
     "gs_adam_step": (_c_int, [_vp, _vp, _vp, _vp, ctypes.c_longlong, _vp, ctypes.c_float, ctypes.c_float,
                               ctypes.c_float, ctypes.c_float, _vp]),
 }
@@ -293,6 +294,11 @@ def gs_fp32_peak(stream: int | None = None) -> float:
     if rc != GS_OK:
         raise GSError(rc, "gs_fp32_peak")
     return out.value
+
+
+def gs_stream_notify(stream: int | None, fd: int) -> int:
+    """Enqueue a write of 1 to ``fd`` once ``stream`` reaches it; returns the status code."""
+    return lib().gs_stream_notify(_vp(stream or 0), int(fd))
 
 
 def gs_destroy(ctx: int) -> int:

@@ -19,9 +19,16 @@ module serves a stream of such requests on one GPU:
   lane (kept on the device, one warm-start buffer per lane); the last mask of
   a launch becomes that lane's next warm start. A class with several lanes
   therefore keeps one warm start per lane, not one for the class.
-* The per-launch sequence (target upload from pinned host memory, warm-start
-  copies, the batched run, the warm-start update) is captured once per lane
-  and batch size as a CUDA graph and replayed.
+* Targets reach the lane from pinned host memory: a client renders each
+  pattern into a buffer of a pinned pool before it submits the request (the
+  loop stages upcoming requests this way while it has nothing else to do;
+  a request staged late pays for the copy in its latency), and the launch
+  copies it to the device on the lane's stream. The rest of the per-launch
+  sequence (warm-start copies, the batched run, the warm-start update) is
+  captured once per lane and batch size as a CUDA graph and replayed.
+* The loop either spins on the lanes' completion events or sleeps until the
+  next arrival or the next completion, which the library signals through an
+  eventfd (gs_stream_notify) from the end of each launch.
 
 Every step of the method runs in the CUDA library; this module only moves
 buffers and decides what to launch when.
@@ -52,6 +59,7 @@ class Request:
     warm_in: Optional[np.ndarray] = None   # kept when the server records inputs
     phase: Optional[np.ndarray] = None     # kept when the server records results
     residual: Optional[float] = None
+    pinned: Optional[object] = None        # the target in a pinned host buffer of the client's pool
 
     @property
     def latency(self) -> float:
@@ -77,14 +85,17 @@ def lane_bytes(n: int, max_batch: int, iters: int, workspace_bytes: Callable[[in
 
 def plan_lanes(sizes: Sequence[int], lanes_per_size: Sequence[int], sm_count: int, budget_bytes: int, iters: int,
                workspace_bytes: Callable[[int, int, int], int], max_batch_cap: int = 16,
-               weights: Optional[Sequence[float]] = None) -> List[LanePlan]:
+               weights: Optional[Sequence[float]] = None, share_sms: bool = False) -> List[LanePlan]:
     """Split the SMs and the memory budget among the lanes.
 
     SMs go to each size in proportion to its expected work (``weights``,
     default n^2 log n per request, equal request rates) and then evenly to its
     lanes. Each lane gets the largest batch (<= max_batch_cap) whose bytes fit
     its share of the budget, which is split in the same proportion. Raises
-    ValueError when a lane cannot hold even one mask.
+    ValueError when a lane cannot hold even one mask. With ``share_sms`` every
+    lane's grid is the whole device instead: the lanes' launches time-share
+    the SMs (a launch starts when the previous one leaves room for all its
+    blocks) instead of running side by side on disjoint shares.
     """
     if weights is None:
         weights = [n * n * math.log2(n) for n in sizes]
@@ -104,6 +115,10 @@ def plan_lanes(sizes: Sequence[int], lanes_per_size: Sequence[int], sm_count: in
                 raise ValueError(f"memory budget too small for one {n}x{n} mask")
             plans.append(LanePlan(f"{n}/{li}", n, b, grid, lane_bytes(n, b, iters, workspace_bytes)))
             sm_left -= grid
+    if share_sms:
+        for p in plans:
+            p.grid = sm_count
+        return plans
     # hand SMs lost to rounding to the largest lanes, never exceeding the device
     i = 0
     while sm_left > 0 and plans:
@@ -154,10 +169,15 @@ class Scheduler:
 
 
 class GpuExecutor:
-    """Runs lanes on the GPU through the C ABI (batched runs, graph replay)."""
+    """Runs lanes on the GPU through the C ABI (batched runs, graph replay).
+
+    ``notify=True`` creates an eventfd (``self.fd``) that the end of every
+    launch writes through gs_stream_notify, for loops that sleep."""
 
     def __init__(self, plans: Sequence[LanePlan], iters: int, device=None, use_graphs: bool = True,
-                 record: bool = False, warm_seed: int = 7):
+                 record: bool = False, warm_seed: int = 7, notify: bool = False, pool_extra: int = 16):
+        import os
+
         import torch
 
         from . import _binding as B
@@ -169,9 +189,12 @@ class GpuExecutor:
         self.record = record
         self.use_graphs = use_graphs
         self.device = device or torch.device("cuda", torch.cuda.current_device())
+        self.fd = os.eventfd(0, os.EFD_NONBLOCK) if notify else None
         self.lanes = {}
+        slots = collections.Counter()
         for p in plans:
             n, mb = p.n, p.max_batch
+            slots[n] += mb
             st = torch.cuda.Stream(device=self.device)
             h = B.gs_create_batched(n, n, mb, B.GS_FINAL_RESIDUAL, st.cuda_stream)
             rc = B.gs_set_grid(h, p.grid)
@@ -192,13 +215,15 @@ class GpuExecutor:
                 "launch_id": 0,
             }
             self.lanes[p.name] = L
+        # the clients' pinned buffers: enough for every lane's batch plus the
+        # requests staged ahead of their arrival
+        self.pool = {n: [torch.empty((n, n), dtype=torch.float32).pin_memory() for _ in range(k + pool_extra)]
+                     for n, k in slots.items()}
         self.graph_ok = use_graphs
 
-    # -- the launch sequence of one lane for b masks
+    # -- the launch sequence of one lane for b masks (targets already in L["I"])
     def _enqueue(self, L, b):
-        torch = self.torch
         n = L["plan"].n
-        L["I"][:b].copy_(L["hI"][:b], non_blocking=True)
         L["P"][:b].copy_(L["warm"].expand(b, n, n))
         rc = self.B.gs_run_batched(L["handle"], b, L["I"].data_ptr(), L["P"].data_ptr(), self.iters,
                                    L["P"].data_ptr(), L["R"].data_ptr(), L["G"].data_ptr())
@@ -221,6 +246,19 @@ class GpuExecutor:
                 g = None
         return g
 
+    def stage(self, r: Request) -> bool:
+        """Copy a request's target into a pinned buffer of the pool (the
+        client's side of a submission). False when the pool is empty."""
+        if r.pinned is not None:
+            return True
+        pool = self.pool.get(r.n)
+        if not pool:
+            return False
+        buf = pool.pop()
+        buf.copy_(self.torch.from_numpy(r.target))
+        r.pinned = buf
+        return True
+
     def idle(self, p: LanePlan) -> bool:
         return self.lanes[p.name]["busy"] is None
 
@@ -228,8 +266,11 @@ class GpuExecutor:
         torch = self.torch
         L = self.lanes[p.name]
         b = len(reqs)
+        srcs = []
         for k, r in enumerate(reqs):
-            L["hI"][k].copy_(torch.from_numpy(r.target))
+            if not self.stage(r):  # no pinned buffer left: through the lane's own
+                L["hI"][k].copy_(torch.from_numpy(r.target))
+            srcs.append(r.pinned if r.pinned is not None else L["hI"][k])
             r.slot = k
             r.launch_id = L["launch_id"]
         if self.record:  # the lane is idle, so its warm start is final
@@ -237,6 +278,8 @@ class GpuExecutor:
             for r in reqs:
                 r.warm_in = warm
         with torch.cuda.stream(L["stream"]):
+            for k, src in enumerate(srcs):
+                L["I"][k].copy_(src, non_blocking=True)
             g = self._graph(L, b)
             if g is not None:
                 g.replay()
@@ -244,6 +287,10 @@ class GpuExecutor:
                 self._enqueue(L, b)
             ev = torch.cuda.Event()
             ev.record(L["stream"])
+        if self.fd is not None:
+            rc = self.B.gs_stream_notify(L["stream"].cuda_stream, self.fd)
+            if rc != self.B.GS_OK:
+                raise self.B.GSError(rc, "gs_stream_notify")
         L["busy"] = (ev, reqs)
         L["launch_id"] += 1
 
@@ -266,30 +313,68 @@ class GpuExecutor:
                 r.residual = float(R[k])
         for r in reqs:
             r.finish = now
+            if r.pinned is not None:  # the copy to the device is done: back to the pool
+                self.pool[r.n].append(r.pinned)
+                r.pinned = None
         return reqs
 
+    def wait(self, timeout: float):
+        """Sleep until a launch completes (its notification) or `timeout` s."""
+        import os
+        import select
+
+        if timeout > 0:
+            select.select([self.fd], [], [], timeout)
+        try:
+            os.eventfd_read(self.fd)
+        except BlockingIOError:
+            pass
+
     def close(self):
+        import os
+
         for L in self.lanes.values():
             L["graphs"].clear()
             self.B.gs_destroy(L["handle"])
         self.lanes = {}
+        if self.fd is not None:
+            self.torch.cuda.synchronize(self.device)  # every notification has run
+            os.close(self.fd)
+            self.fd = None
 
 
 def serve(arrivals: Sequence[Request], plans: Sequence[LanePlan], executor, clock=time.perf_counter,
-          t0: Optional[float] = None) -> Scheduler:
+          t0: Optional[float] = None, lookahead_s: float = 0.002, wait: str = "spin") -> Scheduler:
     """Run the request loop until every request in ``arrivals`` (sorted by
     arrival time, relative to ``t0``) is finished. Returns the scheduler; the
-    finished requests are in ``scheduler.done`` with their times."""
+    finished requests are in ``scheduler.done`` with their times.
+
+    While it has nothing else to do, the loop plays the clients' part for the
+    requests due within ``lookahead_s``: their targets go into pinned buffers
+    (``executor.stage``) before they are submitted. ``wait="event"`` sleeps
+    between events (``executor.wait``: a completion, or the next arrival)
+    instead of spinning."""
     sch = Scheduler(plans, executor)
     t0 = clock() if t0 is None else t0
     i = 0
     total = len(arrivals)
+    stage = getattr(executor, "stage", None)
+    sleep = wait == "event" and getattr(executor, "fd", None) is not None
+    staged = 0
     while len(sch.done) < total:
         now = clock() - t0
         while i < total and arrivals[i].arrival <= now:
             sch.submit(arrivals[i])
             i += 1
         sch.tick(now)
+        if stage is not None:
+            staged = max(staged, i)
+            while staged < total and arrivals[staged].arrival <= now + lookahead_s and stage(arrivals[staged]):
+                staged += 1
+        if sleep and not any(sch.pending[p.n] and executor.idle(p) for p in plans):
+            # nothing to launch: sleep until a completion or the next arrival
+            nxt = arrivals[i].arrival - (clock() - t0) if i < total else 0.05
+            executor.wait(min(max(nxt, 0.0), 0.05))
     return sch
 
 
@@ -334,16 +419,19 @@ def latency_summary(done: Sequence[Request]) -> dict:
 
 def run_service(rate_hz: float = 1000.0, seconds: float = 10.0, sizes=(512, 1024), lanes=(1, 2), iters: int = 30,
                 budget_bytes: int = 2 << 30, seed: int = 0, max_batch_cap: int = 16, record: bool = False,
-                use_graphs: bool = True, warmup_s: float = 0.5, weights=None):
+                use_graphs: bool = True, warmup_s: float = 0.5, weights=None, wait: str = "spin",
+                share_sms: bool = True):
     """Serve a Poisson stream on the current GPU; returns (summary, scheduler, executor).
 
-    ``weights`` splits the SMs among the sizes (see plan_lanes); by default
-    every lane gets the same share. At 512^2 and 1024^2 a mask's latency is
-    dominated by the fixed cost of each pass rather than by its work, so equal
-    shares give the lower tail: on one GB300 (1 kHz, 50/50 sizes, 30
-    iterations, one 512 lane and two 1024 lanes) p99 3.45 ms (p50 1.35) with
-    equal shares against 4.19 ms (p50 1.10) with shares proportional to
-    n^2 log n."""
+    By default every lane's launches use the whole device and time-share it
+    (``share_sms``): at 512^2 and 1024^2 a mask's latency is set by the fixed
+    cost of each pass, which a share of the SMs stretches (about 1.3 ms for a
+    1024^2 mask on a third of the device against 0.5 ms on all of it), while
+    at 1 kHz the device is busy less than half the time. On one GB300 (1 kHz,
+    50/50 sizes, 30 iterations, one 512 lane and two 1024 lanes): p50 / p99
+    0.59 / 2.11 ms time-sharing, 1.22 / 3.08 ms on disjoint equal shares (and
+    1.54 / 2.60 ms with three 1024 lanes). ``weights`` splits the SMs among the
+    sizes when the lanes do not share them (see plan_lanes)."""
     import torch
 
     from . import _binding as B
@@ -355,21 +443,21 @@ def run_service(rate_hz: float = 1000.0, seconds: float = 10.0, sizes=(512, 1024
         weights = [1.0] * len(sizes)
     plans = plan_lanes(list(sizes), list(lanes), sm, budget_bytes, iters,
                        lambda nx, ny, b: B.gs_workspace_bytes_batched(nx, ny, b, B.GS_FINAL_RESIDUAL),
-                       max_batch_cap=max_batch_cap, weights=weights)
-    ex = GpuExecutor(plans, iters, use_graphs=use_graphs, record=record)
+                       max_batch_cap=max_batch_cap, weights=weights, share_sms=share_sms)
+    ex = GpuExecutor(plans, iters, use_graphs=use_graphs, record=record, notify=(wait == "event"))
     if warmup_s > 0:  # capture every graph and warm the lanes, untimed
         warm = poisson_stream(rate_hz, warmup_s, sizes, seed + 1)
-        serve(warm, plans, ex)
+        serve(warm, plans, ex, wait=wait)
         for p in plans:
             for b in range(1, p.max_batch + 1):
                 ex._graph(ex.lanes[p.name], b)
         torch.cuda.synchronize()
     reqs = poisson_stream(rate_hz, seconds, sizes, seed)
-    sch = serve(reqs, plans, ex)
+    sch = serve(reqs, plans, ex, wait=wait)
     summ = latency_summary(sch.done)
     summ.update({
         "rate_hz": rate_hz, "seconds": seconds, "iters": iters, "launches": sch.launches,
-        "lanes": [dataclasses.asdict(p) for p in plans], "graphs": ex.graph_ok,
+        "lanes": [dataclasses.asdict(p) for p in plans], "graphs": ex.graph_ok, "wait": wait, "share_sms": share_sms,
         "throughput_masks_per_s": len(sch.done) / max(max(r.finish for r in sch.done), 1e-9),
     })
     return summ, sch, ex
@@ -384,7 +472,11 @@ if __name__ == "__main__":
     ap.add_argument("--seconds", type=float, default=10.0)
     ap.add_argument("--iters", type=int, default=30)
     ap.add_argument("--no-graphs", action="store_true")
+    ap.add_argument("--wait", choices=["spin", "event"], default="spin")
+    ap.add_argument("--lanes", default="1,2", help="lanes per size (512, 1024)")
+    ap.add_argument("--split-sms", action="store_true", help="lanes on disjoint shares of the SMs")
     a = ap.parse_args()
-    s, _, ex = run_service(a.rate, a.seconds, iters=a.iters, use_graphs=not a.no_graphs)
+    s, _, ex = run_service(a.rate, a.seconds, iters=a.iters, use_graphs=not a.no_graphs, wait=a.wait,
+                           lanes=tuple(int(x) for x in a.lanes.split(",")), share_sms=not a.split_sms)
     ex.close()
     print(json.dumps(s))

@@ -107,3 +107,14 @@ def test_plan_lanes_with_equal_weights_gives_every_lane_the_same_share():
                           workspace_bytes=fake_workspace, max_batch_cap=16, weights=[1.0, 1.0])
     grids = [p.grid for p in plans]
     assert sum(grids) == 152 and max(grids) - min(grids) <= 1
+
+
+def test_plan_lanes_sharing_the_device():
+    """Time-shared lanes: every grid is the whole device, batches still from
+    the memory budget."""
+    plans = SV.plan_lanes([512, 1024], [1, 2], sm_count=152, budget_bytes=2 << 30, iters=30,
+                          workspace_bytes=fake_workspace, max_batch_cap=16, weights=[1.0, 1.0], share_sms=True)
+    assert [p.grid for p in plans] == [152, 152, 152]
+    split = SV.plan_lanes([512, 1024], [1, 2], sm_count=152, budget_bytes=2 << 30, iters=30,
+                          workspace_bytes=fake_workspace, max_batch_cap=16, weights=[1.0, 1.0])
+    assert [p.max_batch for p in plans] == [p.max_batch for p in split]
