@@ -488,7 +488,7 @@ def run_gpu(args):
     if args.serve_seconds > 0 and ws == 1:
         from paper_1302_0120_gb300 import serving as SV
 
-        def stream(rate, seconds, **kw):
+        def serve_stream(rate, seconds, **kw):
             summ, sch, ex = SV.run_service(rate_hz=rate, seconds=seconds, sizes=(512, 1024), lanes=(1, 2), iters=30,
                                            warmup_s=0.3, **kw)
             ex.close()
@@ -497,15 +497,15 @@ def run_gpu(args):
             out["lanes"] = [f"{p['name']} batch<={p['max_batch']} grid={p['grid']}" for p in summ["lanes"]]
             return out
 
-        serving = stream(args.serve_rate, args.serve_seconds)
+        serving = serve_stream(args.serve_rate, args.serve_seconds)
         half = max(1.0, args.serve_seconds / 2)
         # twice the rate; the same rate with a loop that sleeps between events;
         # the same rate on disjoint shares of the SMs
-        serving["at_2x_rate"] = {k: v for k, v in stream(2 * args.serve_rate, half).items()
+        serving["at_2x_rate"] = {k: v for k, v in serve_stream(2 * args.serve_rate, half).items()
                                  if k in ("requests", "p50_ms", "p99_ms", "max_ms", "rate_hz", "by_size")}
-        serving["event_driven"] = {k: v for k, v in stream(args.serve_rate, half, wait="event").items()
+        serving["event_driven"] = {k: v for k, v in serve_stream(args.serve_rate, half, wait="event").items()
                                    if k in ("requests", "p50_ms", "p99_ms", "max_ms", "rate_hz", "wait")}
-        serving["disjoint_sm_shares"] = {k: v for k, v in stream(args.serve_rate, half, share_sms=False).items()
+        serving["disjoint_sm_shares"] = {k: v for k, v in serve_stream(args.serve_rate, half, share_sms=False).items()
                                          if k in ("requests", "p50_ms", "p99_ms", "max_ms", "lanes")}
 
     def timed(fn, steps):
@@ -565,14 +565,17 @@ def run_gpu(args):
             if gst.status() != 0:
                 raise RuntimeError(f"tensor-core run failed ({name})")
             r_t = float(res_t["r"][-1].item())
-            tf = tc_flops / (ms_t * 1e-3) / 1e12
+            # BF16 operands are split into a rounded part and a remainder:
+            # three products per K step
+            flops_form = tc_flops * (3 if kw.get("bf16") else 1)
+            tf = flops_form / (ms_t * 1e-3) / 1e12
             tensor_core[name] = {
                 "ms_per_mask": round(ms_t, 4),
                 "achieved_gbs": round((BYTES_PER_PX_FIXED + BYTES_PER_PX_ITER * iters) * n / (ms_t * 1e6), 1),
                 "speedup_vs_fp32": round(mean_ms / ms_t, 4), "final_residual": r_t,
                 "final_residual_rel_diff_vs_fp32": round(abs(r_t - r_final) / r_final, 6),
                 "matched_within_2pct": abs(r_t - r_final) <= 0.02 * r_final,
-                "tensor_tflops": round(tf, 2), "tensor_peak_tflops": tc_peak[0],
+                "tensor_flops": flops_form, "tensor_tflops": round(tf, 2), "tensor_peak_tflops": tc_peak[0],
                 "tensor_frac": round(tf / tc_peak[0], 4), "tensor_peak_kind": tc_peak[1]}
             gst.close()
         # the headline of the form: the tcgen05 FP16 engine
