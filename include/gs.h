@@ -84,18 +84,21 @@ enum {
    * FP32 one by about 1e-3 (relative L2). The operands are kept in the FP16
    * range by a power-of-two scale per mask (inputs below 2^15 from the bound
    * sqrt(n sum p^2) of every transform input; the scale is undone in FP32),
-   * so any laser amplitude is accepted. On 1024 x 1024 grids the products run
-   * on the fifth-generation tensor cores (tcgen05: operands in shared memory,
-   * FP32 accumulators in tensor memory, each stage one M = 128 product over
-   * four lines); on 256 and 512 as warp-level mma.sync products. */
+   * so any laser amplitude is accepted. The products run on the
+   * fifth-generation tensor cores (tcgen05: operands in shared memory, FP32
+   * accumulators in tensor memory, each stage M = 128 products over the rows
+   * of four warps' lines). */
   GS_TENSOR_CORE = 4u,
-  /* With GS_TENSOR_CORE on a 1024 x 1024 grid (tcgen05): BF16 operands
-   * instead of FP16 (8 bits of significand instead of 11, FP32's range). Not
-   * accepted without GS_TENSOR_CORE, on other sizes or with GS_TC_MMA_SYNC. */
+  /* With GS_TENSOR_CORE: BF16 operands instead of FP16 (8 bits of
+   * significand instead of 11, FP32's range), each split into its BF16
+   * rounding and the rounding of the remainder, three products per K step,
+   * to keep the FP16 form's accuracy. Not accepted without GS_TENSOR_CORE or
+   * with GS_TC_MMA_SYNC. */
   GS_BF16 = 8u,
-  /* With GS_TENSOR_CORE on a 1024 x 1024 grid: run the products as
-   * warp-level mma.sync tiles (the form used at 256 and 512) instead of
-   * tcgen05, for comparison. Not accepted without GS_TENSOR_CORE. */
+  /* With GS_TENSOR_CORE: run the products as warp-level mma.sync tiles (FP16)
+   * instead of tcgen05, for comparison; batches of mixed sizes
+   * (gs_create_mixed) always use this form. Not accepted without
+   * GS_TENSOR_CORE. */
   GS_TC_MMA_SYNC = 16u
 };
 

@@ -321,9 +321,9 @@ int gs_create_batched(gs_ctx** out, int nx, int ny, int max_batch, unsigned flag
   const bool tc = (flags & GS_TENSOR_CORE) != 0;
   if (tc && !(nx == ny && is_pow2(nx) && nx >= 256 && nx <= 1024)) return GS_EINVAL;
   if ((flags & (GS_BF16 | GS_TC_MMA_SYNC)) != 0 && !tc) return GS_EINVAL;
-  // 1024 x 1024 runs its transforms through tcgen05 unless mma.sync is asked
-  // for; the other sizes use mma.sync, with FP16 operands only
-  const bool tc5 = tc && nx == 1024 && !(flags & GS_TC_MMA_SYNC);
+  // the transforms run through tcgen05 unless mma.sync is asked for (FP16
+  // operands only)
+  const bool tc5 = tc && !(flags & GS_TC_MMA_SYNC);
   if ((flags & GS_BF16) != 0 && !tc5) return GS_EINVAL;
   const int tc_mode = !tc ? gsk::kTcNone : !tc5 ? gsk::kTcMmaSync : (flags & GS_BF16) ? gsk::kTcGen05Bf16 : gsk::kTcGen05F16;
   gs_ctx* c = new (std::nothrow) gs_ctx();

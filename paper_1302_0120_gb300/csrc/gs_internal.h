@@ -17,11 +17,11 @@ constexpr int kTraceRows = 2 * kMaxIterPerLaunch + 4;
 // which is 256 * 33 complex whatever n is.
 constexpr int kGroupSmemBytes = kThreads * 33 * 8;
 // Extra shared memory of the tensor-core kernels: stage twiddles [32][32]
-// complex and a 32-entry cos/sin table (mma.sync); the DFT matrix (hi and lo
-// parts, 8 KiB each) and an 8 KiB twiddle table (tcgen05, whose operands
-// share the exchange buffers).
+// complex and a 32-entry cos/sin table (mma.sync); the two DFT matrices (hi
+// and lo parts, 8 KiB each) and an 8 KiB twiddle table (tcgen05, whose
+// operands share the exchange buffers).
 constexpr int kTcExtraSmemBytes = 32 * 32 * 8 + 32 * 8;
-constexpr int kTc5ExtraSmemBytes = 2 * 64 * 64 * 2 + 32 * 32 * 8;
+constexpr int kTc5ExtraSmemBytes = 4 * 64 * 64 * 2 + 32 * 32 * 8;
 
 struct Params {
   int nx, ny;          // grid, powers of two in [32, 4096]
@@ -56,8 +56,8 @@ struct Params {
   unsigned extra_arrivals;  // test hook: arrivals a barrier waits for beyond the grid (0 in use)
   float inv_sqrt_n;    // 1/sqrt(N)
   double inv_n;        // 1/N
-  int tensor_core;     // host side: transforms on the FP32 ALUs (0) or the tensor cores: mma.sync (1,
-                       // square 256, 512, 1024), tcgen05 with FP16 (2) or BF16 (3) operands (1024 x 1024)
+  int tensor_core;     // host side: transforms on the FP32 ALUs (0) or the tensor cores (square 256,
+                       // 512, 1024): mma.sync (1), tcgen05 with FP16 (2) or BF16 (3) operands
   unsigned long long* trace;  // [kTraceRows][grid][2] globaltimer stamps of block 0's thread 0 per block, or null
   int group;           // masks iterated together, 1..batch: the batch runs group after group
                        // through the whole schedule, so that a group's fields stay in L2
@@ -157,8 +157,9 @@ cudaError_t launch_iterations(const Params& p, int grid, cudaStream_t s);
 // sum p^2 of an SLM amplitude into *energy (NaN if p has a negative or non-finite value)
 cudaError_t launch_energy(const float* p, long long n, double* energy, cudaStream_t s);
 cudaError_t iteration_occupancy(int nx, int ny, int* blocks_per_sm, int tc_mode = kTcNone);
-// The tcgen05 kernel of 1024 x 1024 masks (gs_tc5_inst.cu); FP16 or BF16 operands.
-const void* iterate_kernel_tc5(bool bf16);
+// The tcgen05 kernel of n x n masks, log2(n) = l in 8..10 (gs_tc5_inst.cu);
+// FP16 or BF16 operands; null for other sizes.
+const void* iterate_kernel_tc5(int l, bool bf16);
 // Small grids (small_grid): allow the kernel its shared memory, and launch
 // one block per mask of p.batch (gs_small_inst.cu).
 cudaError_t small_prepare(int nx, int ny);

@@ -275,7 +275,9 @@ __device__ __forceinline__ float run_pass(const Params& p, int mb, int kind, boo
   constexpr int W = L::W;
   static_assert(N == L::NY, "column transforms have length ny");
   const bool gact = g < W;                                // this group owns a column
-  const bool wact = ((threadIdx.x & ~31) >> LOGT) < W;    // some group of this warp does
+  // some group of this warp owns a column (tcgen05: of this half of the
+  // block, whose warps issue their products together)
+  const bool wact = TCF::kTcgen05 ? ((((threadIdx.x >> 7) << 7) >> LOGT) < W) : (((threadIdx.x & ~31) >> LOGT) < W);
   const int gq = gact ? g : 0;                            // idle groups read a valid column
   for (int cb = lo; cb < hi; ++cb) {
     __syncthreads();  // the previous round is done with the staging buffers
@@ -684,13 +686,13 @@ __global__ void __launch_bounds__(kThreads, 1) gs_iterate(const Params p) {
   iterate_class<LX, LY, kHold>(p, sh, smem, tw_rows, tcf);
 }
 
-// The tensor-core form on tcgen05 (1024 x 1024 masks): the same schedule with
-// every 1024-point transform issued by the block's halves as products on the
+// The tensor-core form on tcgen05 (square 256, 512, 1024): the same schedule
+// with every transform issued by the block's halves as products on the
 // tensor cores (gs_tc5.cuh). Warp 0 holds the block's TMEM columns from the
 // start of the launch to its end, on every exit path.
 constexpr int kTc5Offset = kBlockSmemOffset + kBlockSmemBytes;  // after the amplitude and field blocks
 
-template <bool BF16>
+template <int L, bool BF16>
 __global__ void __launch_bounds__(kThreads, 1) gs_iterate_tc5(const Params p) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ Shared sh;
@@ -699,23 +701,23 @@ __global__ void __launch_bounds__(kThreads, 1) gs_iterate_tc5(const Params p) {
   if (*reinterpret_cast<volatile int*>(p.abort_flag) != 0) return;  // an earlier chunk failed
   static_assert(2 * kTc5HalfStride == kGroupSmemBytes, "the A operands fill the exchange area");
   unsigned char* abuf = smem;  // the exchange area (gs_tc5.cuh)
-  unsigned char* bmat = smem + kTc5Offset;
-  float2* tw = reinterpret_cast<float2*>(bmat + 2 * kTc5BBytes);
-  tc5_build_tables<BF16>(bmat, tw);
+  unsigned char* tabs = smem + kTc5Offset;
+  tc5_build_tables<L, BF16>(tabs);
   if (threadIdx.x == 0) {
     mbar_init(&tc_mbar[0], 1);
     mbar_init(&tc_mbar[1], 1);
     fence_barrier_init();
   }
   if ((threadIdx.x >> 5) == 0) tc5_alloc(&tc_tmem);
-  fence_proxy_async_smem();  // the DFT matrix is read by the tensor cores
+  fence_proxy_async_smem();  // the DFT matrices are read by the tensor cores
   tc5_fence_before();
   __syncthreads();
   tc5_fence_after();
   unsigned phase = 0;
-  const Tc5Fft<BF16> tcf{abuf, smem_u32(bmat), tw, tc_mbar, tc_tmem, &phase, &p};
-  const StageTw<10> none{};
-  iterate_class<10, 10, false>(p, sh, smem, none, tcf);
+  const Tc5Fft<L, BF16> tcf{abuf, smem_u32(tabs), reinterpret_cast<const float2*>(tabs + kTc5TwOffset),
+                            tc_mbar, tc_tmem, &phase, &p};
+  const StageTw<L> none{};
+  iterate_class<L, L, false>(p, sh, smem, none, tcf);
   tc5_fence_before();
   __syncthreads();
   if ((threadIdx.x >> 5) == 0) tc5_dealloc(tc_tmem);

@@ -52,7 +52,7 @@ static const void* kernel_for(int nx, int ny, int tc_mode) {
   if (uses_general(nx, ny)) return tc_mode != kTcNone ? nullptr : iterate_kernel_general();
   const int ly = log2_exact(ny);
   if (tc_mode == kTcGen05F16 || tc_mode == kTcGen05Bf16)
-    return (nx == 1024 && ny == 1024) ? iterate_kernel_tc5(tc_mode == kTcGen05Bf16) : nullptr;
+    return nx == ny ? iterate_kernel_tc5(ly, tc_mode == kTcGen05Bf16) : nullptr;
   if (tc_mode == kTcMmaSync) return nx == ny ? iterate_kernel_tc(ly) : nullptr;
   switch (log2_exact(nx)) {
     case 5: return iterate_kernel_lx<5>(ly);

@@ -1,34 +1,41 @@
-// gs_tc5.cuh -- the 1024-point DFT of the tensor-core form on the fifth-
-// generation tensor cores (tcgen05): FP16 or BF16 operands in shared memory,
-// FP32 accumulators in tensor memory (TMEM).
+// gs_tc5.cuh -- the DFTs of the tensor-core form on the fifth-generation
+// tensor cores (tcgen05): FP16 or BF16 operands in shared memory, FP32
+// accumulators in tensor memory (TMEM), for lines of n = 32 R points
+// (R = 8, 16, 32: the square grids 256, 512, 1024).
 //
-// Same arithmetic as gs_tc.cuh (the four-step factorisation 1024 = 32 x 32,
-// both stages dense products with the real form of the 32-point DFT matrix),
-// but batched: the four warps of one half of the block hold four lines (one
-// line per warp, lane t holding x[t + 32 i], i = 0..31, the thread layout of
-// the FP32 transforms), and each stage is ONE product of the half's 128 rows
-// (line, t) with the 64 x 64 real-form matrix, issued by one thread as four
-// tcgen05.mma (M = 128, N = 64, K = 16) into 64 TMEM columns:
+// Same arithmetic as gs_tc.cuh (the four-step factorisation n = 32 x R, both
+// stages dense products with the real forms of the 32-point and R-point DFT
+// matrices), but batched over the four warps of one half of the block. Lane
+// l = R gamma + t of a warp holds x_gamma[t + R i], i = 0..31, of line gamma
+// of the warp (32/R lines per warp: the thread layout of the FP32
+// transforms). Each stage is issued by one thread of the half:
 //
-//   stage 1  D1[(w, t)][k1]   = sum_i  x_w[t + 32 i] W_32^{i k1}        (A K-major: row (w, t) = [re x_i | im x_i])
-//   twiddle  Z[(w, k1)][t]    = D1[(w, t)][k1] W_1024^{k1 t} / 32       (epilogue of tcgen05.ld, FP32)
-//   stage 2  D2[(w, k1)][k2]  = sum_t  Z[(w, k1)][t] W_32^{t k2}         (A MN-major: column t = [re | im])
-//            X_w[k1 + 32 k2]  = 32 D2[(w, k1)][k2]
+//   stage 1  D1[(w, l)][k1] = sum_i x[t + R i] W_32^{i k1}          one M = 128 product, N = K = 64
+//            (A K-major: row (w, l) = [re x_i | im x_i])
+//   twiddle  Z[(gamma, k1)][t] = D1[(w, l)][k1] W_n^{k1 t} / 32      (epilogue of tcgen05.ld, FP32)
+//   stage 2  D2[(gamma, k1)][k2] = sum_t Z[(gamma, k1)][t] W_R^{t k2}   32/R products, M = 128, N = K = 2R
+//            (A MN-major: column t = [re | im])
+//            X_gamma[k1 + 32 k2] = 32 D2[(gamma, k1)][k2]
 //
-// Lane t of warp w reads TMEM lane 32 (w mod 4) + t, i.e. row (w, t) of D1 and
-// row (w, k1 = t) of D2, so the result X_w[t + 32 k2] lands in the thread
-// layout the transform started from. The two halves of the block run their
-// products independently (own mbarrier, own TMEM columns, own named
-// barrier), so one half's tensor-core latency overlaps the other's FP32
-// epilogue.
+// The rows of stage 2 are placed so that every lane reads back its own
+// outputs: row (gamma, k1) of warp w goes to tile c = k1 / R (its own
+// product, 2R TMEM columns) at TMEM lane 32 (w mod 4) + R gamma + (k1 mod R),
+// so lane R gamma + t finds rows (gamma, t + R c), i.e. X_gamma[t + R (c +
+// (32/R) k2)], in its own lane of every tile: the result lands in the thread
+// layout the transform started from, with no exchange. Stage 1 of every
+// length uses the same 64 TMEM columns per half as stage 2 ((32/R) tiles of
+// 2R columns), and four tcgen05.mma (K = 16 each) per half and stage. The two
+// halves of the block run their products independently (own mbarrier, own
+// TMEM columns, own named barrier), so one half's tensor-core latency can
+// overlap the other's FP32 epilogue.
 //
 // Shared-memory operands use the canonical no-swizzle layout: 8 x 16-byte
-// core matrices, 128 bytes each. K-major: core (m/8, k/8) at ((m/8) 8 +
+// core matrices, 128 bytes each. K-major: core (m/8, k/8) at ((m/8) (K/8) +
 // k/8) 128, row m mod 8 at 16 (m mod 8); the leading byte offset (next core
-// along K) is 128, the stride byte offset (next core along M or N) 1024.
-// MN-major: core (m/8, k/8) at ((k/8) 16 + m/8) 128, row k mod 8 at
-// 16 (k mod 8), m mod 8 at 2 (m mod 8); leading byte offset (along K) 2048,
-// stride byte offset (along M) 128.
+// along K) is 128, the stride byte offset (next core along M or N) (K/8) 128.
+// MN-major: core (m/8, k/8) at ((k/8) 16 + m/8) 128 within an M-tile of 128
+// rows, row k mod 8 at 16 (k mod 8), m mod 8 at 2 (m mod 8); leading byte
+// offset (along K) 2048, stride byte offset (along M) 128.
 //
 // Range: the caller passes a power-of-two input scale that keeps every FP16
 // operand below 2^15 (stage-1 inputs are bounded by sqrt(n sum p^2), stage-1
@@ -62,14 +69,17 @@
 namespace gsk {
 
 // Shared memory of the tcgen05 transform after the iteration kernel's own:
-// the real-form DFT matrix (hi, then lo: 8 KiB each) and the 8 KiB twiddle
-// table [k1][t]. The A operands live in the exchange area (kTc5HalfStride
-// bytes per half: A_hi 16 KiB, A_lo 16 KiB).
+// the real-form 32-point DFT matrix B1 (hi, then lo: 8 KiB each), the
+// real-form R-point matrix B2 (hi, then lo, 8 KiB each at most), and the
+// 8 KiB twiddle table [k1][lane]. The A operands live in the exchange area
+// (kTc5HalfStride bytes per half: A_hi 16 KiB, A_lo 16 KiB).
 constexpr int kTc5HalfStride = 4 * 32 * 33 * 8;  // the exchange buffers of four warps
 constexpr int kTc5AloOffset = 16384;
-constexpr int kTc5BBytes = 64 * 64 * 2;
+constexpr int kTc5BBytes = 64 * 64 * 2;          // one real-form matrix of the largest size, one part
+constexpr int kTc5B2Offset = 2 * kTc5BBytes;
+constexpr int kTc5TwOffset = 4 * kTc5BBytes;
 constexpr int kTc5TwBytes = 32 * 32 * 8;
-constexpr int kTc5SmemBytes = 2 * kTc5BBytes + kTc5TwBytes;
+constexpr int kTc5SmemBytes = 4 * kTc5BBytes + kTc5TwBytes;
 static_assert(kTc5SmemBytes == kTc5ExtraSmemBytes, "tcgen05 tables match the launch size");
 static_assert(2 * kTc5AloOffset <= kTc5HalfStride, "both A operands of a half fit its exchange buffers");
 constexpr int kTc5TmemCols = 128;  // two halves x 64 FP32 columns
@@ -80,10 +90,10 @@ __device__ __forceinline__ uint64_t tc5_desc(unsigned addr, unsigned lbo, unsign
 }
 
 // Instruction descriptor of kind::f16: FP32 accumulator, FP16 (0) or BF16 (1)
-// operands, A K-major (0) or MN-major (1), B K-major, N = 64, M = 128.
-__host__ __device__ constexpr unsigned tc5_idesc(bool bf16, bool a_mn) {
+// operands, A K-major (0) or MN-major (1), B K-major, N columns, M = 128.
+__host__ __device__ constexpr unsigned tc5_idesc(bool bf16, bool a_mn, unsigned n) {
   return (1u << 4) | ((bf16 ? 1u : 0u) << 7) | ((bf16 ? 1u : 0u) << 10) | ((a_mn ? 1u : 0u) << 15) |
-         ((64u >> 3) << 17) | ((128u >> 4) << 24);
+         ((n >> 3) << 17) | ((128u >> 4) << 24);
 }
 
 __device__ __forceinline__ void tc5_mma(unsigned d_tmem, uint64_t adesc, uint64_t bdesc, unsigned idesc,
@@ -143,33 +153,47 @@ __device__ __forceinline__ uint32_t tc5_pack(float lo, float hi) {
   return u;
 }
 
-// The block's constant tables: the real form of the 32-point DFT matrix as
-// the K-major B operand (row n, column K): n < 32 gives Re y_n, n >= 32 gives
-// Im y_{n-32}; K < 32 multiplies re x_K, K >= 32 im x_{K-32}:
-//   B[n][K] = cos, B[n][32+K] = sin, B[32+n][K] = -sin, B[32+n][32+K] = cos
-// of 2 pi n K / 32 (since W (a + i b) = (c a + s b) + i (c b - s a) for
-// W = c - i s); and the stage twiddles tw[k1][t] = W_1024^{k1 t} / 32.
-template <bool BF16>
-__device__ void tc5_build_tables(unsigned char* bmat, float2* tw) {
-  for (int e = threadIdx.x; e < 64 * 64; e += blockDim.x) {
-    const int n = e >> 6, K = e & 63;
-    const int kk = K & 31, nn = n & 31;
+// The real form of the P-point DFT matrix (P = 32 or R) as a K-major B
+// operand of 2P x 2P at dst (remainder at dst + kTc5BBytes for BF16): row n
+// < P gives Re y_n, n >= P gives Im y_{n-P}; column K < P multiplies re x_K,
+// K >= P im x_{K-P}:
+//   B[n][K] = cos, B[n][P+K] = sin, B[P+n][K] = -sin, B[P+n][P+K] = cos
+// of 2 pi n K / P (since W (a + i b) = (c a + s b) + i (c b - s a) for
+// W = c - i s).
+template <int P, bool BF16>
+__device__ void tc5_real_form(unsigned char* dst) {
+  constexpr int P2 = 2 * P;
+  for (int e = threadIdx.x; e < P2 * P2; e += blockDim.x) {
+    const int n = e / P2, K = e % P2;
+    const int kk = K % P, nn = n % P;
     float s, c;
-    sincospif(static_cast<float>((nn * kk) & 31) / 16.0f, &s, &c);
-    const float val = ((n < 32) == (K < 32)) ? c : (n < 32 ? s : -s);
-    const unsigned off = ((n >> 3) * 8 + (K >> 3)) * 128 + (n & 7) * 16 + (K & 7) * 2;
+    sincospif(2.0f * static_cast<float>((nn * kk) % P) / static_cast<float>(P), &s, &c);
+    const float val = ((n < P) == (K < P)) ? c : (n < P ? s : -s);
+    const unsigned off = ((n >> 3) * (P2 / 8) + (K >> 3)) * 128 + (n & 7) * 16 + (K & 7) * 2;
     if constexpr (BF16) {
       const __nv_bfloat16 hi = __float2bfloat16_rn(val);
-      *reinterpret_cast<__nv_bfloat16*>(bmat + off) = hi;
-      *reinterpret_cast<__nv_bfloat16*>(bmat + kTc5BBytes + off) = __float2bfloat16_rn(val - __bfloat162float(hi));
+      *reinterpret_cast<__nv_bfloat16*>(dst + off) = hi;
+      *reinterpret_cast<__nv_bfloat16*>(dst + kTc5BBytes + off) = __float2bfloat16_rn(val - __bfloat162float(hi));
     } else {
-      *reinterpret_cast<__half*>(bmat + off) = __float2half_rn(val);
+      *reinterpret_cast<__half*>(dst + off) = __float2half_rn(val);
     }
   }
+}
+
+// The block's constant tables for lines of n = 2^LOGN: B1 (32-point), B2
+// (R-point) and the stage twiddles tw[k1][lane] = W_n^{k1 t} / 32 with
+// t = lane mod R.
+template <int LOGN, bool BF16>
+__device__ void tc5_build_tables(unsigned char* tabs) {
+  constexpr int N = 1 << LOGN;
+  constexpr int R = N >> 5;
+  tc5_real_form<32, BF16>(tabs);
+  tc5_real_form<R, BF16>(tabs + kTc5B2Offset);
+  float2* tw = reinterpret_cast<float2*>(tabs + kTc5TwOffset);
   for (int e = threadIdx.x; e < 32 * 32; e += blockDim.x) {
-    const int k1 = e >> 5, t = e & 31;
+    const int k1 = e >> 5, t = (e & 31) & (R - 1);
     float s, c;
-    sincospif(static_cast<float>((k1 * t) & 1023) / 512.0f, &s, &c);
+    sincospif(2.0f * static_cast<float>((k1 * t) % N) / static_cast<float>(N), &s, &c);
     tw[e] = make_float2(c * (1.0f / 32.0f), -s * (1.0f / 32.0f));
   }
 }
@@ -210,13 +234,18 @@ __device__ __forceinline__ void tc5_pack8(const float (&x)[8], uint4& hi, uint4&
   lo = make_uint4(l[0], l[1], l[2], l[3]);
 }
 
-template <bool BF16>
+template <int LOGN, bool BF16>
 struct Tc5Fft {
   static constexpr bool kEnabled = true;
   static constexpr bool kTcgen05 = true;
+  static constexpr int N = 1 << LOGN;
+  static constexpr int R = N >> 5;   // stage-2 length
+  static constexpr int Q = 32 / R;   // lines per warp = stage-2 tiles per half
+  static constexpr int N2 = 2 * R;   // stage-2 N and K (real form)
+  static_assert(R == 8 || R == 16 || R == 32, "tcgen05 transforms have length 256, 512 or 1024");
   unsigned char* abuf;  // the exchange area: half h's A operands at h * kTc5HalfStride
-  unsigned bmat;        // shared-memory address of the real-form DFT matrix (BF16: hi, then lo)
-  const float2* tw;     // [k1][t] twiddles / 32
+  unsigned tabs;        // shared-memory address of the tables (tc5_build_tables)
+  const float2* tw;     // [k1][lane] twiddles / 32
   uint64_t* mbar;       // [2] completion of each half's products
   unsigned tmem;        // TMEM base of kTc5TmemCols columns
   unsigned* phase;      // this thread's parity of its half's mbarrier
@@ -235,33 +264,36 @@ struct Tc5Fft {
     return ok;
   }
 
-  // The transform. Every thread of the block must call it, with the same
-  // scales within each half; v holds x[t + 32 i] on entry, X[t + 32 i] on exit.
-  // The K-steps of one stage: A (hi, lo at +kTc5AloOffset) at a_addr with
-  // step `astep` and byte offsets (lbo, sbo); B (hi, lo at +kTc5BBytes).
+  // The K-steps of one product into d_tmem: A (hi, lo at +kTc5AloOffset) at
+  // a_addr with step `astep` and byte offsets (lbo, sbo); B (hi, lo at
+  // +kTc5BBytes) at b_addr, K-major with stride byte offset b_sbo.
+  template <int KSTEPS>
   __device__ __forceinline__ void issue(unsigned d_tmem, unsigned a_addr, unsigned astep, unsigned lbo, unsigned sbo,
-                                        unsigned idesc) const {
+                                        unsigned b_addr, unsigned b_sbo, unsigned idesc) const {
 #pragma unroll
-    for (int s = 0; s < 4; ++s) {
+    for (int s = 0; s < KSTEPS; ++s) {
       const uint64_t ah = tc5_desc(a_addr + astep * s, lbo, sbo);
-      const uint64_t bh = tc5_desc(bmat + 256u * s, 128u, 1024u);
+      const uint64_t bh = tc5_desc(b_addr + 256u * s, 128u, b_sbo);
       tc5_mma(d_tmem, ah, bh, idesc, s > 0 ? 1u : 0u);
       if constexpr (BF16) {
-        tc5_mma(d_tmem, ah, tc5_desc(bmat + kTc5BBytes + 256u * s, 128u, 1024u), idesc, 1u);
+        tc5_mma(d_tmem, ah, tc5_desc(b_addr + kTc5BBytes + 256u * s, 128u, b_sbo), idesc, 1u);
         tc5_mma(d_tmem, tc5_desc(a_addr + kTc5AloOffset + astep * s, lbo, sbo), bh, idesc, 1u);
       }
     }
   }
 
+  // The transform. Every thread of the half must call it, with the same
+  // scales; v holds x[t + R i] on entry, X[t + R i] on exit (lane R gamma + t).
   __device__ __forceinline__ void run(float2 (&v)[32], float in_scale, float out_scale) const {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int half = warp >> 2, wq = warp & 3;
+    const int gam = lane / R, t = lane & (R - 1);
     unsigned char* A = abuf + half * kTc5HalfStride;
     const unsigned a_addr = smem_u32(A);
     const unsigned d_tmem = tmem + 64u * half;
     const unsigned t_addr = d_tmem + (static_cast<unsigned>(32 * wq) << 16);
     const bool leader = (wq == 0) && (lane == 0);
-    const int r = 32 * wq + lane;  // this thread's row of the half's product
+    const int r = 32 * wq + lane;  // this thread's row of the half's stage-1 product
     // the operands overwrite the half's exchange buffers: every warp of the
     // half is done with its own first
     asm volatile("bar.sync %0, 128;" ::"r"(1 + half) : "memory");
@@ -291,12 +323,12 @@ struct Tc5Fft {
     asm volatile("bar.sync %0, 128;" ::"r"(1 + half) : "memory");
     if (leader) {
       tc5_fence_after();
-      issue(d_tmem, a_addr, 256u, 128u, 1024u, tc5_idesc(BF16, false));
+      issue<4>(d_tmem, a_addr, 256u, 128u, 1024u, tabs, 1024u, tc5_idesc(BF16, false, 64u));
       tc5_commit(&mbar[half]);
     }
     wait(half);
     tc5_fence_after();
-    // stage-1 result row (w, t): columns 0..31 re D1[k1], 32..63 im D1[k1]
+    // stage-1 result row (w, lane): columns 0..31 re D1[k1], 32..63 im D1[k1]
     float d[64];
     {
       float q[16];
@@ -308,8 +340,9 @@ struct Tc5Fft {
       }
       tc5_wait_ld();
     }
-    // twiddle and the stage-2 operand, MN-major: K = t (re) and 32 + t (im),
-    // M = 32 wq + k1; eight consecutive k1 make one 16-byte row of a core.
+    // twiddle and the stage-2 operand, MN-major: K = t (re) and R + t (im);
+    // row (gamma, k1) in tile c = k1 / R at M = 32 wq + R gamma + (k1 mod R),
+    // so eight consecutive k1 make one 16-byte row of a core
     const float2* twl = tw + lane;
 #pragma unroll
     for (int g = 0; g < 4; ++g) {
@@ -322,12 +355,14 @@ struct Tc5Fft {
         zr[j] = a * w.x - b * w.y;
         zi[j] = a * w.y + b * w.x;
       }
-      const int mi = 4 * wq + g;
+      const int c = (8 * g) / R;
+      const int m = 32 * wq + R * gam + (8 * g) % R;
       uint4 hr, lr, hi_, li;
       tc5_pack8<BF16>(zr, hr, lr);
       tc5_pack8<BF16>(zi, hi_, li);
-      const int o_re = ((lane >> 3) * 16 + mi) * 128 + (lane & 7) * 16;
-      const int o_im = ((4 + (lane >> 3)) * 16 + mi) * 128 + (lane & 7) * 16;
+      const int tile = c * R * 512;  // (2R/8) k-cores of 16 m-cores of 128 bytes
+      const int o_re = tile + ((t >> 3) * 16 + (m >> 3)) * 128 + (t & 7) * 16;
+      const int o_im = tile + (((R + t) >> 3) * 16 + (m >> 3)) * 128 + ((R + t) & 7) * 16;
       *reinterpret_cast<uint4*>(A + o_re) = hr;
       *reinterpret_cast<uint4*>(A + o_im) = hi_;
       if constexpr (BF16) {
@@ -340,7 +375,10 @@ struct Tc5Fft {
     asm volatile("bar.sync %0, 128;" ::"r"(1 + half) : "memory");
     if (leader) {
       tc5_fence_after();
-      issue(d_tmem, a_addr, 4096u, 2048u, 128u, tc5_idesc(BF16, true));
+#pragma unroll
+      for (int c = 0; c < Q; ++c)
+        issue<N2 / 16>(d_tmem + static_cast<unsigned>(c * N2), a_addr + c * R * 512, 4096u, 2048u, 128u,
+                       tabs + kTc5B2Offset, (N2 / 8) * 128u, tc5_idesc(BF16, true, N2));
       tc5_commit(&mbar[half]);
     }
     wait(half);
@@ -348,15 +386,22 @@ struct Tc5Fft {
     {
       float q[16];
 #pragma unroll
-      for (int b = 0; b < 4; ++b) {
-        tc5_ld16(q, t_addr + 16u * b);
+      for (int c = 0; c < Q; ++c) {
 #pragma unroll
-        for (int j = 0; j < 16; ++j) d[16 * b + j] = q[j];
+        for (int b = 0; b < N2 / 16; ++b) {
+          tc5_ld16(q, t_addr + static_cast<unsigned>(c * N2 + 16 * b));
+#pragma unroll
+          for (int j = 0; j < 16; ++j) d[c * N2 + 16 * b + j] = q[j];
+        }
       }
       tc5_wait_ld();
     }
+    // tile c holds re X[t + R (c + Q k2)] in columns k2 < R, im in R + k2
 #pragma unroll
-    for (int k2 = 0; k2 < 32; ++k2) v[k2] = make_float2(d[k2] * out_scale, d[32 + k2] * out_scale);
+    for (int c = 0; c < Q; ++c)
+#pragma unroll
+      for (int k2 = 0; k2 < R; ++k2)
+        v[c + Q * k2] = make_float2(d[c * N2 + k2] * out_scale, d[c * N2 + R + k2] * out_scale);
   }
 };
 

@@ -24,8 +24,8 @@ FINAL_TOL = 0.02
 CHAIN_SLACK = 5e-3
 
 
-# Engines of the tensor-core form: at 1024 x 1024, tcgen05 with FP16 or BF16
-# operands and the warp-level mma.sync products; at 256 and 512, mma.sync.
+# Engines of the tensor-core form: tcgen05 with FP16 or BF16 operands, and
+# the warp-level mma.sync products.
 ENGINES = {"tcgen05-f16": {}, "tcgen05-bf16": {"bf16": True}, "mma-sync": {"mma_sync": True}}
 
 
@@ -36,7 +36,7 @@ def tc_run(I, phi0, iters, p=None, engine="tcgen05-f16"):
 
     build_lib.build()
     ny, nx = I.shape
-    kw = ENGINES[engine] if nx == 1024 else {}
+    kw = ENGINES[engine]
     with GerchbergSaxton(nx, ny, tensor_core=True, **kw) as gs:
         pt = None
         if p is not None:
@@ -55,8 +55,7 @@ def check_chain(r, g):
     assert np.all(r[1:] <= g * (1 + CHAIN_SLACK)), np.max(r[1:] / g)
 
 
-CASES = [(256, 20, "mma-sync"), (512, 40, "mma-sync"), (1024, 50, "tcgen05-f16"), (1024, 50, "tcgen05-bf16"),
-         (1024, 50, "mma-sync")]
+CASES = [(n, s, e) for n, s in ((256, 20), (512, 40), (1024, 50)) for e in ("tcgen05-f16", "tcgen05-bf16", "mma-sync")]
 
 
 @pytest.mark.parametrize("n,nspots,engine", CASES)
@@ -85,7 +84,7 @@ def test_one_step(n, nspots, engine):
     assert abs(r[0] - r_ref) <= STEP_TOL * r_ref and abs(g[0] - g_ref) <= STEP_TOL * g_ref
 
 
-@pytest.mark.parametrize("n", [512, 1024])
+@pytest.mark.parametrize("n", [256, 512, 1024])
 def test_batch_matches_single_runs(n):
     """Each mask of a batched launch has the single-mask run's phase, bit for
     bit, and its gaps to FP64 rounding (at 1024: tcgen05, whose products mix
@@ -155,8 +154,7 @@ def test_laser_amplitude():
     check_chain(r, g)
 
 
-@pytest.mark.parametrize("n,engine", [(256, "mma-sync"), (512, "mma-sync"), (1024, "tcgen05-f16"),
-                                      (1024, "tcgen05-bf16"), (1024, "mma-sync")])
+@pytest.mark.parametrize("n,engine", [(n, e) for n in (256, 512, 1024) for e in ("tcgen05-f16", "tcgen05-bf16", "mma-sync")])
 def test_large_laser_amplitude_is_rescaled(n, engine):
     """p = 100 everywhere: n sum p^2 = n^3 1e4 puts the raw transform inputs far
     beyond the FP16 range (65504); the per-mask power-of-two scale keeps the
