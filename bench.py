@@ -677,8 +677,12 @@ def run_gpu(args):
         mixed64 = {"masks": len(masks), "iters": 50, "launches_per_run": 1,
                    "sizes": {str(k_): len(v_) for k_, v_ in sorted(groups.items())}}
         rfin = {}
-        for tc in (False, True):
-            gm = MixedGerchbergSaxton({n_: len(ks) for n_, ks in groups.items()}, stream=stream, tensor_core=tc)
+        # FP32; the tensor-core form on tcgen05 (FP16, the default engine) and
+        # as warp-level mma.sync products
+        forms = (("fp32", {}), ("tensor_core", {"tensor_core": True}),
+                 ("mma_sync", {"tensor_core": True, "mma_sync": True}))
+        for name, kw in forms:
+            gm = MixedGerchbergSaxton({n_: len(ks) for n_, ks in groups.items()}, stream=stream, **kw)
             keep = {}
 
             def mixed_step():
@@ -686,19 +690,20 @@ def run_gpu(args):
 
             ms_m = timed(mixed_step, args.mixed_steps)
             if gm.status() != 0:
-                raise RuntimeError("mixed batch failed")
+                raise RuntimeError(f"mixed batch failed ({name})")
             for n_, ks in groups.items():
                 rr = keep["out"][n_][1].cpu().numpy()
                 for j, k in enumerate(ks):
-                    rfin[(tc, k)] = float(rr[j][-1])
+                    rfin[(name, k)] = float(rr[j][-1])
             mixed64["grid_ctas"] = gm.grid
             gm.close()
-            mixed64["tensor_core_ms" if tc else "fp32_ms"] = round(ms_m, 4)
+            mixed64[f"{name}_ms"] = round(ms_m, 4)
             mbytes = sum((BYTES_PER_PX_FIXED + BYTES_PER_PX_ITER * 50) * n_ * n_ * len(ks) for n_, ks in groups.items())
-            mixed64["tensor_core_achieved_gbs" if tc else "fp32_achieved_gbs"] = round(mbytes / (ms_m * 1e6), 1)
-            mixed64["tensor_core_ms_per_mask" if tc else "fp32_ms_per_mask"] = round(ms_m / len(masks), 4)
+            mixed64[f"{name}_achieved_gbs"] = round(mbytes / (ms_m * 1e6), 1)
+            mixed64[f"{name}_ms_per_mask"] = round(ms_m / len(masks), 4)
+        mixed64["tensor_core_engine"] = "tcgen05, FP16 operands"
         mixed64["worst_final_residual_rel_diff_tc_vs_fp32"] = round(
-            max(abs(rfin[(True, k)] - rfin[(False, k)]) / rfin[(False, k)] for k in range(len(masks))), 6)
+            max(abs(rfin[("tensor_core", k)] - rfin[("fp32", k)]) / rfin[("fp32", k)] for k in range(len(masks))), 6)
 
     # end to end through the public host-pointer call (gs_run_host)
     pin_I = torch.from_numpy(I_np).pin_memory()

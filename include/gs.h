@@ -96,9 +96,8 @@ enum {
    * with GS_TC_MMA_SYNC. */
   GS_BF16 = 8u,
   /* With GS_TENSOR_CORE: run the products as warp-level mma.sync tiles (FP16)
-   * instead of tcgen05, for comparison; batches of mixed sizes
-   * (gs_create_mixed) always use this form. Not accepted without
-   * GS_TENSOR_CORE. */
+   * instead of tcgen05, for comparison. Not accepted without GS_TENSOR_CORE
+   * or with GS_BF16. */
   GS_TC_MMA_SYNC = 16u
 };
 
@@ -192,7 +191,8 @@ int gs_run_batched(gs_ctx* c, int batch, const float* target_intensity, const fl
  * Eq. (e:AP) on every mask of every size in one persistent launch.
  *   out        host pointer that receives the context (NULL on failure).
  *   max_batch  host int[3]: masks of size 256 << k, each 0..64, sum 1..64.
- *   flags      GS_FINAL_RESIDUAL, GS_INIT_FROM_TARGET, GS_TENSOR_CORE.
+ *   flags      GS_FINAL_RESIDUAL, GS_INIT_FROM_TARGET, GS_TENSOR_CORE (tcgen05
+ *              products at every size), GS_BF16, GS_TC_MMA_SYNC.
  *   stream     a cudaStream_t, or NULL for the legacy default stream.
  * Only gs_run_mixed, gs_status, gs_set_grid, gs_get_grid and gs_destroy
  * accept a mixed context; the single-size calls return GS_EINVAL.

@@ -470,11 +470,19 @@ int gs_create_mixed(gs_ctx** out, const int* max_batch, unsigned flags, void* st
     total += max_batch[k];
   }
   if (total < 1 || total > gsk::kMaxBatch) return GS_EINVAL;
-  if ((flags & ~static_cast<unsigned>(GS_FINAL_RESIDUAL | GS_INIT_FROM_TARGET | GS_TENSOR_CORE)) != 0)
+  if ((flags & ~static_cast<unsigned>(GS_FINAL_RESIDUAL | GS_INIT_FROM_TARGET | GS_TENSOR_CORE | GS_BF16 |
+                                      GS_TC_MMA_SYNC)) != 0)
     return GS_EINVAL;
   const bool tc = (flags & GS_TENSOR_CORE) != 0;
+  if ((flags & (GS_BF16 | GS_TC_MMA_SYNC)) != 0 && !tc) return GS_EINVAL;
+  if ((flags & GS_BF16) != 0 && (flags & GS_TC_MMA_SYNC) != 0) return GS_EINVAL;
+  const int tc_mode = !tc ? gsk::kTcNone
+                      : (flags & GS_TC_MMA_SYNC) ? gsk::kTcMmaSync
+                      : (flags & GS_BF16) ? gsk::kTcGen05Bf16
+                                          : gsk::kTcGen05F16;
   gs_ctx* c = new (std::nothrow) gs_ctx();
   if (c == nullptr) return GS_ENOMEM;
+  c->tc_mode = tc_mode;
   c->mixed = true;
   c->flags = flags;
   c->stream = static_cast<cudaStream_t>(stream);
@@ -494,7 +502,7 @@ int gs_create_mixed(gs_ctx** out, const int* max_batch, unsigned flags, void* st
   c->max_batch = total;
   if (cudaGetDevice(&c->device) != cudaSuccess ||
       cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess ||
-      gsk::mixed_occupancy(tc, &c->blocks_per_sm) != cudaSuccess || c->blocks_per_sm < 1) {
+      gsk::mixed_occupancy(tc_mode, &c->blocks_per_sm) != cudaSuccess || c->blocks_per_sm < 1) {
     cudaGetLastError();
     delete c;
     return GS_ECUDA;
@@ -561,7 +569,7 @@ int gs_run_mixed(gs_ctx* c, const int* batch, const float* const* target_intensi
     p.final_resid = (c->flags & GS_FINAL_RESIDUAL) ? 1 : 0;
     p.init_target = from_target ? 1 : 0;
     p.extra_arrivals = c->extra_arrivals;
-    p.tensor_core = (c->flags & GS_TENSOR_CORE) ? 1 : 0;
+    p.tensor_core = c->tc_mode;
     p.group = group_size(c, static_cast<long long>(n) * n, batch[k] > 0 ? batch[k] : 1);
     p.inv_sqrt_n = static_cast<float>(1.0 / n);
     p.inv_n = 1.0 / (static_cast<double>(n) * n);
@@ -601,7 +609,7 @@ int gs_run_mixed(gs_ctx* c, const int* batch, const float* const* target_intensi
       mp.cls[k].do_final = (it1 == iters) ? 1 : 0;
     }
     if (cudaMemsetAsync(mp.cls[0].bar, 0, sizeof(unsigned), c->stream) != cudaSuccess ||
-        gsk::launch_mixed(mp, grid, (c->flags & GS_TENSOR_CORE) != 0, c->stream) != cudaSuccess) {
+        gsk::launch_mixed(mp, grid, c->tc_mode, c->stream) != cudaSuccess) {
       cudaGetLastError();
       return GS_ECUDA;
     }

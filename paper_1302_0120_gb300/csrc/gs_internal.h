@@ -22,6 +22,9 @@ constexpr int kGroupSmemBytes = kThreads * 33 * 8;
 // operands share the exchange buffers).
 constexpr int kTcExtraSmemBytes = 32 * 32 * 8 + 32 * 8;
 constexpr int kTc5ExtraSmemBytes = 4 * 64 * 64 * 2 + 32 * 32 * 8;
+// The mixed launch on tcgen05: the 32-point matrix (hi, lo), the 8-, 16- and
+// 32-point matrices (hi, lo) and three twiddle tables.
+constexpr int kMixedTc5ExtraSmemBytes = 2 * 64 * 64 * 2 + 2 * (16 * 16 + 32 * 32 + 64 * 64) * 2 + 3 * 32 * 32 * 8;
 
 struct Params {
   int nx, ny;          // grid, powers of two in [32, 4096]
@@ -118,11 +121,12 @@ const void* iterate_kernel_lx(int ly);
 const void* iterate_kernel_tc(int l);
 // Kernel for grids with a side that is not a power of two (gs_general_inst.cu).
 const void* iterate_kernel_general();
-// Kernel for three square size classes in one launch (gs_mixed_inst.cu).
-const void* iterate_kernel_mixed(bool tc);
-size_t mixed_smem_bytes(bool tensor_core);
-cudaError_t mixed_occupancy(bool tensor_core, int* blocks_per_sm);
-cudaError_t launch_mixed(const MixedParams& mp, int grid, bool tensor_core, cudaStream_t s);
+// Kernel for three square size classes in one launch (gs_mixed_inst.cu), by
+// TcMode.
+const void* iterate_kernel_mixed(int tc_mode);
+size_t mixed_smem_bytes(int tc_mode);
+cudaError_t mixed_occupancy(int tc_mode, int* blocks_per_sm);
+cudaError_t launch_mixed(const MixedParams& mp, int grid, int tc_mode, cudaStream_t s);
 
 // Tensor-core modes of Params::tensor_core.
 enum TcMode { kTcNone = 0, kTcMmaSync = 1, kTcGen05F16 = 2, kTcGen05Bf16 = 3 };

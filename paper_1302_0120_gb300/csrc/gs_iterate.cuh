@@ -702,7 +702,7 @@ __global__ void __launch_bounds__(kThreads, 1) gs_iterate_tc5(const Params p) {
   static_assert(2 * kTc5HalfStride == kGroupSmemBytes, "the A operands fill the exchange area");
   unsigned char* abuf = smem;  // the exchange area (gs_tc5.cuh)
   unsigned char* tabs = smem + kTc5Offset;
-  tc5_build_tables<L, BF16>(tabs);
+  tc5_build_tables<L, BF16>(tabs, tabs + kTc5B2Offset, reinterpret_cast<float2*>(tabs + kTc5TwOffset));
   if (threadIdx.x == 0) {
     mbar_init(&tc_mbar[0], 1);
     mbar_init(&tc_mbar[1], 1);
@@ -714,8 +714,8 @@ __global__ void __launch_bounds__(kThreads, 1) gs_iterate_tc5(const Params p) {
   __syncthreads();
   tc5_fence_after();
   unsigned phase = 0;
-  const Tc5Fft<L, BF16> tcf{abuf, smem_u32(tabs), reinterpret_cast<const float2*>(tabs + kTc5TwOffset),
-                            tc_mbar, tc_tmem, &phase, &p};
+  const Tc5Fft<L, BF16> tcf{abuf, smem_u32(tabs), smem_u32(tabs + kTc5B2Offset),
+                            reinterpret_cast<const float2*>(tabs + kTc5TwOffset), tc_mbar, tc_tmem, &phase, &p};
   const StageTw<L> none{};
   iterate_class<L, L, false>(p, sh, smem, none, tcf);
   tc5_fence_before();
@@ -739,28 +739,16 @@ __device__ __forceinline__ void mixed_class_pass(const MixedParams& mp, Shared& 
   }
 }
 
-template <bool TC>
-__global__ void __launch_bounds__(kThreads, 1) gs_iterate_mixed(const MixedParams mp) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ Shared sh;
+// The schedule of a mixed launch (the tcgen05 form; gs_iterate_mixed writes
+// the same out): A0 for every class, then the classes one after the other,
+// each (in mask groups) through the whole schedule of passes;
+// `pass(c, w0, w1, f, mphase)` runs one pass of class c. Returns early when a
+// barrier gave up or every mask was rejected.
+template <class PassFn>
+__device__ __forceinline__ void iterate_mixed(const MixedParams& mp, Shared& sh, unsigned char* smem, PassFn&& pass) {
   const Params& p0 = mp.cls[0];  // barrier, status, abort flag, schedule
-  if (*reinterpret_cast<volatile int*>(p0.abort_flag) != 0) return;
   unsigned target = 0;
   unsigned mphase = 0;
-  TcStage1 s1;
-  TcStage2<8> s2a;
-  TcStage2<16> s2b;
-  TcStage2<32> s2c;
-  if constexpr (TC) {
-    float2* cs = reinterpret_cast<float2*>(smem + kTcTwOffset + 3 * kTcTwBytes);
-    tc_build_tables<8>(reinterpret_cast<float2*>(smem + kTcTwOffset), cs);
-    tc_build_tables<9>(reinterpret_cast<float2*>(smem + kTcTwOffset + kTcTwBytes), cs);
-    tc_build_tables<10>(reinterpret_cast<float2*>(smem + kTcTwOffset + 2 * kTcTwBytes), cs);
-    __syncthreads();
-    s1.load(cs);
-    s2a.load(cs);
-    s2b.load(cs);
-  }
   block_setup(sh);
   const int total = mp.cls[0].batch + mp.cls[1].batch + mp.cls[2].batch;
   const int base1 = mp.cls[0].batch, base2 = base1 + mp.cls[1].batch;
@@ -792,6 +780,70 @@ __global__ void __launch_bounds__(kThreads, 1) gs_iterate_mixed(const MixedParam
     for (int w0 = 0; w0 < pc.batch; w0 += gsz) {
       const int w1 = min(pc.batch, w0 + gsz);
       for (int q0 = 0; q0 < npass; ++q0) {
+        pass(c, w0, w1, pass_info(p0, q0), mphase);
+        if (!grid_sync(p0, target, sh)) {
+          drain_copies(sh);
+          return;
+        }
+      }
+    }
+  }
+  final_gaps(mp.cls[0], sh, 0);
+  final_gaps(mp.cls[1], sh, base1);
+  final_gaps(mp.cls[2], sh, base2);
+}
+
+template <bool TC>
+__global__ void __launch_bounds__(kThreads, 1) gs_iterate_mixed(const MixedParams mp) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ Shared sh;
+  if (*reinterpret_cast<volatile int*>(mp.cls[0].abort_flag) != 0) return;
+  TcStage1 s1;
+  TcStage2<8> s2a;
+  TcStage2<16> s2b;
+  TcStage2<32> s2c;
+  if constexpr (TC) {
+    float2* cs = reinterpret_cast<float2*>(smem + kTcTwOffset + 3 * kTcTwBytes);
+    tc_build_tables<8>(reinterpret_cast<float2*>(smem + kTcTwOffset), cs);
+    tc_build_tables<9>(reinterpret_cast<float2*>(smem + kTcTwOffset + kTcTwBytes), cs);
+    tc_build_tables<10>(reinterpret_cast<float2*>(smem + kTcTwOffset + 2 * kTcTwBytes), cs);
+    __syncthreads();
+    s1.load(cs);
+    s2a.load(cs);
+    s2b.load(cs);
+  }
+  // The schedule of iterate_mixed, written out: passing the register-held
+  // DFT fragments through a closure moved them to local memory.
+  const Params& p0 = mp.cls[0];
+  unsigned target = 0;
+  unsigned mphase = 0;
+  block_setup(sh);
+  const int total = mp.cls[0].batch + mp.cls[1].batch + mp.cls[2].batch;
+  const int base1 = mp.cls[0].batch, base2 = base1 + mp.cls[1].batch;
+  if (p0.do_init) {
+    for (int c = 0; c < 3; ++c) a0_partials(mp.cls[c], sh);
+    if (!grid_sync(p0, target, sh)) return;
+    const int nbad = a0_scales(mp.cls[0], sh, 0) + a0_scales(mp.cls[1], sh, base1) + a0_scales(mp.cls[2], sh, base2);
+    if (nbad == total) {
+      if (blockIdx.x == 0 && threadIdx.x == 0) atomicExch(p0.abort_flag, 1);
+      return;
+    }
+    build_amplitudes<8>(mp.cls[0], sh, 0, smem);
+    build_amplitudes<9>(mp.cls[1], sh, base1, smem);
+    build_amplitudes<10>(mp.cls[2], sh, base2, smem);
+  } else {
+    restore_flags(mp.cls[0], sh, 0);
+    restore_flags(mp.cls[1], sh, base1);
+    restore_flags(mp.cls[2], sh, base2);
+  }
+  __syncthreads();
+  const int npass = pass_count(p0);
+  for (int c = 0; c < 3; ++c) {
+    const Params& pc = mp.cls[c];
+    const int gsz = pc.group > 0 ? pc.group : pc.batch;
+    for (int w0 = 0; w0 < pc.batch; w0 += gsz) {
+      const int w1 = min(pc.batch, w0 + gsz);
+      for (int q0 = 0; q0 < npass; ++q0) {
         const PassInfo f = pass_info(p0, q0);
         if (c == 0) mixed_class_pass<0, TC>(mp, sh, w0, w1, f, smem, mphase, s1, s2a);
         else if (c == 1) mixed_class_pass<1, TC>(mp, sh, w0, w1, f, smem, mphase, s1, s2b);
@@ -806,6 +858,66 @@ __global__ void __launch_bounds__(kThreads, 1) gs_iterate_mixed(const MixedParam
   final_gaps(mp.cls[0], sh, 0);
   final_gaps(mp.cls[1], sh, base1);
   final_gaps(mp.cls[2], sh, base2);
+}
+
+// The mixed launch with tcgen05 transforms: one TMEM allocation for the
+// launch, the 32-point matrix shared by the three lengths, an R-point matrix
+// and a twiddle table per length (kMixedTc5SmemBytes after the kernel's own
+// shared memory).
+// offset of the R-point matrix of class c (R = 8 << c) in the tables
+__host__ __device__ constexpr int mixed_b2_offset(int c) {
+  return 2 * tc5_form_bytes(32) + (c > 0 ? 2 * tc5_form_bytes(8) : 0) + (c > 1 ? 2 * tc5_form_bytes(16) : 0);
+}
+constexpr int kMixedTwOffset = 4 * tc5_form_bytes(32) + 2 * tc5_form_bytes(8) + 2 * tc5_form_bytes(16);
+static_assert(kMixedTwOffset + 3 * kTc5TwBytes == kMixedTc5ExtraSmemBytes, "mixed tcgen05 tables match the launch size");
+
+template <int C, bool BF16>
+__device__ __forceinline__ void mixed_class_pass_tc5(const MixedParams& mp, Shared& sh, int w0, int w1,
+                                                     const PassInfo& f, unsigned char* smem, unsigned& mphase,
+                                                     const Tc5Fft<8 + C, BF16>& tcf) {
+  constexpr int L = 8 + C;
+  const int base = (C > 0 ? mp.cls[0].batch : 0) + (C > 1 ? mp.cls[1].batch : 0);
+  const StageTw<L> none{};
+  class_pass<L, L, false>(mp.cls[C], sh, base, w0, w1, f, smem, mphase, none, tcf);
+}
+
+template <bool BF16>
+__global__ void __launch_bounds__(kThreads, 1) gs_iterate_mixed_tc5(const MixedParams mp) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ Shared sh;
+  __shared__ uint64_t tc_mbar[2];
+  __shared__ unsigned tc_tmem;
+  const Params& p0 = mp.cls[0];
+  if (*reinterpret_cast<volatile int*>(p0.abort_flag) != 0) return;
+  static_assert(2 * kTc5HalfStride == kGroupSmemBytes, "the A operands fill the exchange area");
+  unsigned char* tabs = smem + kTc5Offset;
+  float2* tw = reinterpret_cast<float2*>(tabs + kMixedTwOffset);
+  tc5_build_tables<8, BF16>(tabs, tabs + mixed_b2_offset(0), tw);
+  tc5_build_tables<9, BF16>(nullptr, tabs + mixed_b2_offset(1), tw + 1024);
+  tc5_build_tables<10, BF16>(nullptr, tabs + mixed_b2_offset(2), tw + 2048);
+  if (threadIdx.x == 0) {
+    mbar_init(&tc_mbar[0], 1);
+    mbar_init(&tc_mbar[1], 1);
+    fence_barrier_init();
+  }
+  if ((threadIdx.x >> 5) == 0) tc5_alloc(&tc_tmem);
+  fence_proxy_async_smem();  // the DFT matrices are read by the tensor cores
+  tc5_fence_before();
+  __syncthreads();
+  tc5_fence_after();
+  unsigned phase = 0;  // one parity per half, shared by the three lengths (their products run in turn)
+  const unsigned b1 = smem_u32(tabs);
+  const Tc5Fft<8, BF16> t8{smem, b1, smem_u32(tabs + mixed_b2_offset(0)), tw, tc_mbar, tc_tmem, &phase, &p0};
+  const Tc5Fft<9, BF16> t9{smem, b1, smem_u32(tabs + mixed_b2_offset(1)), tw + 1024, tc_mbar, tc_tmem, &phase, &p0};
+  const Tc5Fft<10, BF16> t10{smem, b1, smem_u32(tabs + mixed_b2_offset(2)), tw + 2048, tc_mbar, tc_tmem, &phase, &p0};
+  iterate_mixed(mp, sh, smem, [&](int c, int w0, int w1, const PassInfo& f, unsigned& mphase) {
+    if (c == 0) mixed_class_pass_tc5<0, BF16>(mp, sh, w0, w1, f, smem, mphase, t8);
+    else if (c == 1) mixed_class_pass_tc5<1, BF16>(mp, sh, w0, w1, f, smem, mphase, t9);
+    else mixed_class_pass_tc5<2, BF16>(mp, sh, w0, w1, f, smem, mphase, t10);
+  });
+  tc5_fence_before();
+  __syncthreads();
+  if ((threadIdx.x >> 5) == 0) tc5_dealloc(tc_tmem);
 }
 
 }  // namespace gsk

@@ -89,23 +89,27 @@ cudaError_t iteration_occupancy(int nx, int ny, int* blocks_per_sm, int tc_mode)
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k, kThreads, smem);
 }
 
-size_t mixed_smem_bytes(bool tensor_core) {
-  // one twiddle table per class, then the shared cos/sin table
-  return kGroupSmemBytes + 8192 * 4 + 8192 * 8 + (tensor_core ? 3 * 32 * 32 * 8 + 32 * 8 : 0);
+size_t mixed_smem_bytes(int tc_mode) {
+  // mma.sync: one twiddle table per class, then the shared cos/sin table;
+  // tcgen05: the matrices and twiddle tables of the three lengths
+  const size_t extra = tc_mode == kTcMmaSync ? 3 * 32 * 32 * 8 + 32 * 8
+                       : (tc_mode == kTcGen05F16 || tc_mode == kTcGen05Bf16) ? kMixedTc5ExtraSmemBytes
+                                                                               : 0;
+  return kGroupSmemBytes + 8192 * 4 + 8192 * 8 + extra;
 }
 
-cudaError_t mixed_occupancy(bool tensor_core, int* blocks_per_sm) {
-  const void* k = iterate_kernel_mixed(tensor_core);
-  const size_t smem = mixed_smem_bytes(tensor_core);
+cudaError_t mixed_occupancy(int tc_mode, int* blocks_per_sm) {
+  const void* k = iterate_kernel_mixed(tc_mode);
+  const size_t smem = mixed_smem_bytes(tc_mode);
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
   if (e != cudaSuccess) return e;
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k, kThreads, smem);
 }
 
-cudaError_t launch_mixed(const MixedParams& mp, int grid, bool tensor_core, cudaStream_t s) {
+cudaError_t launch_mixed(const MixedParams& mp, int grid, int tc_mode, cudaStream_t s) {
   void* args[] = {const_cast<MixedParams*>(&mp)};
-  return cudaLaunchCooperativeKernel(iterate_kernel_mixed(tensor_core), dim3(grid), dim3(kThreads), args,
-                                     mixed_smem_bytes(tensor_core), s);
+  return cudaLaunchCooperativeKernel(iterate_kernel_mixed(tc_mode), dim3(grid), dim3(kThreads), args,
+                                     mixed_smem_bytes(tc_mode), s);
 }
 
 cudaError_t launch_iterations(const Params& p, int grid, cudaStream_t s) {

@@ -69,10 +69,10 @@
 namespace gsk {
 
 // Shared memory of the tcgen05 transform after the iteration kernel's own:
-// the real-form 32-point DFT matrix B1 (hi, then lo: 8 KiB each), the
-// real-form R-point matrix B2 (hi, then lo, 8 KiB each at most), and the
-// 8 KiB twiddle table [k1][lane]. The A operands live in the exchange area
-// (kTc5HalfStride bytes per half: A_hi 16 KiB, A_lo 16 KiB).
+// the real-form 32-point DFT matrix B1, the real-form R-point matrix B2 (each
+// its FP16 or BF16 rounding, then for BF16 the remainder: tc5_real_form) and
+// the 8 KiB twiddle table [k1][lane]. The A operands live in the exchange
+// area (kTc5HalfStride bytes per half: A_hi 16 KiB, A_lo 16 KiB).
 constexpr int kTc5HalfStride = 4 * 32 * 33 * 8;  // the exchange buffers of four warps
 constexpr int kTc5AloOffset = 16384;
 constexpr int kTc5BBytes = 64 * 64 * 2;          // one real-form matrix of the largest size, one part
@@ -80,6 +80,8 @@ constexpr int kTc5B2Offset = 2 * kTc5BBytes;
 constexpr int kTc5TwOffset = 4 * kTc5BBytes;
 constexpr int kTc5TwBytes = 32 * 32 * 8;
 constexpr int kTc5SmemBytes = 4 * kTc5BBytes + kTc5TwBytes;
+// bytes of one part of the real form of the P-point DFT matrix (2P x 2P)
+__host__ __device__ constexpr int tc5_form_bytes(int P) { return 2 * P * 2 * P * 2; }
 static_assert(kTc5SmemBytes == kTc5ExtraSmemBytes, "tcgen05 tables match the launch size");
 static_assert(2 * kTc5AloOffset <= kTc5HalfStride, "both A operands of a half fit its exchange buffers");
 constexpr int kTc5TmemCols = 128;  // two halves x 64 FP32 columns
@@ -154,7 +156,7 @@ __device__ __forceinline__ uint32_t tc5_pack(float lo, float hi) {
 }
 
 // The real form of the P-point DFT matrix (P = 32 or R) as a K-major B
-// operand of 2P x 2P at dst (remainder at dst + kTc5BBytes for BF16): row n
+// operand of 2P x 2P at dst (remainder at dst + tc5_form_bytes(P) for BF16): row n
 // < P gives Re y_n, n >= P gives Im y_{n-P}; column K < P multiplies re x_K,
 // K >= P im x_{K-P}:
 //   B[n][K] = cos, B[n][P+K] = sin, B[P+n][K] = -sin, B[P+n][P+K] = cos
@@ -173,23 +175,23 @@ __device__ void tc5_real_form(unsigned char* dst) {
     if constexpr (BF16) {
       const __nv_bfloat16 hi = __float2bfloat16_rn(val);
       *reinterpret_cast<__nv_bfloat16*>(dst + off) = hi;
-      *reinterpret_cast<__nv_bfloat16*>(dst + kTc5BBytes + off) = __float2bfloat16_rn(val - __bfloat162float(hi));
+      *reinterpret_cast<__nv_bfloat16*>(dst + tc5_form_bytes(P) + off) =
+          __float2bfloat16_rn(val - __bfloat162float(hi));
     } else {
       *reinterpret_cast<__half*>(dst + off) = __float2half_rn(val);
     }
   }
 }
 
-// The block's constant tables for lines of n = 2^LOGN: B1 (32-point), B2
-// (R-point) and the stage twiddles tw[k1][lane] = W_n^{k1 t} / 32 with
-// t = lane mod R.
+// The block's constant tables for lines of n = 2^LOGN: B1 (32-point, unless
+// b1 is null: shared by every length), B2 (R-point) and the stage twiddles
+// tw[k1][lane] = W_n^{k1 t} / 32 with t = lane mod R.
 template <int LOGN, bool BF16>
-__device__ void tc5_build_tables(unsigned char* tabs) {
+__device__ void tc5_build_tables(unsigned char* b1, unsigned char* b2, float2* tw) {
   constexpr int N = 1 << LOGN;
   constexpr int R = N >> 5;
-  tc5_real_form<32, BF16>(tabs);
-  tc5_real_form<R, BF16>(tabs + kTc5B2Offset);
-  float2* tw = reinterpret_cast<float2*>(tabs + kTc5TwOffset);
+  if (b1 != nullptr) tc5_real_form<32, BF16>(b1);
+  tc5_real_form<R, BF16>(b2);
   for (int e = threadIdx.x; e < 32 * 32; e += blockDim.x) {
     const int k1 = e >> 5, t = (e & 31) & (R - 1);
     float s, c;
@@ -244,7 +246,7 @@ struct Tc5Fft {
   static constexpr int N2 = 2 * R;   // stage-2 N and K (real form)
   static_assert(R == 8 || R == 16 || R == 32, "tcgen05 transforms have length 256, 512 or 1024");
   unsigned char* abuf;  // the exchange area: half h's A operands at h * kTc5HalfStride
-  unsigned tabs;        // shared-memory address of the tables (tc5_build_tables)
+  unsigned b1, b2;      // shared-memory addresses of the real-form matrices (tc5_build_tables)
   const float2* tw;     // [k1][lane] twiddles / 32
   uint64_t* mbar;       // [2] completion of each half's products
   unsigned tmem;        // TMEM base of kTc5TmemCols columns
@@ -266,17 +268,17 @@ struct Tc5Fft {
 
   // The K-steps of one product into d_tmem: A (hi, lo at +kTc5AloOffset) at
   // a_addr with step `astep` and byte offsets (lbo, sbo); B (hi, lo at
-  // +kTc5BBytes) at b_addr, K-major with stride byte offset b_sbo.
+  // +b_lo) at b_addr, K-major with stride byte offset b_sbo.
   template <int KSTEPS>
   __device__ __forceinline__ void issue(unsigned d_tmem, unsigned a_addr, unsigned astep, unsigned lbo, unsigned sbo,
-                                        unsigned b_addr, unsigned b_sbo, unsigned idesc) const {
+                                        unsigned b_addr, unsigned b_sbo, unsigned b_lo, unsigned idesc) const {
 #pragma unroll
     for (int s = 0; s < KSTEPS; ++s) {
       const uint64_t ah = tc5_desc(a_addr + astep * s, lbo, sbo);
       const uint64_t bh = tc5_desc(b_addr + 256u * s, 128u, b_sbo);
       tc5_mma(d_tmem, ah, bh, idesc, s > 0 ? 1u : 0u);
       if constexpr (BF16) {
-        tc5_mma(d_tmem, ah, tc5_desc(b_addr + kTc5BBytes + 256u * s, 128u, b_sbo), idesc, 1u);
+        tc5_mma(d_tmem, ah, tc5_desc(b_addr + b_lo + 256u * s, 128u, b_sbo), idesc, 1u);
         tc5_mma(d_tmem, tc5_desc(a_addr + kTc5AloOffset + astep * s, lbo, sbo), bh, idesc, 1u);
       }
     }
@@ -323,7 +325,7 @@ struct Tc5Fft {
     asm volatile("bar.sync %0, 128;" ::"r"(1 + half) : "memory");
     if (leader) {
       tc5_fence_after();
-      issue<4>(d_tmem, a_addr, 256u, 128u, 1024u, tabs, 1024u, tc5_idesc(BF16, false, 64u));
+      issue<4>(d_tmem, a_addr, 256u, 128u, 1024u, b1, 1024u, tc5_form_bytes(32), tc5_idesc(BF16, false, 64u));
       tc5_commit(&mbar[half]);
     }
     wait(half);
@@ -377,8 +379,8 @@ struct Tc5Fft {
       tc5_fence_after();
 #pragma unroll
       for (int c = 0; c < Q; ++c)
-        issue<N2 / 16>(d_tmem + static_cast<unsigned>(c * N2), a_addr + c * R * 512, 4096u, 2048u, 128u,
-                       tabs + kTc5B2Offset, (N2 / 8) * 128u, tc5_idesc(BF16, true, N2));
+        issue<N2 / 16>(d_tmem + static_cast<unsigned>(c * N2), a_addr + c * R * 512, 4096u, 2048u, 128u, b2,
+                       (N2 / 8) * 128u, tc5_form_bytes(R), tc5_idesc(BF16, true, N2));
       tc5_commit(&mbar[half]);
     }
     wait(half);

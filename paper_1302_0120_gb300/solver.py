@@ -176,7 +176,7 @@ class MixedGerchbergSaxton:
     SIZES = (256, 512, 1024)
 
     def __init__(self, max_batch: dict, final_residual: bool = True, stream=None, tensor_core: bool = False,
-                 init_from_target: bool = False):
+                 init_from_target: bool = False, bf16: bool = False, mma_sync: bool = False):
         import torch
 
         if stream is None:
@@ -186,7 +186,8 @@ class MixedGerchbergSaxton:
         self.init_from_target = bool(init_from_target)
         self.max_batch = {n: int(max_batch.get(n, 0)) for n in self.SIZES}
         flags = ((B.GS_FINAL_RESIDUAL if final_residual else 0) | (B.GS_INIT_FROM_TARGET if init_from_target else 0)
-                 | (B.GS_TENSOR_CORE if tensor_core else 0))
+                 | (B.GS_TENSOR_CORE if tensor_core else 0) | (B.GS_BF16 if bf16 else 0)
+                 | (B.GS_TC_MMA_SYNC if mma_sync else 0))
         self.handle = B.gs_create_mixed([self.max_batch[n] for n in self.SIZES], flags, stream.cuda_stream)
 
     def run(self, targets: dict, phases: dict | None, iters: int):

@@ -109,7 +109,19 @@ def test_batch_matches_single_runs(n):
         assert np.allclose(r[k], r1, rtol=GROUPING_RTOL, atol=0) and np.allclose(g[k], g1, rtol=GROUPING_RTOL, atol=0)
 
 
-def test_mixed_sizes_64_masks():
+_ORACLE_FINAL = {}
+
+
+def oracle_final_residual(k, I, phi0, iters):
+    """The oracle's r^K of mask k of the mixed batch (computed once for the
+    three engines)."""
+    if k not in _ORACLE_FINAL:
+        _ORACLE_FINAL[k] = O.gs_run(I, phi0, iters)["r"][-1]
+    return _ORACLE_FINAL[k]
+
+
+@pytest.mark.parametrize("engine", ["tcgen05-f16", "tcgen05-bf16", "mma-sync"])
+def test_mixed_sizes_64_masks(engine):
     """64 masks drawn from 256, 512 and 1024 with 10..200 spots, 50 iterations
     in one persistent launch: every final residual within 2% of the oracle's
     (the oracle runs each mask at full size)."""
@@ -126,7 +138,7 @@ def test_mixed_sizes_64_masks():
     assert len(by_size) == 3
     T = {n: torch.from_numpy(np.stack([masks[k][0] for k in ks])).cuda() for n, ks in by_size.items()}
     P = {n: torch.from_numpy(np.stack([masks[k][1] for k in ks])).cuda() for n, ks in by_size.items()}
-    with MixedGerchbergSaxton({n: len(ks) for n, ks in by_size.items()}, tensor_core=True) as gs:
+    with MixedGerchbergSaxton({n: len(ks) for n, ks in by_size.items()}, tensor_core=True, **ENGINES[engine]) as gs:
         out = gs.run(T, P, iters)
         assert gs.status() == 0
     r_final = {}
@@ -137,7 +149,7 @@ def test_mixed_sizes_64_masks():
             r_final[k] = r[j][-1]
     worst = 0.0
     for k, (I, phi0) in enumerate(masks):
-        ref = O.gs_run(I, phi0, iters)["r"][-1]
+        ref = oracle_final_residual(k, I, phi0, iters)
         worst = max(worst, abs(r_final[k] - ref) / ref)
     assert worst <= FINAL_TOL, worst
 
