@@ -22,6 +22,13 @@ struct Shared {
   int pending;    // a bulk copy into shared memory may still be in flight
   const float* m_block;  // global address of the amplitude block in shared memory (null: none)
   unsigned pending_phase;  // the mbarrier phase that copy completes
+  // Column passes that keep two column blocks in flight, one per half of the
+  // block (slot): each slot's completion mbarrier, resident amplitude block
+  // and pending copy, as above.
+  uint64_t mbar_s[2];
+  const float* m_slot[2];
+  int pend_s[2];
+  unsigned pend_phase_s[2];
   double red[kThreads / 32];
   float redf[kThreads / 32];
   float scale[kMaxBatch];  // sqrt(N / sum I) per mask

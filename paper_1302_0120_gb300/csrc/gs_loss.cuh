@@ -72,7 +72,7 @@ static __device__ bool loss_sync(const LossParams& p, unsigned& target, Shared& 
 template <int LN, int MODE>
 __global__ void __launch_bounds__(kThreads, 1) gs_loss_kernel(const LossParams p) {
   using G = GroupT<LN>;
-  using L = FieldLayout<LN, LN>;
+  using L = FieldLayout<LN, LN, false>;
   constexpr int N = G::N;
   constexpr int T = G::T;
   constexpr int LOGT = LN - 5;
