@@ -141,6 +141,18 @@ float2 unit_root(long long k, long long M) {
 // both sides, the stage tables of its radix plan: the stage with
 // sub-transform length ns and radix R holds W_{ns R}^{r m} at entry
 // ns - 1 + (m - 1) ns + r (1 <= m < R, r < ns); n - 1 entries in all.
+// Tables of the register-resident kernel (gs_rg.cuh) for a side n = T V:
+// W_n^{t q} at [q T + t] (q < V, t < T), then W_n^{q j} at n + [j V + q].
+std::vector<float2> rg_twiddles(int n) {
+  std::vector<float2> w(kTwiddleEntries, make_float2(0.f, 0.f));
+  const int T = gsk::rg_threads(n), V = n / T;
+  for (int q = 0; q < V; ++q)
+    for (int t = 0; t < T; ++t) w[q * T + t] = unit_root(static_cast<long long>(t) * q, n);
+  for (int j = 0; j < T; ++j)
+    for (int q = 0; q < V; ++q) w[n + j * V + q] = unit_root(static_cast<long long>(q) * j, n);
+  return w;
+}
+
 std::vector<float2> twiddles(int n, bool general) {
   std::vector<float2> w(kTwiddleEntries, make_float2(0.f, 0.f));
   if (general) {
@@ -269,7 +281,7 @@ int check_guards(const unsigned char* ws, const Layout& L) {
 }
 
 int choose_grid(const gs_ctx* c) {
-  if (!c->mixed && gsk::uses_general(c->nx, c->ny) && c->grid_override <= 0) {
+  if (!c->mixed && gsk::uses_general(c->nx, c->ny) && !gsk::uses_rg(c->nx, c->ny) && c->grid_override <= 0) {
     // general sides: one row per team (four per block) and one 4-column
     // group per block, so that each pass is one round
     const int t = gsk::kGenTeams;
@@ -349,8 +361,9 @@ int gs_create_batched(gs_ctx** out, int nx, int ny, int max_batch, unsigned flag
     return GS_ENOMEM;
   }
   const bool general = gsk::uses_general(nx, ny);
-  const std::vector<float2> wx = twiddles(nx, general);
-  const std::vector<float2> wy = twiddles(ny, general);
+  const bool rg = gsk::uses_rg(nx, ny);
+  const std::vector<float2> wx = rg ? rg_twiddles(nx) : twiddles(nx, general);
+  const std::vector<float2> wy = rg ? rg_twiddles(ny) : twiddles(ny, general);
   const std::vector<float> ones(4096, 1.0f);
   bool ok = cudaMemcpy(c->ws + c->L.twx, wx.data(), wx.size() * sizeof(float2), cudaMemcpyHostToDevice) == cudaSuccess &&
             cudaMemcpy(c->ws + c->L.ones, ones.data(), ones.size() * sizeof(float), cudaMemcpyHostToDevice) == cudaSuccess &&

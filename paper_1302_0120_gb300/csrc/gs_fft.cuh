@@ -19,10 +19,10 @@
 
 namespace gsk {
 
-__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
-__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__host__ __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__host__ __device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
 // a * w for a twiddle w = (c, s) meaning c + i s.
-__device__ __forceinline__ float2 cmul(float2 a, float2 w) {
+__host__ __device__ __forceinline__ float2 cmul(float2 a, float2 w) {
   return make_float2(a.x * w.x - a.y * w.y, a.x * w.y + a.y * w.x);
 }
 
@@ -51,7 +51,7 @@ struct W32 {
 // (+-1 - i)/sqrt2 one addition pair less than a general factor, and the
 // general case uses fused multiply-adds with a - w b = 2a - (a + w b).
 template <int E>
-__device__ __forceinline__ void bfly(float2& a, float2& b) {
+__host__ __device__ __forceinline__ void bfly(float2& a, float2& b) {
   if constexpr (E == 0) {
     const float2 s = make_float2(a.x + b.x, a.y + b.y);
     b = make_float2(a.x - b.x, a.y - b.y);
@@ -89,24 +89,24 @@ __device__ __forceinline__ void bfly(float2& a, float2& b) {
 template <int R, int H>
 struct DitStage {
   template <int BASE, int K>
-  static __device__ __forceinline__ void k_loop(float2 (&a)[R]) {
+  static __host__ __device__ __forceinline__ void k_loop(float2 (&a)[R]) {
     if constexpr (K < H) {
       bfly<K * (16 / H)>(a[BASE + K], a[BASE + K + H]);
       k_loop<BASE, K + 1>(a);
     }
   }
   template <int BASE>
-  static __device__ __forceinline__ void b_loop(float2 (&a)[R]) {
+  static __host__ __device__ __forceinline__ void b_loop(float2 (&a)[R]) {
     if constexpr (BASE < R) {
       k_loop<BASE, 0>(a);
       b_loop<BASE + 2 * H>(a);
     }
   }
-  static __device__ __forceinline__ void run(float2 (&a)[R]) { b_loop<0>(a); }
+  static __host__ __device__ __forceinline__ void run(float2 (&a)[R]) { b_loop<0>(a); }
 };
 
 template <int R, int H>
-__device__ __forceinline__ void dit_all(float2 (&a)[R]) {
+__host__ __device__ __forceinline__ void dit_all(float2 (&a)[R]) {
   if constexpr (H < R) {
     DitStage<R, H>::run(a);
     dit_all<R, 2 * H>(a);
@@ -122,7 +122,7 @@ __host__ __device__ constexpr int bitrev(int i, int bits) {
 __host__ __device__ constexpr int ilog2(int n) { return n <= 1 ? 0 : 1 + ilog2(n >> 1); }
 
 template <int R, int I>
-__device__ __forceinline__ void bitrev_copy(float2 (&dst)[R], const float2 (&src)[R]) {
+__host__ __device__ __forceinline__ void bitrev_copy(float2 (&dst)[R], const float2 (&src)[R]) {
   if constexpr (I < R) {
     dst[I] = src[bitrev(I, ilog2(R))];
     bitrev_copy<R, I + 1>(dst, src);
@@ -133,7 +133,7 @@ __device__ __forceinline__ void bitrev_copy(float2 (&dst)[R], const float2 (&src
 // order in and out: bit-reversal permutation (register renaming only), then
 // log2(R) radix-2 decimation-in-time stages.
 template <int R>
-__device__ __forceinline__ void dft(float2 (&a)[R]) {
+__host__ __device__ __forceinline__ void dft(float2 (&a)[R]) {
   float2 t[R];
   bitrev_copy<R, 0>(t, a);
   dit_all<R, 1>(t);

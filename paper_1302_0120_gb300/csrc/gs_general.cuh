@@ -40,7 +40,7 @@ __host__ __device__ constexpr int radix_of_code(unsigned c) {
 
 // 3-point DFT, exp(-2 pi i jk/3): with t = a1 + a2 and d = (sqrt3/2)(a1 - a2),
 // y1,2 = a0 - t/2 -/+ i d.
-__device__ __forceinline__ void dft3(float2 (&a)[3]) {
+__host__ __device__ __forceinline__ void dft3(float2 (&a)[3]) {
   constexpr float h = 0.8660254037844386f;  // sqrt(3)/2
   const float2 t = cadd(a[1], a[2]);
   const float2 d = make_float2(h * (a[1].x - a[2].x), h * (a[1].y - a[2].y));
@@ -55,7 +55,7 @@ __device__ __forceinline__ void dft3(float2 (&a)[3]) {
 //   y1,4 = a0 + c1 b1 + c2 b2 -/+ i (s1 d1 + s2 d2)
 //   y2,3 = a0 + c2 b1 + c1 b2 -/+ i (s2 d1 - s1 d2)
 // with ck = cos(2 pi k/5), sk = sin(2 pi k/5).
-__device__ __forceinline__ void dft5(float2 (&a)[5]) {
+__host__ __device__ __forceinline__ void dft5(float2 (&a)[5]) {
   constexpr float c1 = 0.30901699437494745f, c2 = -0.8090169943749475f;
   constexpr float s1 = 0.9510565162951535f, s2 = 0.5877852522924731f;
   const float2 b1 = cadd(a[1], a[4]), b2 = cadd(a[2], a[3]);
@@ -73,7 +73,7 @@ __device__ __forceinline__ void dft5(float2 (&a)[5]) {
 }
 
 template <int R>
-__device__ __forceinline__ void small_dft(float2 (&a)[R]) {
+__host__ __device__ __forceinline__ void small_dft(float2 (&a)[R]) {
   if constexpr (R == 3) dft3(a);
   else if constexpr (R == 5) dft5(a);
   else dft<R>(a);

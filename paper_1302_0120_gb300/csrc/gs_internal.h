@@ -94,6 +94,16 @@ inline __host__ __device__ bool uses_general(int nx, int ny) {
   return !px || !py || nx < 32 || ny < 32;
 }
 
+// Register-resident general-grid kernel (gs_rg.cuh): sides n = T V with a
+// line in one warp (T lanes of V points, T, V <= 32). rg_threads(n) is T for
+// the sides it serves (600 = 24 x 25, 800 = 32 x 25), else 0; a grid whose two
+// sides are both served runs there, any other side that is not a power of
+// two on the shared-memory general kernel. Kernel templates take such a side
+// itself in place of log2 nx (is_rg_side).
+inline __host__ __device__ constexpr int rg_threads(int n) { return n == 600 ? 24 : n == 800 ? 32 : 0; }
+inline __host__ __device__ constexpr bool is_rg_side(int lx) { return lx >= 32; }
+inline __host__ __device__ bool uses_rg(int nx, int ny) { return rg_threads(nx) > 0 && rg_threads(ny) > 0; }
+
 // Sides of the general kernel: 5-smooth (2^a 3^b 5^c) in [8, kMaxGeneralSide].
 constexpr int kMaxGeneralSide = 1536;
 constexpr int kMaxGeneralStages = 10;
@@ -121,6 +131,12 @@ const void* iterate_kernel_lx(int ly);
 const void* iterate_kernel_tc(int l);
 // Kernel for grids with a side that is not a power of two (gs_general_inst.cu).
 const void* iterate_kernel_general();
+// Register-resident kernel for an nx x ny grid with uses_rg (gs_rg_inst.cu),
+// its dynamic shared memory, and the layout of its twiddle tables: for a side
+// n = T V, n entries W_n^{t q} at [q T + t] (q < V, t < T), then n entries
+// W_n^{q j} at [j V + q].
+const void* iterate_kernel_rg(int nx, int ny);
+size_t rg_smem_bytes(int nx, int ny);
 // Kernel for three square size classes in one launch (gs_mixed_inst.cu), by
 // TcMode.
 const void* iterate_kernel_mixed(int tc_mode);

@@ -40,6 +40,7 @@
 #include "gs_common.cuh"
 #include "gs_fft.cuh"
 #include "gs_general.cuh"
+#include "gs_rg.cuh"
 #include "gs_internal.h"
 #include "gs_tc.cuh"
 #include "gs_tc5.cuh"
@@ -521,11 +522,12 @@ static __device__ __forceinline__ void restore_flags(const Params& p, Shared& sh
     for (int mb = 0; mb < p.batch; ++mb) sh.bad[base + mb] = p.mask_flags[mb];
 }
 
-template <int LX>
+template <int LX, int LY = LX>
 __device__ __forceinline__ void build_amplitudes(const Params& p, Shared& sh, int base, unsigned char* smem) {
   for (int mb = 0; mb < p.batch; ++mb)
     if (!sh.bad[base + mb]) {
       if constexpr (LX == 0) gen_build_amplitude(p, mb, sh.scale[base + mb]);
+      else if constexpr (is_rg_side(LX)) rg_build_amplitude<LX, LY>(p, mb, sh.scale[base + mb], smem);
       else build_amplitude(p, mb, sh.scale[base + mb], smem);
     }
 }
@@ -570,13 +572,14 @@ static __device__ __forceinline__ PassInfo pass_info(const Params& p, int q0) {
 // blocks, so that small masks of a batch do not leave blocks idle; a block
 // works through its share mask by mask and writes the FP64 partial of each
 // mask's gap to its slot (zero for the masks it does not touch).
-template <int LX, int LY, bool HOLD, class TCF>
+template <int LX, int LY, bool HOLD, class TCF, class TW>
 __device__ __forceinline__ void class_pass(const Params& p, Shared& sh, int base, int w0, int w1, const PassInfo& f,
-                                           unsigned char* smem, unsigned& mphase, const StageTw<LX>& tw_rows,
+                                           unsigned char* smem, unsigned& mphase, const TW& tw_rows,
                                            const TCF& tcf) {
   const bool rows = (f.kind == kInit || f.kind == kRow);
   int per;  // units of one mask
   if constexpr (LX == 0) per = rows ? p.ny : (p.nx + kGenTeams - 1) / kGenTeams;
+  else if constexpr (is_rg_side(LX)) per = rows ? p.ny : LX / RgLayout<LX, LY>::W;
   else per = rows ? p.ny : FieldLayout<LX, LY>::NBLK;
   const int G = gridDim.x;
   int lo, hi, m0, m1;
@@ -602,6 +605,8 @@ __device__ __forceinline__ void class_pass(const Params& p, Shared& sh, int base
     float a;
     if constexpr (LX == 0) {
       a = run_pass_gen(p, mb, f.kind, f.last, slo, shi, smem);
+    } else if constexpr (is_rg_side(LX)) {
+      a = run_pass_rg<LX, LY>(p, mb, f.kind, f.last, slo, shi, smem, sh, mphase);
     } else if constexpr (LX == LY) {
       a = run_pass<LX, LX, LY, HOLD>(p, mb, f.kind, f.last, slo, shi, smem, sh, mphase, tw_rows, tcf);
     } else {
@@ -664,13 +669,14 @@ static __device__ __forceinline__ void block_setup(Shared& sh) {
 // The schedule of one size class (every grid): A0, then the passes, then the
 // gaps. Returns early (in every thread of the block) when a grid barrier gave
 // up or every mask was rejected.
-template <int LX, int LY, bool kHold, class TCF>
+template <int LX, int LY, bool kHold, class TCF, class TW>
 __device__ __forceinline__ void iterate_class(const Params& p, Shared& sh, unsigned char* smem,
-                                              const StageTw<LX>& tw_rows, const TCF& tcf) {
+                                              const TW& tw_rows, const TCF& tcf) {
   unsigned target = 0;
   unsigned mphase = 0;
   block_setup(sh);
   if constexpr (LX == 0) gen_load_twiddles(p, smem);  // sides that are not powers of two
+  if constexpr (is_rg_side(LX)) rg_load_twiddles<LX, LY>(p, smem);
 
   if (p.do_init) {
     a0_partials(p, sh);
@@ -680,7 +686,7 @@ __device__ __forceinline__ void iterate_class(const Params& p, Shared& sh, unsig
       if (blockIdx.x == 0 && threadIdx.x == 0) atomicExch(p.abort_flag, 1);  // later launches of the run
       return;
     }
-    build_amplitudes<LX>(p, sh, 0, smem);
+    build_amplitudes<LX, LY>(p, sh, 0, smem);
     // the target start transforms m in its first pass, reading columns that
     // other blocks built
     if (p.init_target && !grid_sync(p, target, sh)) return;

@@ -49,7 +49,10 @@ static int log2_exact(int n) {
 }
 
 static const void* kernel_for(int nx, int ny, int tc_mode) {
-  if (uses_general(nx, ny)) return tc_mode != kTcNone ? nullptr : iterate_kernel_general();
+  if (uses_general(nx, ny)) {
+    if (tc_mode != kTcNone) return nullptr;
+    return uses_rg(nx, ny) ? iterate_kernel_rg(nx, ny) : iterate_kernel_general();
+  }
   const int ly = log2_exact(ny);
   if (tc_mode == kTcGen05F16 || tc_mode == kTcGen05Bf16)
     return nx == ny ? iterate_kernel_tc5(ly, tc_mode == kTcGen05Bf16) : nullptr;
@@ -68,6 +71,7 @@ static const void* kernel_for(int nx, int ny, int tc_mode) {
 }
 
 size_t iteration_smem_bytes(int nx, int ny, int tc_mode) {
+  if (uses_rg(nx, ny)) return rg_smem_bytes(nx, ny);
   if (uses_general(nx, ny)) return gen_smem_bytes(nx, ny);
   // group exchange buffers, one column block of the amplitude, one of the
   // field; then the tensor-core tables (and, for tcgen05, operands)
@@ -83,7 +87,7 @@ cudaError_t iteration_occupancy(int nx, int ny, int* blocks_per_sm, int tc_mode)
   const size_t smem = iteration_smem_bytes(nx, ny, tc_mode);
   // The general kernel serves every size: allow its largest request, so that
   // contexts of different sizes do not undo each other's setting.
-  const size_t allow = uses_general(nx, ny) ? gen_smem_bytes(kMaxGeneralSide, kMaxGeneralSide) : smem;
+  const size_t allow = (uses_general(nx, ny) && !uses_rg(nx, ny)) ? gen_smem_bytes(kMaxGeneralSide, kMaxGeneralSide) : smem;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(allow));
   if (e != cudaSuccess) return e;
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k, kThreads, smem);

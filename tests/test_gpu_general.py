@@ -17,7 +17,10 @@ pytestmark = pytest.mark.gpu
 @pytest.mark.parametrize(
     "ny,nx,iters,nspots",
     [
-        (600, 800, 25, 50),   # the paper's SLM and iteration count
+        (600, 800, 25, 50),   # the paper's SLM and iteration count (register-resident kernel)
+        (800, 600, 10, 30),   # the other sides of the register-resident kernel
+        (800, 800, 8, 30),
+        (600, 600, 8, 30),
         (160, 96, 20, 10),
         (36, 75, 15, 4),      # 75 columns: a ragged last group of 3
         (512, 800, 10, 30),   # one side a power of two
@@ -47,6 +50,15 @@ def test_parity_grid_shares(grid):
     I = S.spot_target(3, 90, 120, 12, (0.5, 1.0))
     phi0 = S.random_phase(3, 90, 120)
     check_run(I, phi0, 6, grid=grid, one_step_at=(0,))
+
+
+@pytest.mark.parametrize("grid", [1, 7, 151])
+def test_register_kernel_grid_shares(grid):
+    """The register-resident kernel (sides 600 and 800) with ragged shares of
+    rows and column blocks over the blocks, several rounds per block."""
+    I = S.spot_target(5, 600, 800, 30, (0.5, 1.0))
+    phi0 = S.random_phase(5, 600, 800)
+    check_run(I, phi0, 4, grid=grid, one_step_at=(0, 3))
 
 
 def test_800x600_paper_variants():
