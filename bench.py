@@ -508,6 +508,20 @@ def run_gpu(args):
         serving["disjoint_sm_shares"] = {k: v for k, v in serve_stream(args.serve_rate, half, share_sms=False).items()
                                          if k in ("requests", "p50_ms", "p99_ms", "max_ms", "lanes")}
 
+        # the persistent server (gs_serve_*): one launch on the whole device
+        # admits requests between iterations, 4 slots per size
+        def persistent(rate, seconds):
+            summ, sch, ex = SV.run_persistent_service(rate_hz=rate, seconds=seconds, sizes=(512, 1024), slots=(4, 4),
+                                                      iters=30, warmup_s=0.3)
+            ex.close()
+            del sch, ex
+            return {k: (round(v, 4) if isinstance(v, float) else v) for k, v in summ.items()
+                    if k in ("requests", "p50_ms", "p99_ms", "max_ms", "rate_hz", "by_size", "slots", "grid", "mode")}
+
+        serving["persistent"] = persistent(args.serve_rate, half)
+        serving["persistent"]["at_2x_rate"] = {k: v for k, v in persistent(2 * args.serve_rate, half).items()
+                                               if k in ("requests", "p50_ms", "p99_ms", "max_ms", "rate_hz")}
+
     def timed(fn, steps):
         """Mean device ms of fn() over `steps` launches, L2 flushed before each."""
         fn()

@@ -525,6 +525,76 @@ int gs_fp32_peak(double* tflops_out, void* stream);
  */
 int gs_stream_notify(void* stream, int fd);
 
+/*
+ * Persistent server (serving; the paper has no counterpart): one cooperative
+ * launch that keeps iterating Eq. (e:AP) for the requests posted to its slots
+ * and admits a request between two iterations of the others (continuous
+ * batching with no host step between iterations). A request is the call of
+ * gs_run for one n x n mask (n = 256, 512 or 1024; requests of different
+ * sizes run together), p = 1, random-phase start: K iterations from
+ * phase_in, phase_out and r^nu, g^nu (nu < K; no final residual) out. A
+ * request of K iterations takes K + 1 server iterations (the first computes
+ * the amplitude of Eq. pattern-constraint and u^0).
+ *
+ * Every buffer of a request is pinned host memory (cudaHostAlloc, or a
+ * registered range) that the device reads and writes in place: the target
+ * intensity and start phase ([n][n] row-major FP32) are read by the server,
+ * the final phase ([n][n], may alias phase_in) and r, g (K doubles each, or
+ * NULL) written by it. The caller keeps them alive and leaves them alone until
+ * gs_serve_poll reports the request done.
+ */
+typedef struct gs_server gs_server;
+
+/*
+ * gs_serve_create -- a server for grids up to max_n x max_n (max_n = 256, 512
+ * or 1024) with `slots` request slots (1..16) on `stream` (a cudaStream_t;
+ * NULL: the legacy default stream, which the server then occupies while it
+ * runs). `grid` is the number of blocks of its launches (0: one per SM; each
+ * SM holds at most one), so two servers on two streams can share the device
+ * by SM counts whose sum does not exceed it. Allocates the slot arrays
+ * (12 max_n^2 bytes per slot) and the request table; launches nothing.
+ * Returns GS_EINVAL for bad arguments, GS_ENOMEM, GS_ECUDA.
+ */
+int gs_serve_create(gs_server** out, int max_n, int slots, int grid, void* stream);
+
+/*
+ * gs_serve_submit -- post a request of `iters` >= 1 iterations for an n x n
+ * grid (n = 256, 512 or 1024, at most max_n) to slot `slot`, which must be
+ * free (its previous request reported done). Writes the
+ * request and its sequence number (returned in *seq_out, nonzero, if not
+ * NULL) to the table and launches the server if no launch is serving. Returns
+ * GS_EINVAL for a busy slot, a bad argument or a buffer the device cannot
+ * address, GS_ECUDA if the launch fails, or the server's failure status.
+ */
+int gs_serve_submit(gs_server* s, int slot, int n, const float* target_intensity, const float* phase_in,
+                    int iters, float* phase_out, double* residual_out, double* object_gap_out, unsigned* seq_out);
+
+/*
+ * gs_serve_poll -- the sequence number of the last request of `slot` that is
+ * done (*done_seq; the request's outputs are complete once it equals the
+ * submitted one) and that request's status (*request_status: GS_OK,
+ * GS_ENUMERIC for a target with a negative, non-finite or all-zero
+ * intensity, GS_EINVAL). Relaunches the server when requests are outstanding
+ * and no launch runs (a launch leaves after 20 ms without work, and after
+ * 2^20 iterations). Non-blocking. Returns GS_OK, or the server's failure
+ * status (e.g. GS_ETIMEOUT from a grid barrier), after which no request
+ * completes.
+ */
+int gs_serve_poll(gs_server* s, int slot, unsigned* done_seq, int* request_status);
+
+/*
+ * gs_serve_stop -- block until every posted request is done and no launch
+ * runs. Returns GS_OK, the server's failure status, or GS_ETIMEOUT if
+ * requests were still outstanding after 60 s.
+ */
+int gs_serve_stop(gs_server* s);
+
+/* gs_serve_grid -- blocks per launch of the server (0 for NULL). */
+int gs_serve_grid(const gs_server* s);
+
+/* gs_serve_destroy -- stop, then free the server. NULL is a no-op. */
+void gs_serve_destroy(gs_server* s);
+
 /* gs_strerror -- static English text for a status code (never NULL). */
 const char* gs_strerror(int code);
 

@@ -60,6 +60,12 @@ SIGNATURES = {
     "gs_get_trace": (_c_int, [_vp, _vp, _c_int, ctypes.POINTER(_c_int), ctypes.POINTER(_c_int)]),
     "gs_fp32_peak": (_c_int, [ctypes.POINTER(ctypes.c_double), _vp]),
     "gs_stream_notify": (_c_int, [_vp, _c_int]),
+    "gs_serve_create": (_c_int, [ctypes.POINTER(_vp), _c_int, _c_int, _c_int, _vp]),
+    "gs_serve_submit": (_c_int, [_vp, _c_int, _c_int, _vp, _vp, _c_int, _vp, _vp, _vp, ctypes.POINTER(_c_uint)]),
+    "gs_serve_poll": (_c_int, [_vp, _c_int, ctypes.POINTER(_c_uint), ctypes.POINTER(_c_int)]),
+    "gs_serve_stop": (_c_int, [_vp]),
+    "gs_serve_grid": (_c_int, [_vp]),
+    "gs_serve_destroy": (None, [_vp]),
     "gs_adam_step": (_c_int, [_vp, _vp, _vp, _vp, ctypes.c_longlong, _vp, ctypes.c_float, ctypes.c_float,
                               ctypes.c_float, ctypes.c_float, _vp]),
 }
@@ -299,6 +305,43 @@ def gs_fp32_peak(stream: int | None = None) -> float:
 def gs_stream_notify(stream: int | None, fd: int) -> int:
     """Enqueue a write of 1 to ``fd`` once ``stream`` reaches it; returns the status code."""
     return lib().gs_stream_notify(_vp(stream or 0), int(fd))
+
+
+def gs_serve_create(max_n: int, slots: int, grid: int = 0, stream: int | None = None) -> int:
+    """A persistent server for masks up to max_n x max_n with `slots` request slots; returns its handle."""
+    h = _vp()
+    rc = lib().gs_serve_create(ctypes.byref(h), int(max_n), int(slots), int(grid), _vp(stream or 0))
+    if rc != GS_OK:
+        raise GSError(rc, "gs_serve_create")
+    return h.value
+
+
+def gs_serve_submit(srv: int, slot: int, n: int, target: int, phase_in: int, iters: int, phase_out: int,
+                    r_out: int = 0, g_out: int = 0):
+    """Post a request for an n x n mask (pinned host pointers); returns (status code, sequence number)."""
+    seq = _c_uint(0)
+    rc = lib().gs_serve_submit(_vp(srv), int(slot), int(n), _vp(target), _vp(phase_in), int(iters), _vp(phase_out),
+                               _vp(r_out or None), _vp(g_out or None), ctypes.byref(seq))
+    return rc, seq.value
+
+
+def gs_serve_poll(srv: int, slot: int):
+    """(server status, last done sequence number of the slot, that request's status)."""
+    d, st = _c_uint(0), _c_int(0)
+    rc = lib().gs_serve_poll(_vp(srv), int(slot), ctypes.byref(d), ctypes.byref(st))
+    return rc, d.value, st.value
+
+
+def gs_serve_stop(srv: int) -> int:
+    return lib().gs_serve_stop(_vp(srv))
+
+
+def gs_serve_grid(srv: int) -> int:
+    return lib().gs_serve_grid(_vp(srv))
+
+
+def gs_serve_destroy(srv: int) -> None:
+    lib().gs_serve_destroy(_vp(srv))
 
 
 def gs_destroy(ctx: int) -> int:

@@ -26,6 +26,7 @@ LIB_PATH = os.path.join(OUT_DIR, LIB_NAME)
 SOURCES = [("gs_api.cu", "gs_api", []), ("gs_launch.cu", "gs_launch", []), ("gs_noalloc.cu", "gs_noalloc", []), ("gs_loss_inst.cu", "gs_loss_inst", []), ("gs_tc_inst.cu", "gs_tc_inst", []), ("gs_tc5_inst.cu", "gs_tc5_inst", []),
     ("gs_general_inst.cu", "gs_general_inst", []),
     ("gs_rg_inst.cu", "gs_rg_inst", []),
+    ("gs_serve.cu", "gs_serve", []),
     ("gs_mixed_inst.cu", "gs_mixed_inst", []), ("gs_adam.cu", "gs_adam", []), ("gs_peak.cu", "gs_peak", []), ("gs_notify.cu", "gs_notify", []),
     ("gs_small_inst.cu", "gs_small_inst", [])] + [
     ("gs_inst.cu", f"gs_inst_lx{lx}", [f"-DGS_LX={lx}"]) for lx in range(5, 13)

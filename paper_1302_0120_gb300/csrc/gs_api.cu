@@ -67,7 +67,7 @@ int ilog2i(int n) {
 }
 
 // Entries of one stage-twiddle table (stages after 32 and after 1024 points).
-constexpr int kTwiddleEntries = 31 * 32 + 31 * 1024;
+constexpr int kTwiddleEntries = gsk::kStageTwiddleEntries;
 
 // Offsets of the sub-buffers of one workspace allocation.
 struct Layout {
@@ -295,6 +295,13 @@ int choose_grid(const gs_ctx* c) {
 }
 
 }  // namespace
+
+namespace gsk {
+void stage_twiddles_host(int n, float2* out) {
+  const std::vector<float2> w = twiddles(n, false);
+  std::copy(w.begin(), w.end(), out);
+}
+}  // namespace gsk
 
 extern "C" {
 

@@ -137,6 +137,10 @@ const void* iterate_kernel_general();
 // W_n^{q j} at [j V + q].
 const void* iterate_kernel_rg(int nx, int ny);
 size_t rg_smem_bytes(int nx, int ny);
+// Stage twiddle tables of a power-of-two length n (the layout stage_c reads),
+// kStageTwiddleEntries entries, rounded once from double (gs_api.cu).
+constexpr int kStageTwiddleEntries = 31 * 32 + 31 * 1024;
+void stage_twiddles_host(int n, float2* out);
 // Kernel for three square size classes in one launch (gs_mixed_inst.cu), by
 // TcMode.
 const void* iterate_kernel_mixed(int tc_mode);

@@ -30,6 +30,11 @@ module serves a stream of such requests on one GPU:
   next arrival or the next completion, which the library signals through an
   eventfd (gs_stream_notify) from the end of each launch.
 
+``PersistentExecutor`` and ``run_persistent_service`` serve through the
+library's persistent server instead (gs_serve_create): one launch on the
+whole device keeps iterating, and a request posted to a free slot joins the
+running ones at their next iteration, with no launch per request.
+
 Every step of the method runs in the CUDA library; this module only moves
 buffers and decides what to launch when.
 """
@@ -343,6 +348,107 @@ class GpuExecutor:
             self.fd = None
 
 
+class PersistentExecutor:
+    """Serves through one persistent server (gs_serve_create) on the whole
+    device: its slots are dedicated to the sizes (``slots[i]`` slots for
+    ``sizes[i]``), each slot a lane of one request. A request posted to a free
+    slot joins the server's running requests, of every size, at its next
+    iteration; the host only writes the request table and reads completions.
+    The target and the phase stay in pinned host memory that the server reads
+    and writes in place; every slot warm-starts from its own last mask."""
+
+    def __init__(self, sizes: Sequence[int], slots: Sequence[int], iters: int, grid: int = 0, device=None,
+                 record: bool = False, warm_seed: int = 7, pool_extra: int = 16):
+        import torch
+
+        from . import _binding as B
+        from .synthetic import random_phase
+
+        self.torch = torch
+        self.B = B
+        self.iters = iters
+        self.record = record
+        self.device = device or torch.device("cuda", torch.cuda.current_device())
+        self.stream = torch.cuda.Stream(device=self.device)
+        self.server = B.gs_serve_create(max(sizes), sum(slots), grid, self.stream.cuda_stream)
+        self.grid = B.gs_serve_grid(self.server)
+        self.lanes = {}
+        self.plans: List[LanePlan] = []
+        k = 0
+        for n, s in zip(sizes, slots):
+            for _ in range(s):
+                p = LanePlan(f"{n}/{k}", n, 1, self.grid, 12 * n * n)
+                self.plans.append(p)
+                self.lanes[p.name] = {
+                    "plan": p, "slot": k,
+                    "warm": torch.from_numpy(random_phase(warm_seed, n, n)).pin_memory(),
+                    "hI": torch.empty((n, n), dtype=torch.float32).pin_memory(),
+                    "R": torch.zeros(max(iters, 1), dtype=torch.float64).pin_memory(),
+                    "G": torch.zeros(max(iters, 1), dtype=torch.float64).pin_memory(),
+                    "busy": None,
+                }
+                k += 1
+        self.pool = {n: [torch.empty((n, n), dtype=torch.float32).pin_memory() for _ in range(s + pool_extra)]
+                     for n, s in zip(sizes, slots)}
+        self.graph_ok = False
+
+    def stage(self, r: Request) -> bool:
+        if r.pinned is not None:
+            return True
+        pool = self.pool.get(r.n)
+        if not pool:
+            return False
+        buf = pool.pop()
+        buf.copy_(self.torch.from_numpy(r.target))
+        r.pinned = buf
+        return True
+
+    def idle(self, p: LanePlan) -> bool:
+        return self.lanes[p.name]["busy"] is None
+
+    def launch(self, p: LanePlan, reqs: List[Request], now: float):
+        L = self.lanes[p.name]
+        (r,) = reqs
+        if not self.stage(r):
+            L["hI"].copy_(self.torch.from_numpy(r.target))
+        src = r.pinned if r.pinned is not None else L["hI"]
+        if self.record:
+            r.warm_in = L["warm"].numpy().copy()
+        r.slot = L["slot"]
+        rc, seq = self.B.gs_serve_submit(self.server, L["slot"], r.n, src.data_ptr(), L["warm"].data_ptr(), self.iters,
+                                         L["warm"].data_ptr(), L["R"].data_ptr(), L["G"].data_ptr())
+        if rc != self.B.GS_OK:
+            raise self.B.GSError(rc, "gs_serve_submit")
+        L["busy"] = (seq, r)
+
+    def poll(self, p: LanePlan, now: float) -> List[Request]:
+        L = self.lanes[p.name]
+        if L["busy"] is None:
+            return []
+        seq, r = L["busy"]
+        rc, done, st = self.B.gs_serve_poll(self.server, L["slot"])
+        if rc != self.B.GS_OK:
+            raise self.B.GSError(rc, "persistent server")
+        if done != seq:
+            return []
+        if st != self.B.GS_OK:
+            raise self.B.GSError(st, f"request {r.rid}")
+        L["busy"] = None
+        r.finish = now
+        if self.record:
+            r.phase = L["warm"].numpy().copy()
+            r.residual = float(L["R"][self.iters - 1])
+        if r.pinned is not None:
+            self.pool[r.n].append(r.pinned)
+            r.pinned = None
+        return [r]
+
+    def close(self):
+        if self.server:
+            self.B.gs_serve_destroy(self.server)
+            self.server = None
+
+
 def serve(arrivals: Sequence[Request], plans: Sequence[LanePlan], executor, clock=time.perf_counter,
           t0: Optional[float] = None, lookahead_s: float = 0.002, wait: str = "spin") -> Scheduler:
     """Run the request loop until every request in ``arrivals`` (sorted by
@@ -458,6 +564,28 @@ def run_service(rate_hz: float = 1000.0, seconds: float = 10.0, sizes=(512, 1024
     summ.update({
         "rate_hz": rate_hz, "seconds": seconds, "iters": iters, "launches": sch.launches,
         "lanes": [dataclasses.asdict(p) for p in plans], "graphs": ex.graph_ok, "wait": wait, "share_sms": share_sms,
+        "throughput_masks_per_s": len(sch.done) / max(max(r.finish for r in sch.done), 1e-9),
+    })
+    return summ, sch, ex
+
+
+def run_persistent_service(rate_hz: float = 1000.0, seconds: float = 10.0, sizes=(512, 1024), slots=(8, 8),
+                           iters: int = 30, seed: int = 0, record: bool = False, warmup_s: float = 0.5, grid: int = 0):
+    """Serve a Poisson stream through one persistent server on the whole
+    device (``grid`` blocks; 0: one per SM); returns (summary, scheduler,
+    executor)."""
+    from . import build_lib
+
+    build_lib.build()
+    ex = PersistentExecutor(sizes, slots, iters, grid=grid, record=record)
+    if warmup_s > 0:
+        serve(poisson_stream(rate_hz, warmup_s, sizes, seed + 1), ex.plans, ex)
+    reqs = poisson_stream(rate_hz, seconds, sizes, seed)
+    sch = serve(reqs, ex.plans, ex)
+    summ = latency_summary(sch.done)
+    summ.update({
+        "rate_hz": rate_hz, "seconds": seconds, "iters": iters, "mode": "persistent",
+        "slots": {str(n): s for n, s in zip(sizes, slots)}, "grid": ex.grid,
         "throughput_masks_per_s": len(sch.done) / max(max(r.finish for r in sch.done), 1e-9),
     })
     return summ, sch, ex
