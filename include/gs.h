@@ -541,7 +541,8 @@ int gs_stream_notify(void* stream, int fd);
  * intensity and start phase ([n][n] row-major FP32) are read by the server,
  * the final phase ([n][n], may alias phase_in) and r, g (K doubles each, or
  * NULL) written by it. The caller keeps them alive and leaves them alone until
- * gs_serve_poll reports the request done.
+ * gs_serve_poll reports the request done. A server, like a context, is not
+ * thread-safe: one host thread posts and polls.
  */
 typedef struct gs_server gs_server;
 
