@@ -521,6 +521,7 @@ def run_gpu(args):
         serving["persistent"] = persistent(args.serve_rate, half)
         serving["persistent"]["at_2x_rate"] = {k: v for k, v in persistent(2 * args.serve_rate, half).items()
                                                if k in ("requests", "p50_ms", "p99_ms", "max_ms", "rate_hz")}
+        serving["persistent"]["lone_requests"] = SV.persistent_tick_us()
 
     def timed(fn, steps):
         """Mean device ms of fn() over `steps` launches, L2 flushed before each."""

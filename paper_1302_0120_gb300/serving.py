@@ -591,6 +591,53 @@ def run_persistent_service(rate_hz: float = 1000.0, seconds: float = 10.0, sizes
     return summ, sch, ex
 
 
+def persistent_tick_us(sizes=(512, 1024), k_short: int = 10, k_long: int = 70, reps: int = 12, seed: int = 1):
+    """Time of one server iteration (tick) per size, from lone requests of
+    k_short and k_long iterations timed from post to observed completion:
+    (t_long - t_short) / (k_long - k_short); also the lone latencies (ms).
+    The server leaves before it returns."""
+    import statistics
+
+    import torch
+
+    from . import _binding as B
+    from . import build_lib
+    from . import synthetic as S
+
+    build_lib.build()
+    out = {}
+    srv = B.gs_serve_create(max(sizes), 1, 0, None)
+    try:
+        for n in sizes:
+            I = torch.from_numpy(S.spot_target(seed, n, n, 30, (0.5, 1.0))).pin_memory()
+            ph = torch.from_numpy(S.random_phase(seed, n, n)).pin_memory()
+            r = torch.zeros(k_long, dtype=torch.float64).pin_memory()
+            g = torch.zeros(k_long, dtype=torch.float64).pin_memory()
+            lat = {}
+            for K in (k_short, k_long):
+                ts = []
+                for _ in range(reps):
+                    t0 = time.perf_counter()
+                    rc, seq = B.gs_serve_submit(srv, 0, n, I.data_ptr(), ph.data_ptr(), K, ph.data_ptr(),
+                                                r.data_ptr(), g.data_ptr())
+                    if rc != B.GS_OK:
+                        raise B.GSError(rc, "gs_serve_submit")
+                    while True:
+                        rc, done, st = B.gs_serve_poll(srv, 0)
+                        if rc != B.GS_OK:
+                            raise B.GSError(rc, "gs_serve_poll")
+                        if done == seq:
+                            break
+                    ts.append((time.perf_counter() - t0) * 1e3)
+                    time.sleep(0.002)
+                lat[K] = statistics.median(ts[2:])
+            out[str(n)] = {"tick_us": round((lat[k_long] - lat[k_short]) / (k_long - k_short) * 1e3, 2),
+                           f"lone_ms_k{k_short}": round(lat[k_short], 4), f"lone_ms_k{k_long}": round(lat[k_long], 4)}
+    finally:
+        B.gs_serve_destroy(srv)
+    return out
+
+
 if __name__ == "__main__":
     import argparse
     import json
