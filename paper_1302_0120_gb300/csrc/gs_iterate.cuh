@@ -311,7 +311,7 @@ __device__ __forceinline__ float run_pass(const Params& p, int mb, int kind, boo
   };
   for (int cb0 = lo; cb0 < hi; cb0 += P) {
     const int cb = cb0 + slot;
-    if (cb >= hi) break;  // P = 2: no block for this slot in this round, nor later
+    if (cb >= hi) break;  // P = 2: no block left for this slot
     slot_sync();  // the previous round is done with this slot's staging buffers
     const bool from_m = (kind == kInitM);  // transform m itself (the target start)
     const unsigned par = (mphase & pbit) ? 1u : 0u;
