@@ -593,6 +593,13 @@ int gs_serve_stop(gs_server* s);
 /* gs_serve_grid -- blocks per launch of the server (0 for NULL). */
 int gs_serve_grid(const gs_server* s);
 
+/*
+ * gs_serve_test_tick_limit -- test hook: a launch leaves after `ticks`
+ * iterations (1..2^20; 2^20 by default) even with requests running, which the
+ * next launch resumes. Only while no launch runs; GS_EINVAL otherwise.
+ */
+int gs_serve_test_tick_limit(gs_server* s, int ticks);
+
 /* gs_serve_destroy -- stop, then free the server. NULL is a no-op. */
 void gs_serve_destroy(gs_server* s);
 

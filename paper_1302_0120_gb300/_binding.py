@@ -65,6 +65,7 @@ SIGNATURES = {
     "gs_serve_poll": (_c_int, [_vp, _c_int, ctypes.POINTER(_c_uint), ctypes.POINTER(_c_int)]),
     "gs_serve_stop": (_c_int, [_vp]),
     "gs_serve_grid": (_c_int, [_vp]),
+    "gs_serve_test_tick_limit": (_c_int, [_vp, _c_int]),
     "gs_serve_destroy": (None, [_vp]),
     "gs_adam_step": (_c_int, [_vp, _vp, _vp, _vp, ctypes.c_longlong, _vp, ctypes.c_float, ctypes.c_float,
                               ctypes.c_float, ctypes.c_float, _vp]),
@@ -338,6 +339,11 @@ def gs_serve_stop(srv: int) -> int:
 
 def gs_serve_grid(srv: int) -> int:
     return lib().gs_serve_grid(_vp(srv))
+
+
+def gs_serve_test_tick_limit(srv: int, ticks: int) -> int:
+    """Test hook: launches leave after `ticks` iterations; returns the status code."""
+    return lib().gs_serve_test_tick_limit(_vp(srv), int(ticks))
 
 
 def gs_serve_destroy(srv: int) -> None:

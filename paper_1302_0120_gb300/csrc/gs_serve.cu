@@ -148,6 +148,7 @@ int gs_serve_create(gs_server** out, int max_n, int slots, int grid, void* strea
   for (int k = 0; k < 3; ++k)
     s->sp.tw[k] = 8 + k <= L ? reinterpret_cast<const float2*>(s->ws + otw) + k * gsk::kStageTwiddleEntries : nullptr;
   s->sp.max_log = L;
+  s->sp.max_ticks = gsk::kServeMaxTicks;
   p.ones = reinterpret_cast<const float*>(s->ws + oones);
   p.bar = reinterpret_cast<unsigned*>(s->ws + obar);
   p.status = reinterpret_cast<int*>(s->ws + ostat);
@@ -237,6 +238,16 @@ int gs_serve_stop(gs_server* s) {
 }
 
 int gs_serve_grid(const gs_server* s) { return s ? s->grid : 0; }
+
+int gs_serve_test_tick_limit(gs_server* s, int ticks) {
+  if (s == nullptr || ticks < 1 || static_cast<unsigned>(ticks) > gsk::kServeMaxTicks) return GS_EINVAL;
+  if (load_i32(&s->table->running) != 0 || (s->launched && cudaEventQuery(s->ev) == cudaErrorNotReady)) {
+    cudaGetLastError();
+    return GS_EINVAL;  // only between launches
+  }
+  s->sp.max_ticks = static_cast<unsigned>(ticks);
+  return GS_OK;
+}
 
 void gs_serve_destroy(gs_server* s) {
   if (s == nullptr) return;

@@ -96,6 +96,7 @@ struct ServeParams {
   Params base;          // slot arrays (strided by mstride: the largest grid), barrier, status
   const float2* tw[3];  // stage twiddle tables for n = 256, 512, 1024 (null above the largest)
   int max_log;          // log2 of the largest grid
+  unsigned max_ticks;   // ticks per launch (kServeMaxTicks; lower only in tests)
   ServeTable* table;    // device address of the mapped request table
   ServeState* st;
   double* part;         // [3][kServeMaxSlots][grid]: A0, column and row partial sums
@@ -229,7 +230,7 @@ __device__ void serve_plan(const ServeParams& sp, const ServePlan* cur, ServePla
     for (int s = 0; s < S; ++s) pending = pending || (cur->row[s] == kRowLast);
   int stop = 0;
   if (!any) {
-    if (stop_asked() || ticks >= kServeMaxTicks) {
+    if (stop_asked() || ticks >= sp.max_ticks) {
       stop = 1;
     } else if (pending) {
       // an empty tick: it publishes, and its own planning waits
@@ -254,7 +255,7 @@ __device__ void serve_plan(const ServeParams& sp, const ServePlan* cur, ServePla
         if (!any) stop = 1;
       }
     }
-  } else if (ticks >= kServeMaxTicks) {
+  } else if (ticks >= sp.max_ticks) {
     stop = 1;  // leave between ticks; the slots resume in the next launch
   }
   if (lane == 0) {

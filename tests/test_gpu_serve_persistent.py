@@ -92,6 +92,30 @@ def test_requests_joining_mid_run_match_runs_alone(sizes):
         B.gs_serve_destroy(srv)
 
 
+def test_launches_leaving_mid_request_resume():
+    """Launches that leave every 5 ticks with requests running (the tick limit
+    that keeps the barrier counter in range, lowered by a test hook): the next
+    launch resumes the slots, and every result is the result of the run alone."""
+    from paper_1302_0120_gb300 import _binding as B
+    from paper_1302_0120_gb300 import build_lib
+
+    build_lib.build()
+    srv = B.gs_serve_create(512, 3, 0, None)
+    try:
+        assert B.gs_serve_test_tick_limit(srv, 5) == B.GS_OK
+        a, b, c = _Req(512, 11, 23), _Req(256, 12, 17), _Req(512, 13, 9)
+        assert a.submit(B, srv, 0) == B.GS_OK
+        assert b.submit(B, srv, 1) == B.GS_OK
+        assert c.submit(B, srv, 2) == B.GS_OK
+        for req, slot in ((a, 0), (b, 1), (c, 2)):
+            assert _wait(B, srv, slot, req.seq) == B.GS_OK
+        assert B.gs_serve_stop(srv) == B.GS_OK
+        for req in (a, b, c):
+            _check_alone(req)
+    finally:
+        B.gs_serve_destroy(srv)
+
+
 def test_bad_target_busy_slot_and_idle_relaunch():
     from paper_1302_0120_gb300 import _binding as B
     from paper_1302_0120_gb300 import build_lib
