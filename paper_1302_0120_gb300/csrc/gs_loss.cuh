@@ -33,6 +33,13 @@ constexpr float kTolDark = 3e-4f;  // t_d, Sec. II
 // reduced target statistics of a prepared target (flag, sum I, max I).
 enum LossRow { kRowFlag = 0, kRowSumI = 1, kRowMaxI = 2, kRowLoss = 3, kRowEl = 4, kRowEd = 5, kRowStaged = 6 };
 
+// Record a failure: the first one also adds the abort bit to the barrier
+// counter, which releases every waiting block (as fail() in gs_common.cuh).
+static __device__ void loss_fail(const LossParams& p, int code) {
+  atomicCAS(p.status, 0, code);
+  if (atomicExch(p.abort_flag, 1) == 0) atomicAdd(p.bar, kAbortBit);
+}
+
 // Grid barrier for the loss kernel (same protocol as grid_sync).
 static __device__ bool loss_sync(const LossParams& p, unsigned& target, Shared& sh) {
   __syncthreads();
@@ -42,21 +49,21 @@ static __device__ bool loss_sync(const LossParams& p, unsigned& target, Shared& 
     asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(p.bar) : "memory");
     unsigned spins = 0;
     unsigned long long t0 = 0;
-    while (static_cast<int>(ld_acquire_gpu(p.bar) - target) < 0) {
+    unsigned v;
+    while (static_cast<int>((v = ld_acquire_gpu(p.bar)) - target) < 0) {
       ++spins;
       if ((spins & 255u) == 0) {
         const unsigned long long now = global_ns();
         if (t0 == 0) t0 = now;
         if (now - t0 > kBarrierTimeoutNs || spins > kMaxSpins) {
           ok = 0;
-          atomicCAS(p.status, 0, GS_ETIMEOUT);
-          atomicExch(p.abort_flag, 1);
+          loss_fail(p, GS_ETIMEOUT);
           break;
         }
       }
     }
     asm volatile("fence.proxy.async.global;" ::: "memory");
-    if (ok && *reinterpret_cast<volatile int*>(p.abort_flag) != 0) ok = 0;
+    if (ok && (v & kAbortBit) != 0) ok = 0;  // a block failed in this launch
     sh.flag = ok;
   }
   __syncthreads();
@@ -197,7 +204,9 @@ __global__ void __launch_bounds__(kThreads, 1) gs_loss_kernel(const LossParams p
         for (int i = 0; i < 32; ++i) cp_async4(&su[T * i].y, pp + T * i);
       }
       cp_async_wait_all();
-#pragma unroll 1
+      // four copies of sincosf: independent work for the scheduler, while
+      // the code stays small (instruction fetch is this kernel's top stall)
+#pragma unroll 4
       for (int i = 0; i < 32; ++i) {
         float s, c;
         const float2 fa = su[T * i];
@@ -275,8 +284,7 @@ __global__ void __launch_bounds__(kThreads, 1) gs_loss_kernel(const LossParams p
       const bool landed = mbar_wait_bounded(&sh.mbar, mphase);
       mphase ^= 1u;
       if (!landed) {
-        atomicCAS(p.status, 0, GS_ETIMEOUT);
-        atomicExch(p.abort_flag, 1);
+        loss_fail(p, GS_ETIMEOUT);
       } else if (threadIdx.x == 0) {
         sh.pending = 0;
       }
