@@ -130,6 +130,23 @@ def test_noalloc_validates_before_cuda(lib):
     assert lib.gs_run_noalloc(64, 64, 1, None, None, None, -1, None, None, None, None) == B.GS_EINVAL
 
 
+def test_serve_validates_before_cuda(lib):
+    """The persistent server's arguments are checked before any CUDA call."""
+    h = ctypes.c_void_p()
+    assert lib.gs_serve_create(None, 512, 4, 0, None) == B.GS_EINVAL
+    for n, slots, grid in ((300, 4, 0), (128, 4, 0), (2048, 4, 0), (512, 0, 0), (512, 17, 0), (512, 4, -1)):
+        assert lib.gs_serve_create(ctypes.byref(h), n, slots, grid, None) == B.GS_EINVAL, (n, slots, grid)
+        assert h.value is None
+    seq = ctypes.c_uint(0)
+    d, st = ctypes.c_uint(0), ctypes.c_int(0)
+    assert lib.gs_serve_submit(None, 0, 512, None, None, 30, None, None, None, ctypes.byref(seq)) == B.GS_EINVAL
+    assert lib.gs_serve_poll(None, 0, ctypes.byref(d), ctypes.byref(st)) == B.GS_EINVAL
+    assert lib.gs_serve_stop(None) == B.GS_EINVAL
+    assert lib.gs_serve_grid(None) == 0
+    assert lib.gs_serve_test_tick_limit(None, 5) == B.GS_EINVAL
+    lib.gs_serve_destroy(None)  # a no-op
+
+
 def test_missing_library_fails_loudly(monkeypatch, tmp_path):
     monkeypatch.setattr(B, "_lib", None)
     monkeypatch.setattr(B, "LIB_PATH", str(tmp_path / "nope.so"))
