@@ -25,12 +25,11 @@ LIB_PATH = os.path.join(OUT_DIR, LIB_NAME)
 # log2(nx) so that the 64 size instantiations build in parallel.
 SOURCES = [("gs_api.cu", "gs_api", []), ("gs_launch.cu", "gs_launch", []), ("gs_noalloc.cu", "gs_noalloc", []), ("gs_loss_inst.cu", "gs_loss_inst", []), ("gs_tc_inst.cu", "gs_tc_inst", []), ("gs_tc5_inst.cu", "gs_tc5_inst", []),
     ("gs_general_inst.cu", "gs_general_inst", []),
-    ("gs_rg_inst.cu", "gs_rg_inst", []),
     ("gs_serve.cu", "gs_serve", []),
     ("gs_mixed_inst.cu", "gs_mixed_inst", []), ("gs_adam.cu", "gs_adam", []), ("gs_peak.cu", "gs_peak", []), ("gs_notify.cu", "gs_notify", []),
     ("gs_small_inst.cu", "gs_small_inst", [])] + [
     ("gs_inst.cu", f"gs_inst_lx{lx}", [f"-DGS_LX={lx}"]) for lx in range(5, 13)
-]
+] + [("gs_rg_inst.cu", f"gs_rg_inst_{nx}", [f"-DGS_RG_NX={nx}"]) for nx in (600, 768, 800, 1024)]
 GENCODE = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = [
     "-O3",

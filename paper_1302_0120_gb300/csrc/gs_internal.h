@@ -96,13 +96,18 @@ inline __host__ __device__ bool uses_general(int nx, int ny) {
 
 // Register-resident general-grid kernel (gs_rg.cuh): sides n = T V with a
 // line in one warp (T lanes of V points, T, V <= 32). rg_threads(n) is T for
-// the sides it serves (600 = 24 x 25, 800 = 32 x 25), else 0; a grid whose two
-// sides are both served runs there, any other side that is not a power of
-// two on the shared-memory general kernel. Kernel templates take such a side
-// itself in place of log2 nx (is_rg_side).
-inline __host__ __device__ constexpr int rg_threads(int n) { return n == 600 ? 24 : n == 800 ? 32 : 0; }
+// the sides it serves (600 = 24 x 25, 768 = 32 x 24, 800 = 32 x 25,
+// 1024 = 32 x 32), else 0; a grid whose two sides are both served, and not
+// both powers of two, runs there (800 x 600, 1024 x 768, ...); any other grid
+// with a side that is not a power of two on the shared-memory general kernel.
+// Kernel templates take such a side itself in place of log2 nx (is_rg_side).
+inline __host__ __device__ constexpr int rg_threads(int n) {
+  return n == 600 ? 24 : (n == 768 || n == 800 || n == 1024) ? 32 : 0;
+}
 inline __host__ __device__ constexpr bool is_rg_side(int lx) { return lx >= 32; }
-inline __host__ __device__ bool uses_rg(int nx, int ny) { return rg_threads(nx) > 0 && rg_threads(ny) > 0; }
+inline __host__ __device__ bool uses_rg(int nx, int ny) {
+  return rg_threads(nx) > 0 && rg_threads(ny) > 0 && !(nx == 1024 && ny == 1024);
+}
 
 // Sides of the general kernel: 5-smooth (2^a 3^b 5^c) in [8, kMaxGeneralSide].
 constexpr int kMaxGeneralSide = 1536;
@@ -137,6 +142,12 @@ const void* iterate_kernel_general();
 // W_n^{q j} at [j V + q].
 const void* iterate_kernel_rg(int nx, int ny);
 size_t rg_smem_bytes(int nx, int ny);
+// The kernels and shared memory for one row length, from the object of
+// gs_rg_inst.cu compiled for it.
+template <int NX>
+const void* iterate_kernel_rg_nx(int ny);
+template <int NX>
+size_t rg_smem_bytes_nx(int ny);
 // Stage twiddle tables of a power-of-two length n (the layout stage_c reads),
 // kStageTwiddleEntries entries, rounded once from double (gs_api.cu).
 constexpr int kStageTwiddleEntries = 31 * 32 + 31 * 1024;

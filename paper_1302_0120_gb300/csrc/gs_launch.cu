@@ -42,6 +42,35 @@ extern template const void* iterate_kernel_lx<10>(int);
 extern template const void* iterate_kernel_lx<11>(int);
 extern template const void* iterate_kernel_lx<12>(int);
 
+extern template const void* iterate_kernel_rg_nx<600>(int);
+extern template const void* iterate_kernel_rg_nx<768>(int);
+extern template const void* iterate_kernel_rg_nx<800>(int);
+extern template const void* iterate_kernel_rg_nx<1024>(int);
+extern template size_t rg_smem_bytes_nx<600>(int);
+extern template size_t rg_smem_bytes_nx<768>(int);
+extern template size_t rg_smem_bytes_nx<800>(int);
+extern template size_t rg_smem_bytes_nx<1024>(int);
+
+const void* iterate_kernel_rg(int nx, int ny) {
+  switch (nx) {
+    case 600: return iterate_kernel_rg_nx<600>(ny);
+    case 768: return iterate_kernel_rg_nx<768>(ny);
+    case 800: return iterate_kernel_rg_nx<800>(ny);
+    case 1024: return iterate_kernel_rg_nx<1024>(ny);
+    default: return nullptr;
+  }
+}
+
+size_t rg_smem_bytes(int nx, int ny) {
+  switch (nx) {
+    case 600: return rg_smem_bytes_nx<600>(ny);
+    case 768: return rg_smem_bytes_nx<768>(ny);
+    case 800: return rg_smem_bytes_nx<800>(ny);
+    case 1024: return rg_smem_bytes_nx<1024>(ny);
+    default: return 0;
+  }
+}
+
 static int log2_exact(int n) {
   int l = 0;
   while ((1 << l) < n) ++l;

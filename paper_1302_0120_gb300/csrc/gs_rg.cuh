@@ -1,6 +1,7 @@
-// gs_rg.cuh -- register-resident passes for grids whose sides are not powers
-// of two but factor as n = T V with T, V <= 32 (600 = 24 x 25, 800 = 32 x 25:
-// the 800 x 600 SLM of Sec. V). Other 5-smooth sides keep the shared-memory
+// gs_rg.cuh -- register-resident passes for grids whose sides factor as
+// n = T V with T, V <= 32 and are not both powers of two (600 = 24 x 25,
+// 768 = 32 x 24, 800 = 32 x 25, 1024 = 32 x 32: the 800 x 600 SLM of Sec. V,
+// the 1024 x 768 format). Other 5-smooth sides keep the shared-memory
 // Stockham passes of gs_general.cuh.
 //
 // One warp holds one line (row or column) from load to store. A length-n

@@ -1,6 +1,15 @@
-// gs_rg_inst.cu -- the register-resident iteration kernels for grids whose
-// sides are 600 or 800 (gs_rg.cuh), one per pair of sides.
+// gs_rg_inst.cu -- the register-resident iteration kernels (gs_rg.cuh), one
+// per pair of sides.
+//
+// Compiled once per row length nx in {600, 768, 800, 1024} with
+// -DGS_RG_NX=<nx>; each object provides iterate_kernel_rg_nx<GS_RG_NX>(ny)
+// and rg_smem_bytes_nx<GS_RG_NX>(ny) for every column length ny of the same
+// set (1024 x 1024 excepted: it runs on the power-of-two kernel).
 #include "gs_iterate.cuh"
+
+#ifndef GS_RG_NX
+#error "GS_RG_NX must be defined (the row length)"
+#endif
 
 namespace gsk {
 
@@ -13,20 +22,30 @@ __global__ void __launch_bounds__(kThreads, 1) gs_iterate_rg(const Params p) {
   iterate_class<NX, NY, false>(p, sh, smem, none, NoTc{});
 }
 
-const void* iterate_kernel_rg(int nx, int ny) {
-  if (nx == 800 && ny == 600) return reinterpret_cast<const void*>(gs_iterate_rg<800, 600>);
-  if (nx == 600 && ny == 800) return reinterpret_cast<const void*>(gs_iterate_rg<600, 800>);
-  if (nx == 800 && ny == 800) return reinterpret_cast<const void*>(gs_iterate_rg<800, 800>);
-  if (nx == 600 && ny == 600) return reinterpret_cast<const void*>(gs_iterate_rg<600, 600>);
-  return nullptr;
+template <>
+const void* iterate_kernel_rg_nx<GS_RG_NX>(int ny) {
+  switch (ny) {
+    case 600: return reinterpret_cast<const void*>(gs_iterate_rg<GS_RG_NX, 600>);
+    case 768: return reinterpret_cast<const void*>(gs_iterate_rg<GS_RG_NX, 768>);
+    case 800: return reinterpret_cast<const void*>(gs_iterate_rg<GS_RG_NX, 800>);
+#if GS_RG_NX != 1024
+    case 1024: return reinterpret_cast<const void*>(gs_iterate_rg<GS_RG_NX, 1024>);
+#endif
+    default: return nullptr;
+  }
 }
 
-size_t rg_smem_bytes(int nx, int ny) {
-  if (nx == 800 && ny == 600) return RgSmem<800, 600>::kBytes;
-  if (nx == 600 && ny == 800) return RgSmem<600, 800>::kBytes;
-  if (nx == 800 && ny == 800) return RgSmem<800, 800>::kBytes;
-  if (nx == 600 && ny == 600) return RgSmem<600, 600>::kBytes;
-  return 0;
+template <>
+size_t rg_smem_bytes_nx<GS_RG_NX>(int ny) {
+  switch (ny) {
+    case 600: return RgSmem<GS_RG_NX, 600>::kBytes;
+    case 768: return RgSmem<GS_RG_NX, 768>::kBytes;
+    case 800: return RgSmem<GS_RG_NX, 800>::kBytes;
+#if GS_RG_NX != 1024
+    case 1024: return RgSmem<GS_RG_NX, 1024>::kBytes;
+#endif
+    default: return 0;
+  }
 }
 
 }  // namespace gsk

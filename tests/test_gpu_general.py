@@ -21,6 +21,10 @@ pytestmark = pytest.mark.gpu
         (800, 600, 10, 30),   # the other sides of the register-resident kernel
         (800, 800, 8, 30),
         (600, 600, 8, 30),
+        (768, 1024, 10, 30),  # the XGA SLM (1024 x 768), and 768 x 1024
+        (1024, 768, 8, 30),
+        (768, 768, 6, 20),
+        (1024, 600, 6, 20),
         (160, 96, 20, 10),
         (36, 75, 15, 4),      # 75 columns: a ragged last group of 3
         (512, 800, 10, 30),   # one side a power of two
@@ -52,12 +56,12 @@ def test_parity_grid_shares(grid):
     check_run(I, phi0, 6, grid=grid, one_step_at=(0,))
 
 
-@pytest.mark.parametrize("grid", [1, 7, 151])
-def test_register_kernel_grid_shares(grid):
-    """The register-resident kernel (sides 600 and 800) with ragged shares of
-    rows and column blocks over the blocks, several rounds per block."""
-    I = S.spot_target(5, 600, 800, 30, (0.5, 1.0))
-    phi0 = S.random_phase(5, 600, 800)
+@pytest.mark.parametrize("ny,nx,grid", [(600, 800, 1), (600, 800, 7), (600, 800, 151), (768, 1024, 7)])
+def test_register_kernel_grid_shares(ny, nx, grid):
+    """The register-resident kernel with ragged shares of rows and column
+    blocks over the blocks, several rounds per block."""
+    I = S.spot_target(5, ny, nx, 30, (0.5, 1.0))
+    phi0 = S.random_phase(5, ny, nx)
     check_run(I, phi0, 4, grid=grid, one_step_at=(0, 3))
 
 
