@@ -97,11 +97,13 @@ Layout make_layout(int nx, int ny, int max_batch) {
   L.guard[L.nguard++] = o; o += kGuardBytes;
   L.ones = o;       o = align_up(o + 4096 * sizeof(float));
   L.guard[L.nguard++] = o; o += kGuardBytes;
-  L.bar = o;        o = align_up(o + sizeof(unsigned));
+  // the barrier counter and the abort word side by side: one memset clears
+  // both before the first launch of a run
+  L.bar = o;
+  L.abort_flag = o + sizeof(unsigned);
+  o = align_up(o + 2 * sizeof(unsigned));
   L.guard[L.nguard++] = o; o += kGuardBytes;
   L.status = o;     o = align_up(o + sizeof(int));
-  L.guard[L.nguard++] = o; o += kGuardBytes;
-  L.abort_flag = o; o = align_up(o + sizeof(int));
   L.guard[L.nguard++] = o; o += kGuardBytes;
   L.mask_flags = o; o = align_up(o + gsk::kMaxBatch * sizeof(int));
   L.guard[L.nguard++] = o; o += kGuardBytes;
@@ -453,10 +455,6 @@ int gs_run_batched(gs_ctx* c, int batch, const float* target_intensity, const fl
     }
     return GS_OK;
   }
-  if (cudaMemsetAsync(p.abort_flag, 0, sizeof(int), c->stream) != cudaSuccess) {
-    cudaGetLastError();
-    return GS_ECUDA;
-  }
   int it0 = 0;
   do {
     int it1 = it0 + gsk::kMaxIterPerLaunch;
@@ -465,7 +463,9 @@ int gs_run_batched(gs_ctx* c, int batch, const float* target_intensity, const fl
     p.it1 = it1;
     p.do_init = (it0 == 0) ? 1 : 0;
     p.do_final = (it1 == iters) ? 1 : 0;
-    if (cudaMemsetAsync(p.bar, 0, sizeof(unsigned), c->stream) != cudaSuccess ||
+    // the barrier counter before every launch; the abort word (next to it)
+    // before the first one only, so that a failed launch stops the later ones
+    if (cudaMemsetAsync(p.bar, 0, (it0 == 0 ? 2 : 1) * sizeof(unsigned), c->stream) != cudaSuccess ||
         gsk::launch_iterations(p, grid, c->stream) != cudaSuccess) {
       cudaGetLastError();
       return GS_ECUDA;
@@ -614,10 +614,6 @@ int gs_run_mixed(gs_ctx* c, const int* batch, const float* const* target_intensi
     p.r_out = residual_out ? residual_out[k] : nullptr;
     p.g_out = object_gap_out ? object_gap_out[k] : nullptr;
   }
-  if (cudaMemsetAsync(mp.cls[0].abort_flag, 0, sizeof(int), c->stream) != cudaSuccess) {
-    cudaGetLastError();
-    return GS_ECUDA;
-  }
   int it0 = 0;
   do {
     int it1 = it0 + gsk::kMaxIterPerLaunch;
@@ -628,7 +624,8 @@ int gs_run_mixed(gs_ctx* c, const int* batch, const float* const* target_intensi
       mp.cls[k].do_init = (it0 == 0) ? 1 : 0;
       mp.cls[k].do_final = (it1 == iters) ? 1 : 0;
     }
-    if (cudaMemsetAsync(mp.cls[0].bar, 0, sizeof(unsigned), c->stream) != cudaSuccess ||
+    // counter before every launch, abort word (next to it) before the first
+    if (cudaMemsetAsync(mp.cls[0].bar, 0, (it0 == 0 ? 2 : 1) * sizeof(unsigned), c->stream) != cudaSuccess ||
         gsk::launch_mixed(mp, grid, c->tc_mode, c->stream) != cudaSuccess) {
       cudaGetLastError();
       return GS_ECUDA;
@@ -738,8 +735,7 @@ int enqueue_loss(gs_ctx* c, const float* target_intensity, const float* phase, d
   p.status = at<int>(c, c->L.status);
   p.abort_flag = at<int>(c, c->L.abort_flag);
   p.inv_n = 1.0f / static_cast<float>(static_cast<double>(c->nx) * c->ny);
-  if (cudaMemsetAsync(p.bar, 0, sizeof(unsigned), c->stream) != cudaSuccess ||
-      cudaMemsetAsync(p.abort_flag, 0, sizeof(int), c->stream) != cudaSuccess ||
+  if (cudaMemsetAsync(p.bar, 0, 2 * sizeof(unsigned), c->stream) != cudaSuccess ||  // counter and abort word
       gsk::launch_loss(p, choose_grid(c), c->stream) != cudaSuccess) {
     cudaGetLastError();
     return GS_ECUDA;
