@@ -414,6 +414,22 @@ int gs_loss_prepare(gs_ctx* c, const float* target_intensity);
 int gs_loss_grad_prepared(gs_ctx* c, const float* phase, double* loss_out, float* grad_out);
 
 /*
+ * gs_loss_adam_prepared -- one step of the phase optimiser in one launch:
+ * gs_loss_grad_prepared followed by gs_adam_step, with the update applied in
+ * the pass that forms the gradient (which is not stored).
+ *   phase      device, float [n][n]: the phase phi of L(phi), updated in place.
+ *   m, v       device, float [n][n]: the running moments of gs_adam_step.
+ *   state      device, int [2] as in gs_adam_step (zero before the first step).
+ *   lr, beta1, beta2, eps   as in gs_adam_step.
+ *   loss_out   device, double [1]: L(phi) before the update.
+ * The update is that of gs_adam_step with the gradient of
+ * gs_loss_grad_prepared. Asynchronous. Returns GS_EINVAL as
+ * gs_loss_grad_prepared and gs_adam_step do; GS_ECUDA if the launch fails.
+ */
+int gs_loss_adam_prepared(gs_ctx* c, float* phase, float* m, float* v, int* state, float lr, float beta1,
+                          float beta2, float eps, double* loss_out);
+
+/*
  * gs_physical_error -- the physical error of a phase mask, Eq. (phys-error).
  *
  * Operation: for the field u = p exp(i phase) on the SLM (p from

@@ -712,9 +712,27 @@ int gs_run_host(gs_ctx* c, const float* target_intensity, const float* phase_in,
 
 namespace {
 
+struct AdamArgs {
+  float* phase;
+  float* m;
+  float* v;
+  int* state;
+  float lr, beta1, beta2, eps;
+};
+
 int enqueue_loss(gs_ctx* c, const float* target_intensity, const float* phase, double* loss_out, float* grad_out,
-                 double* phys_out, int mode = gsk::kLossFused) {
+                 double* phys_out, int mode = gsk::kLossFused, const AdamArgs* adam = nullptr) {
   gsk::LossParams p{};
+  if (adam != nullptr) {
+    p.phase = adam->phase;
+    p.m = adam->m;
+    p.v = adam->v;
+    p.state = adam->state;
+    p.lr = adam->lr;
+    p.beta1 = adam->beta1;
+    p.beta2 = adam->beta2;
+    p.eps = adam->eps;
+  }
   p.mode = mode;
   // the fused and prepare launches stage their target over the previous one
   c->loss_prepared = (mode == gsk::kLossPrepare) || (mode == gsk::kLossStep && c->loss_prepared);
@@ -763,6 +781,16 @@ int gs_loss_grad_prepared(gs_ctx* c, const float* phase, double* loss_out, float
       gsk::uses_general(c->nx, c->ny) || !c->loss_prepared)
     return GS_EINVAL;
   return enqueue_loss(c, nullptr, phase, loss_out, grad_out, nullptr, gsk::kLossStep);
+}
+
+int gs_loss_adam_prepared(gs_ctx* c, float* phase, float* m, float* v, int* state, float lr, float beta1,
+                          float beta2, float eps, double* loss_out) {
+  if (c == nullptr || c->mixed || phase == nullptr || m == nullptr || v == nullptr || state == nullptr ||
+      loss_out == nullptr || c->nx != c->ny || gsk::uses_general(c->nx, c->ny) || !c->loss_prepared ||
+      !(lr > 0.f) || !(beta1 >= 0.f && beta1 < 1.f) || !(beta2 >= 0.f && beta2 < 1.f) || !(eps > 0.f))
+    return GS_EINVAL;
+  const AdamArgs a{phase, m, v, state, lr, beta1, beta2, eps};
+  return enqueue_loss(c, nullptr, phase, loss_out, nullptr, nullptr, gsk::kLossStep, &a);
 }
 
 int gs_physical_error(gs_ctx* c, const float* target_intensity, const float* phase, double* error_out) {

@@ -185,6 +185,14 @@ struct LossParams {
   int* abort_flag;
   float inv_n;             // 1/N
   int mode;                // LossMode: fused, prepare the target, or a step on the prepared target
+  // A step with the Adam update fused into the gradient pass (grad is then
+  // null): phase (the same array as phi) is updated in place with the running
+  // moments m, v; state[0] counts the steps done, state[1] the blocks done.
+  float* phase;
+  float* m;
+  float* v;
+  int* state;
+  float lr, beta1, beta2, eps;
 };
 
 cudaError_t launch_loss(const LossParams& p, int grid, cudaStream_t s);

@@ -261,7 +261,8 @@ __global__ void __launch_bounds__(kThreads, 1) gs_loss_kernel(const LossParams p
 
   // Pass 2 (columns): y = DFT_y(B) = F x; r = |y|^2/N - I; loss partial;
   // B = swap(IDFT_y(r y)) for the adjoint.
-  const bool want_grad = p.grad != nullptr;
+  const bool adam = p.m != nullptr;  // the Adam update in place of the gradient output
+  const bool want_grad = p.grad != nullptr || adam;  // the adjoint passes
   const bool want_phys = p.phys != nullptr;
   float acc = 0.f, acc_l = 0.f, acc_d = 0.f;  // this thread's lines, FP32
   {
@@ -376,7 +377,19 @@ __global__ void __launch_bounds__(kThreads, 1) gs_loss_kernel(const LossParams p
   }
   if (!want_grad) return;
 
-  // Pass 3 (rows): N z = IDFT_x(B), grad = 4 Im(conj(x) z) with x = exp(i phi).
+  // Pass 3 (rows): N z = IDFT_x(B), grad = 4 Im(conj(x) z) with x = exp(i phi);
+  // with the fused update, the Adam step of gs_adam_step on every element
+  // instead of its gradient output (the phase of a row is read into shared
+  // memory before the thread that owns each element updates it).
+  int adam_t = 0;
+  float adam_step = 0.f, adam_rb2 = 0.f;
+  if (adam) {
+    adam_t = p.state[0] + 1;
+    const float b1 = 1.f - powf(p.beta1, static_cast<float>(adam_t));
+    const float b2 = 1.f - powf(p.beta2, static_cast<float>(adam_t));
+    adam_step = p.lr / b1;
+    adam_rb2 = 1.f / sqrtf(b2);
+  }
   {
     const int lo = split(b, gridDim.x, N);
     const int hi = split(b + 1, gridDim.x, N);
@@ -392,14 +405,26 @@ __global__ void __launch_bounds__(kThreads, 1) gs_loss_kernel(const LossParams p
       // (free in this pass), in flight behind the transform
       float* sph = reinterpret_cast<float*>(blk) + threadIdx.x;
       float* spp = sph + 32 * kThreads;
+      // the fused update with p = 1: the row's moments too, into the laser
+      // amplitude's buffer and the staged target's (free in this pass)
+      float* const smm = (adam && !p.p_slm) ? spp : nullptr;
+      float* const smv = (adam && !p.p_slm) ? its + threadIdx.x : nullptr;
       {
-        const float* ph = p.phi + static_cast<size_t>(ridx) * N + t;
+        const size_t r0 = static_cast<size_t>(ridx) * N + t;
+        const float* ph = p.phi + r0;
 #pragma unroll
         for (int i = 0; i < 32; ++i) cp_async4(sph + kThreads * i, ph + T * i);
         if (p.p_slm) {
-          const float* pp = p.p_slm + static_cast<size_t>(ridx) * N + t;
+          const float* pp = p.p_slm + r0;
 #pragma unroll
           for (int i = 0; i < 32; ++i) cp_async4(spp + kThreads * i, pp + T * i);
+        }
+        if (smm != nullptr) {
+#pragma unroll
+          for (int i = 0; i < 32; ++i) {
+            cp_async4(smm + kThreads * i, p.m + r0 + T * i);
+            cp_async4(smv + kThreads * i, p.v + r0 + T * i);
+          }
         }
       }
       group_fft<LN>(v, grp, stw);  // = swap(N z)
@@ -408,7 +433,7 @@ __global__ void __launch_bounds__(kThreads, 1) gs_loss_kernel(const LossParams p
 #pragma unroll
       for (int i = 0; i < 32; ++i) su[T * i] = v[i];
       cp_async_wait_all();
-      if (valid) {
+      if (valid && !adam) {
         float* gr = p.grad + static_cast<size_t>(idx) * N + t;
 #pragma unroll 1
         for (int i = 0; i < 32; ++i) {
@@ -418,8 +443,36 @@ __global__ void __launch_bounds__(kThreads, 1) gs_loss_kernel(const LossParams p
           const float2 w = su[T * i];
           gr[T * i] = scale * a * (c * w.x - s * w.y);
         }
+      } else if (valid) {
+        const size_t e0 = static_cast<size_t>(idx) * N + t;
+#pragma unroll 4
+        for (int i = 0; i < 32; ++i) {
+          float s, c;
+          sincosf(sph[kThreads * i], &s, &c);
+          const float a = p.p_slm ? spp[kThreads * i] : 1.f;
+          const float2 w = su[T * i];
+          const float g = scale * a * (c * w.x - s * w.y);
+          const size_t e = e0 + T * i;
+          const float m0 = smm ? smm[kThreads * i] : p.m[e];
+          const float v0 = smv ? smv[kThreads * i] : p.v[e];
+          const float mi = fmaf(p.beta1, m0, (1.f - p.beta1) * g);
+          const float vi = fmaf(p.beta2, v0, (1.f - p.beta2) * g * g);
+          p.m[e] = mi;
+          p.v[e] = vi;
+          p.phase[e] = sph[kThreads * i] - adam_step * mi / (sqrtf(vi) * adam_rb2 + p.eps);
+        }
       }
       grp.sync();
+    }
+  }
+  if (adam) {  // the last block to finish advances the step count (every block has read it)
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      __threadfence();
+      if (atomicAdd(p.state + 1, 1) == static_cast<int>(gridDim.x) - 1) {
+        p.state[0] = adam_t;
+        p.state[1] = 0;
+      }
     }
   }
 }

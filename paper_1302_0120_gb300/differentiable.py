@@ -131,9 +131,10 @@ def optimize_phase(target, phase0, steps: int = 200, lr: float = 0.05, betas=(0.
     before step k (and the final loss last).
 
     With ``graph`` (the default) the target is staged once (gs_loss_prepare)
-    and one step -- the loss-and-gradient launch on the staged target and the
-    library's Adam update (gs_adam_step) -- is captured once as a CUDA graph
-    and replayed after three eager steps; the context then needs its own
+    and one step -- a single launch forming the loss and the gradient on the
+    staged target and applying the Adam update of gs_adam_step in place
+    (gs_loss_adam_prepared) -- is captured once as a CUDA graph and replayed
+    after three eager steps; the context then needs its own
     (non-default) stream, and one is created when ``lctx`` is None. Otherwise
     every step goes through the autograd function above and torch's Adam."""
     import torch
@@ -146,7 +147,6 @@ def optimize_phase(target, phase0, steps: int = 200, lr: float = 0.05, betas=(0.
     s.wait_stream(torch.cuda.current_stream())
     with torch.cuda.stream(s):
         phase = phase0.detach().clone()
-        grad = torch.zeros_like(phase)
         m = torch.zeros_like(phase)
         v = torch.zeros_like(phase)
         state = torch.zeros(2, dtype=torch.int32, device=phase.device)
@@ -158,14 +158,11 @@ def optimize_phase(target, phase0, steps: int = 200, lr: float = 0.05, betas=(0.
         if rc != B.GS_OK:
             raise B.GSError(rc, "gs_loss_prepare")
 
-        def step():
-            rc = B.gs_loss_grad_prepared(lctx.handle, phase.data_ptr(), loss.data_ptr(), grad.data_ptr())
+        def step():  # loss, gradient and Adam update in one launch
+            rc = B.gs_loss_adam_prepared(lctx.handle, phase.data_ptr(), m.data_ptr(), v.data_ptr(), state.data_ptr(),
+                                         lr, betas[0], betas[1], eps, loss.data_ptr())
             if rc != B.GS_OK:
-                raise B.GSError(rc, "gs_loss_grad_prepared")
-            rc = B.gs_adam_step(phase.data_ptr(), grad.data_ptr(), m.data_ptr(), v.data_ptr(), phase.numel(),
-                                state.data_ptr(), lr, betas[0], betas[1], eps, s.cuda_stream)
-            if rc != B.GS_OK:
-                raise B.GSError(rc, "gs_adam_step")
+                raise B.GSError(rc, "gs_loss_adam_prepared")
 
         warm = 3
         for k in range(warm):

@@ -157,6 +157,48 @@ def test_adam_step_matches_torch_adam():
     assert torch.allclose(ours, ref.detach(), rtol=1e-5, atol=1e-6)
 
 
+@pytest.mark.parametrize("n", [256, 1024])
+def test_fused_adam_step_matches_separate_launches(n):
+    """gs_loss_adam_prepared (the update in the gradient pass) against
+    gs_loss_grad_prepared followed by gs_adam_step, over six steps from the
+    same start: the same losses, moments, step count and phases."""
+    import torch
+
+    from paper_1302_0120_gb300 import _binding as B
+    from paper_1302_0120_gb300 import build_lib
+
+    build_lib.build()
+    I = torch.from_numpy(normalized_target(5, n, 40)).cuda()
+    phi0 = torch.from_numpy(S.random_phase(6, n, n)).cuda()
+    h1, h2 = B.gs_create(n, n), B.gs_create(n, n)
+    try:
+        assert B.gs_loss_prepare(h1, I.data_ptr()) == 0 and B.gs_loss_prepare(h2, I.data_ptr()) == 0
+        ph1, ph2 = phi0.clone(), phi0.clone()
+        m1, v1, m2, v2 = (torch.zeros_like(phi0) for _ in range(4))
+        st1 = torch.zeros(2, dtype=torch.int32, device="cuda")
+        st2 = torch.zeros(2, dtype=torch.int32, device="cuda")
+        l1 = torch.zeros(6, dtype=torch.float64, device="cuda")
+        l2 = torch.zeros(6, dtype=torch.float64, device="cuda")
+        g = torch.empty_like(phi0)
+        stream = torch.cuda.current_stream().cuda_stream
+        for k in range(6):
+            assert B.gs_loss_adam_prepared(h1, ph1.data_ptr(), m1.data_ptr(), v1.data_ptr(), st1.data_ptr(),
+                                           0.05, 0.9, 0.999, 1e-8, l1[k:].data_ptr()) == 0
+            assert B.gs_loss_grad_prepared(h2, ph2.data_ptr(), l2[k:].data_ptr(), g.data_ptr()) == 0
+            assert B.gs_adam_step(ph2.data_ptr(), g.data_ptr(), m2.data_ptr(), v2.data_ptr(), n * n, st2.data_ptr(),
+                                  0.05, 0.9, 0.999, 1e-8, stream) == 0
+        torch.cuda.synchronize()
+        assert B.gs_status(h1) == 0 and B.gs_status(h2) == 0
+        assert st1.tolist() == st2.tolist() == [6, 0]
+        assert torch.allclose(l1, l2, rtol=1e-6, atol=0)
+        assert torch.allclose(m1, m2, rtol=1e-6, atol=1e-12) and torch.allclose(v1, v2, rtol=1e-6, atol=1e-20)
+        assert torch.allclose(ph1, ph2, rtol=0, atol=1e-6)
+        assert l1[5] < l1[0]
+    finally:
+        B.gs_destroy(h1)
+        B.gs_destroy(h2)
+
+
 def test_graph_adam_matches_eager():
     """The graph-replayed step (library Adam) follows the eager autograd
     path with torch's Adam: same losses to 1e-2 over 30 steps, and the loss
