@@ -435,7 +435,7 @@ __global__ void __launch_bounds__(kThreads, 1) gs_loss_kernel(const LossParams p
       cp_async_wait_all();
       if (valid && !adam) {
         float* gr = p.grad + static_cast<size_t>(idx) * N + t;
-#pragma unroll 1
+#pragma unroll 4
         for (int i = 0; i < 32; ++i) {
           float s, c;
           sincosf(sph[kThreads * i], &s, &c);
