@@ -7,13 +7,16 @@ Both the loss and its gradient come from one launch of the library
 (gs_loss_grad): the gradient is produced by the adjoint passes in the forward
 call and scaled by the incoming gradient in ``backward``. Adam itself is
 torch's optimiser acting on the phase tensor there; ``optimize_phase``
-replays one step (loss-and-gradient launch plus the library's Adam update) as
+replays optimiser steps (each one launch: loss, gradient and Adam update) as
 a CUDA graph.
 """
 
 from __future__ import annotations
 
 from . import _binding as B
+
+# optimiser steps captured in one graph by optimize_phase
+GRAPH_CHUNK = 16
 
 
 class LossContext:
@@ -131,12 +134,14 @@ def optimize_phase(target, phase0, steps: int = 200, lr: float = 0.05, betas=(0.
     before step k (and the final loss last).
 
     With ``graph`` (the default) the target is staged once (gs_loss_prepare)
-    and one step -- a single launch forming the loss and the gradient on the
+    and a step is a single launch forming the loss and the gradient on the
     staged target and applying the Adam update of gs_adam_step in place
-    (gs_loss_adam_prepared) -- is captured once as a CUDA graph and replayed
-    after three eager steps; the context then needs its own
-    (non-default) stream, and one is created when ``lctx`` is None. Otherwise
-    every step goes through the autograd function above and torch's Adam."""
+    (gs_loss_adam_prepared); after three eager steps, GRAPH_CHUNK consecutive
+    steps are captured once as a CUDA graph and replayed (the remainder runs
+    eagerly), every step writing its loss into the record on the device; the
+    context then needs its own (non-default) stream, and one is created when
+    ``lctx`` is None. Otherwise every step goes through the autograd function
+    above and torch's Adam."""
     import torch
 
     if lctx is None:
@@ -150,7 +155,6 @@ def optimize_phase(target, phase0, steps: int = 200, lr: float = 0.05, betas=(0.
         m = torch.zeros_like(phase)
         v = torch.zeros_like(phase)
         state = torch.zeros(2, dtype=torch.int32, device=phase.device)
-        loss = torch.zeros(1, dtype=torch.float64, device=phase.device)
         record = torch.zeros(steps + 1, dtype=torch.float64, device=phase.device)
         # the target is validated and staged once; every step runs only the
         # three transform passes on it
@@ -158,26 +162,35 @@ def optimize_phase(target, phase0, steps: int = 200, lr: float = 0.05, betas=(0.
         if rc != B.GS_OK:
             raise B.GSError(rc, "gs_loss_prepare")
 
-        def step():  # loss, gradient and Adam update in one launch
+        def step(loss_ptr):  # loss, gradient and Adam update in one launch
             rc = B.gs_loss_adam_prepared(lctx.handle, phase.data_ptr(), m.data_ptr(), v.data_ptr(), state.data_ptr(),
-                                         lr, betas[0], betas[1], eps, loss.data_ptr())
+                                         lr, betas[0], betas[1], eps, loss_ptr)
             if rc != B.GS_OK:
                 raise B.GSError(rc, "gs_loss_adam_prepared")
 
+        # eager steps write their loss straight into its record slot; the
+        # graph holds `chunk` consecutive steps writing into `lbuf`, copied
+        # into the record once per replay
+        rec = record.data_ptr()
         warm = 3
         for k in range(warm):
-            step()
-            record[k].copy_(loss[0])
+            step(rec + 8 * k)
+        chunk = min(GRAPH_CHUNK, steps - warm)
+        lbuf = torch.zeros(chunk, dtype=torch.float64, device=phase.device)
         g = torch.cuda.CUDAGraph()
         with torch.cuda.graph(g, stream=s):
-            step()
-        for k in range(warm, steps):
+            for j in range(chunk):
+                step(lbuf.data_ptr() + 8 * j)
+        k = warm
+        while k + chunk <= steps:
             g.replay()
-            record[k].copy_(loss[0])
-        rc = B.gs_loss_grad_prepared(lctx.handle, phase.data_ptr(), loss.data_ptr(), 0)
+            record[k:k + chunk].copy_(lbuf)
+            k += chunk
+        for k in range(k, steps):
+            step(rec + 8 * k)
+        rc = B.gs_loss_grad_prepared(lctx.handle, phase.data_ptr(), rec + 8 * steps, 0)
         if rc != B.GS_OK:
             raise B.GSError(rc, "gs_loss_grad_prepared")
-        record[steps].copy_(loss[0])
     torch.cuda.current_stream().wait_stream(s)
     keep = list(range(0, steps, record_every)) + [steps]
     return phase.detach(), record.cpu().numpy()[keep]

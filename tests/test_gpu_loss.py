@@ -199,6 +199,43 @@ def test_fused_adam_step_matches_separate_launches(n):
         B.gs_destroy(h2)
 
 
+@pytest.mark.parametrize("steps", [4, 40])
+def test_graph_chunks_match_single_launches(steps):
+    """optimize_phase's graph of consecutive steps (three eager steps, whole
+    chunks replayed, the remainder eager; 40 = 3 + 2 x 16 + 5) against the
+    same launches issued one at a time: bit-identical losses and phase."""
+    import torch
+
+    from paper_1302_0120_gb300 import _binding as B
+    from paper_1302_0120_gb300.differentiable import GRAPH_CHUNK, LossContext, optimize_phase
+
+    assert GRAPH_CHUNK == 16
+    n = 256
+    I = torch.from_numpy(normalized_target(27, n, 30)).cuda()
+    phi0 = torch.from_numpy(S.random_phase(28, n, n)).cuda()
+    lc = LossContext(n, stream=torch.cuda.Stream())
+    ph_g, loss_g = optimize_phase(I, phi0, steps=steps, lr=0.05, lctx=lc)
+    assert lc.status() == 0
+    h = B.gs_create(n, n)
+    try:
+        assert B.gs_loss_prepare(h, I.data_ptr()) == 0
+        ph = phi0.clone()
+        m, v = torch.zeros_like(ph), torch.zeros_like(ph)
+        st = torch.zeros(2, dtype=torch.int32, device="cuda")
+        rec = torch.zeros(steps + 1, dtype=torch.float64, device="cuda")
+        for k in range(steps):
+            assert B.gs_loss_adam_prepared(h, ph.data_ptr(), m.data_ptr(), v.data_ptr(), st.data_ptr(),
+                                           0.05, 0.9, 0.999, 1e-8, rec[k:].data_ptr()) == 0
+        assert B.gs_loss_grad_prepared(h, ph.data_ptr(), rec[steps:].data_ptr(), 0) == 0
+        assert B.gs_status(h) == 0
+        assert st.tolist() == [steps, 0]
+        assert np.array_equal(loss_g, rec.cpu().numpy())
+        assert torch.equal(ph_g, ph)
+    finally:
+        B.gs_destroy(h)
+        lc.close()
+
+
 def test_graph_adam_matches_eager():
     """The graph-replayed step (library Adam) follows the eager autograd
     path with torch's Adam: same losses to 1e-2 over 30 steps, and the loss
