@@ -430,6 +430,27 @@ int gs_loss_adam_prepared(gs_ctx* c, float* phase, float* m, float* v, int* stat
                           float beta2, float eps, double* loss_out);
 
 /*
+ * gs_loss_adam_run -- `steps` steps of the phase optimiser, each the step of
+ * gs_loss_adam_prepared, with up to 1024 steps per launch.
+ *
+ * The same arithmetic as `steps` calls of gs_loss_adam_prepared in a row
+ * (bit-identical losses, phase and moments), organised differently: within a
+ * launch the pass that applies a step's update also forms the next step's
+ * row transforms of exp(i phase), so a step costs two grid passes and two
+ * grid barriers instead of a launch of three passes.
+ *   phase, m, v, state, lr, beta1, beta2, eps   as gs_loss_adam_prepared.
+ *   steps      >= 1.
+ *   loss_out   device, double [steps]: loss_out[k] = L(phi) before step k.
+ * The phase, m, v and state must not be written by anyone else until the
+ * call's work on the context's stream is done. Asynchronous. Returns
+ * GS_EINVAL as gs_loss_adam_prepared does or for steps < 1; GS_ECUDA if a
+ * launch fails. A non-finite staged target writes NaN losses and leaves
+ * phase, moments and state unchanged (gs_status reports GS_ENUMERIC).
+ */
+int gs_loss_adam_run(gs_ctx* c, float* phase, float* m, float* v, int* state, float lr, float beta1, float beta2,
+                     float eps, int steps, double* loss_out);
+
+/*
  * gs_physical_error -- the physical error of a phase mask, Eq. (phys-error).
  *
  * Operation: for the field u = p exp(i phase) on the SLM (p from

@@ -50,6 +50,8 @@ SIGNATURES = {
     "gs_loss_grad_prepared": (_c_int, [_vp, _vp, _vp, _vp]),
     "gs_loss_adam_prepared": (_c_int, [_vp, _vp, _vp, _vp, _vp, ctypes.c_float, ctypes.c_float, ctypes.c_float,
                                        ctypes.c_float, _vp]),
+    "gs_loss_adam_run": (_c_int, [_vp, _vp, _vp, _vp, _vp, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                                  ctypes.c_float, _c_int, _vp]),
     "gs_set_slm_amplitude": (_c_int, [_vp, _vp]),
     "gs_test_barrier_timeout": (_c_int, [_vp, _c_int]),
     "gs_physical_error": (_c_int, [_vp, _vp, _vp, _vp]),
@@ -262,6 +264,13 @@ def gs_loss_adam_prepared(ctx: int, phase: int, m: int, v: int, state: int, lr: 
     """Enqueue one optimiser step (loss on the staged target, gradient, Adam update in place); returns the status code."""
     return lib().gs_loss_adam_prepared(_vp(ctx), _vp(phase), _vp(m), _vp(v), _vp(state), float(lr), float(beta1),
                                        float(beta2), float(eps), _vp(loss_out))
+
+
+def gs_loss_adam_run(ctx: int, phase: int, m: int, v: int, state: int, lr: float, beta1: float, beta2: float,
+                     eps: float, steps: int, loss_out: int) -> int:
+    """Enqueue `steps` optimiser steps (up to 1024 per launch); loss_out[k] is the loss before step k."""
+    return lib().gs_loss_adam_run(_vp(ctx), _vp(phase), _vp(m), _vp(v), _vp(state), float(lr), float(beta1),
+                                  float(beta2), float(eps), int(steps), _vp(loss_out))
 
 
 def gs_physical_error(ctx: int, target_intensity: int, phase: int, error_out: int) -> int:

@@ -718,6 +718,7 @@ struct AdamArgs {
   float* v;
   int* state;
   float lr, beta1, beta2, eps;
+  int steps;  // in this launch, 1 .. kMaxAdamStepsPerLaunch
 };
 
 int enqueue_loss(gs_ctx* c, const float* target_intensity, const float* phase, double* loss_out, float* grad_out,
@@ -732,6 +733,7 @@ int enqueue_loss(gs_ctx* c, const float* target_intensity, const float* phase, d
     p.beta1 = adam->beta1;
     p.beta2 = adam->beta2;
     p.eps = adam->eps;
+    p.steps = adam->steps;
   }
   p.mode = mode;
   // the fused and prepare launches stage their target over the previous one
@@ -789,8 +791,24 @@ int gs_loss_adam_prepared(gs_ctx* c, float* phase, float* m, float* v, int* stat
       loss_out == nullptr || c->nx != c->ny || gsk::uses_general(c->nx, c->ny) || !c->loss_prepared ||
       !(lr > 0.f) || !(beta1 >= 0.f && beta1 < 1.f) || !(beta2 >= 0.f && beta2 < 1.f) || !(eps > 0.f))
     return GS_EINVAL;
-  const AdamArgs a{phase, m, v, state, lr, beta1, beta2, eps};
+  const AdamArgs a{phase, m, v, state, lr, beta1, beta2, eps, 1};
   return enqueue_loss(c, nullptr, phase, loss_out, nullptr, nullptr, gsk::kLossStep, &a);
+}
+
+int gs_loss_adam_run(gs_ctx* c, float* phase, float* m, float* v, int* state, float lr, float beta1, float beta2,
+                     float eps, int steps, double* loss_out) {
+  if (c == nullptr || c->mixed || phase == nullptr || m == nullptr || v == nullptr || state == nullptr ||
+      loss_out == nullptr || steps < 1 || c->nx != c->ny || gsk::uses_general(c->nx, c->ny) || !c->loss_prepared ||
+      !(lr > 0.f) || !(beta1 >= 0.f && beta1 < 1.f) || !(beta2 >= 0.f && beta2 < 1.f) || !(eps > 0.f))
+    return GS_EINVAL;
+  for (int k0 = 0; k0 < steps;) {  // launches of at most kMaxAdamStepsPerLaunch steps
+    const int n = steps - k0 < gsk::kMaxAdamStepsPerLaunch ? steps - k0 : gsk::kMaxAdamStepsPerLaunch;
+    const AdamArgs a{phase, m, v, state, lr, beta1, beta2, eps, n};
+    const int rc = enqueue_loss(c, nullptr, phase, loss_out + k0, nullptr, nullptr, gsk::kLossStep, &a);
+    if (rc != GS_OK) return rc;
+    k0 += n;
+  }
+  return GS_OK;
 }
 
 int gs_physical_error(gs_ctx* c, const float* target_intensity, const float* phase, double* error_out) {

@@ -174,7 +174,7 @@ struct LossParams {
   const float* I;          // target intensity [n][n]
   const float* phi;        // phase [n][n]
   float* grad;             // dL/dphi [n][n], or null (loss only)
-  double* loss;            // [1]
+  double* loss;            // [steps]: the loss before each step
   double* phys;            // [2]: physical error (E_l, E_d), or null
   const float* p_slm;      // SLM amplitude [n][n], or null (p = 1)
   const double* energy;    // sum p^2 when p_slm is set
@@ -193,7 +193,13 @@ struct LossParams {
   float* v;
   int* state;
   float lr, beta1, beta2, eps;
+  // Adam steps in this launch (1 unless m is set): the gradient pass of a
+  // step also forms the next step's row transforms of exp(i phase).
+  int steps;
 };
+
+// Adam steps per launch of gs_loss_adam_run (a longer run is split).
+constexpr int kMaxAdamStepsPerLaunch = 1024;
 
 cudaError_t launch_loss(const LossParams& p, int grid, cudaStream_t s);
 cudaError_t launch_iterations(const Params& p, int grid, cudaStream_t s);

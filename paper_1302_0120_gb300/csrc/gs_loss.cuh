@@ -252,225 +252,261 @@ __global__ void __launch_bounds__(kThreads, 1) gs_loss_kernel(const LossParams p
       if (b == 0 && threadIdx.x == 0) {
         atomicCAS(p.status, 0, GS_ENUMERIC);
         const double nan = __longlong_as_double(0x7ff8000000000000ll);
-        p.loss[0] = nan;
+        for (int k = 0; k < (p.m != nullptr ? p.steps : 1); ++k) p.loss[k] = nan;
         if (p.phys) p.phys[0] = p.phys[1] = nan;
       }
       return;
     }
   }
 
-  // Pass 2 (columns): y = DFT_y(B) = F x; r = |y|^2/N - I; loss partial;
-  // B = swap(IDFT_y(r y)) for the adjoint.
   const bool adam = p.m != nullptr;  // the Adam update in place of the gradient output
   const bool want_grad = p.grad != nullptr || adam;  // the adjoint passes
   const bool want_phys = p.phys != nullptr;
-  float acc = 0.f, acc_l = 0.f, acc_d = 0.f;  // this thread's lines, FP32
-  {
-    const int lo = split(b, gridDim.x, L::NBLK);
-    const int hi = split(b + 1, gridDim.x, L::NBLK);
-    const bool gact = gidx < W;
-    const bool wact = ((threadIdx.x & ~31) >> LOGT) < W;
-    const int gq = gact ? gidx : 0;
-    for (int cb = lo; cb < hi; ++cb) {
-      __syncthreads();
-      if (threadIdx.x == 0) {
-        bulk_wait_read_all();
-        fence_proxy_async_smem();
-        mbar_arrive_expect_tx(&sh.mbar, L::BLOCK * 12u);
-        bulk_g2s(blk, p.B + static_cast<size_t>(cb) * L::BLOCK, L::BLOCK * 8u, &sh.mbar);
-        bulk_g2s(its, p.IT + static_cast<size_t>(cb) * L::BLOCK, L::BLOCK * 4u, &sh.mbar);
-        sh.pending = 1;
-        sh.pending_phase = mphase;
-      }
-      const bool landed = mbar_wait_bounded(&sh.mbar, mphase);
-      mphase ^= 1u;
-      if (!landed) {
-        loss_fail(p, GS_ETIMEOUT);
-      } else if (threadIdx.x == 0) {
-        sh.pending = 0;
-      }
-      if (wact) {
-        float2 v[32];
-#pragma unroll
-        for (int i = 0; i < 32; ++i) v[i] = blk[L::boff(t + T * i, gq)];
-        group_fft<LN>(v, grp, stw);
-        const float* icol = its + gq * N + t;
-        float* sa2 = reinterpret_cast<float*>(grp.sm) + t;  // |y|^2 for the physical error
-        float part = 0.f;
-#pragma unroll
-        for (int i = 0; i < 32; ++i) {
-          const float2 y = v[i];
-          const float a2 = y.x * y.x + y.y * y.y;
-          const float r = a2 * p.inv_n - icol[T * i];
-          part = fmaf(r, r, part);
-          if (want_phys) sa2[T * i] = a2;
-          v[i] = make_float2(r * y.y, r * y.x);  // swapped: the next forward DFT acts as the inverse
-        }
-        if (gact) acc += part;
-        if (want_phys) {  // Eq. (phys-error), once per call: a rolled loop
-          float el = 0.f, ed = 0.f;
-#pragma unroll 1
-          for (int i = 0; i < 32; ++i) {
-            const float ir = sa2[T * i] * ir_scale;  // reconstructed intensity
-            const float iv = icol[T * i];
-            if (iv > 0.f) {
-              const float it = iv * it_scale;
-              const float rel = fabsf(it - ir) / it;
-              if (rel - kTolLit > 0.f) el += kTolDark * rel / kTolLit - kTolDark;
-            } else if (ir - kTolDark > 0.f) {
-              ed += ir - kTolDark;
-            }
-          }
-          if (gact) {
-            acc_l += el;
-            acc_d += ed;
-          }
-          grp.sync();
-        }
-        if (want_grad) {
-          group_fft<LN>(v, grp, stw);
-          if (gact) {
-#pragma unroll
-            for (int i = 0; i < 32; ++i) blk[L::boff(t + T * i, gidx)] = v[i];
-          }
-        }
-      }
-      if (want_grad) {
+  // Adam steps of this launch; every block reads the step count before the
+  // last block to finish advances it
+  const int steps = adam ? p.steps : 1;
+  const int t_done = adam ? p.state[0] : 0;
+  for (int k = 0; k < steps; ++k) {
+    // Pass 2 (columns): y = DFT_y(B) = F x; r = |y|^2/N - I; loss partial;
+    // B = swap(IDFT_y(r y)) for the adjoint.
+    float acc = 0.f, acc_l = 0.f, acc_d = 0.f;  // this thread's lines, FP32
+    {
+      const int lo = split(b, gridDim.x, L::NBLK);
+      const int hi = split(b + 1, gridDim.x, L::NBLK);
+      const bool gact = gidx < W;
+      const bool wact = ((threadIdx.x & ~31) >> LOGT) < W;
+      const int gq = gact ? gidx : 0;
+      for (int cb = lo; cb < hi; ++cb) {
         __syncthreads();
         if (threadIdx.x == 0) {
+          bulk_wait_read_all();
           fence_proxy_async_smem();
-          bulk_s2g(p.B + static_cast<size_t>(cb) * L::BLOCK, blk, L::BLOCK * 8u);
-          bulk_commit();
+          mbar_arrive_expect_tx(&sh.mbar, L::BLOCK * 12u);
+          bulk_g2s(blk, p.B + static_cast<size_t>(cb) * L::BLOCK, L::BLOCK * 8u, &sh.mbar);
+          bulk_g2s(its, p.IT + static_cast<size_t>(cb) * L::BLOCK, L::BLOCK * 4u, &sh.mbar);
+          sh.pending = 1;
+          sh.pending_phase = mphase;
         }
-      }
-    }
-    if (want_grad && threadIdx.x == 0) bulk_wait_all();
-  }
-  {
-    const int G = gridDim.x;
-    // FP32 within the block, FP64 across blocks (below)
-    const double tot = block_sum_f(acc, sh);
-    if (threadIdx.x == 0) p.partials[kRowLoss * G + b] = tot;
-    if (want_phys) {
-      const double tl = block_sum_f(acc_l, sh);
-      if (threadIdx.x == 0) p.partials[kRowEl * G + b] = tl;
-      const double td = block_sum_f(acc_d, sh);
-      if (threadIdx.x == 0) p.partials[kRowEd * G + b] = td;
-    }
-  }
-  if (!loss_sync(p, target, sh)) {
-    if (threadIdx.x == 0 && sh.pending) mbar_wait_bounded(&sh.mbar, sh.pending_phase);
-    return;
-  }
-  if (b == 0 && threadIdx.x < 32) {
-    const int G = gridDim.x;
-    for (int row = kRowLoss; row <= (want_phys ? kRowEd : kRowLoss); ++row) {
-      double s = 0.0;
-      for (int c = threadIdx.x; c < G; c += 32) s += p.partials[row * G + c];
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-      if (threadIdx.x == 0) {
-        if (row == kRowLoss) p.loss[0] = s;
-        else p.phys[row - kRowEl] = s;
-      }
-    }
-  }
-  if (!want_grad) return;
-
-  // Pass 3 (rows): N z = IDFT_x(B), grad = 4 Im(conj(x) z) with x = exp(i phi);
-  // with the fused update, the Adam step of gs_adam_step on every element
-  // instead of its gradient output (the phase of a row is read into shared
-  // memory before the thread that owns each element updates it).
-  int adam_t = 0;
-  float adam_step = 0.f, adam_rb2 = 0.f;
-  if (adam) {
-    adam_t = p.state[0] + 1;
-    const float b1 = 1.f - powf(p.beta1, static_cast<float>(adam_t));
-    const float b2 = 1.f - powf(p.beta2, static_cast<float>(adam_t));
-    adam_step = p.lr / b1;
-    adam_rb2 = 1.f / sqrtf(b2);
-  }
-  {
-    const int lo = split(b, gridDim.x, N);
-    const int hi = split(b + 1, gridDim.x, N);
-    const float scale = 4.f * p.inv_n;
-    for (int base = lo; base < hi; base += NG) {
-      const int idx = base + gidx;
-      const bool valid = idx < hi;
-      const int ridx = valid ? idx : base;
-      float2 v[32];
-#pragma unroll
-      for (int i = 0; i < 32; ++i) v[i] = p.B[L::off(ridx, t + T * i)];
-      // phi (and p) of this row by cp.async into the field staging buffer
-      // (free in this pass), in flight behind the transform
-      float* sph = reinterpret_cast<float*>(blk) + threadIdx.x;
-      float* spp = sph + 32 * kThreads;
-      // the fused update with p = 1: the row's moments too, into the laser
-      // amplitude's buffer and the staged target's (free in this pass)
-      float* const smm = (adam && !p.p_slm) ? spp : nullptr;
-      float* const smv = (adam && !p.p_slm) ? its + threadIdx.x : nullptr;
-      {
-        const size_t r0 = static_cast<size_t>(ridx) * N + t;
-        const float* ph = p.phi + r0;
-#pragma unroll
-        for (int i = 0; i < 32; ++i) cp_async4(sph + kThreads * i, ph + T * i);
-        if (p.p_slm) {
-          const float* pp = p.p_slm + r0;
-#pragma unroll
-          for (int i = 0; i < 32; ++i) cp_async4(spp + kThreads * i, pp + T * i);
+        const bool landed = mbar_wait_bounded(&sh.mbar, mphase);
+        mphase ^= 1u;
+        if (!landed) {
+          loss_fail(p, GS_ETIMEOUT);
+        } else if (threadIdx.x == 0) {
+          sh.pending = 0;
         }
-        if (smm != nullptr) {
+        if (wact) {
+          float2 v[32];
+#pragma unroll
+          for (int i = 0; i < 32; ++i) v[i] = blk[L::boff(t + T * i, gq)];
+          group_fft<LN>(v, grp, stw);
+          const float* icol = its + gq * N + t;
+          float* sa2 = reinterpret_cast<float*>(grp.sm) + t;  // |y|^2 for the physical error
+          float part = 0.f;
 #pragma unroll
           for (int i = 0; i < 32; ++i) {
-            cp_async4(smm + kThreads * i, p.m + r0 + T * i);
-            cp_async4(smv + kThreads * i, p.v + r0 + T * i);
+            const float2 y = v[i];
+            const float a2 = y.x * y.x + y.y * y.y;
+            const float r = a2 * p.inv_n - icol[T * i];
+            part = fmaf(r, r, part);
+            if (want_phys) sa2[T * i] = a2;
+            v[i] = make_float2(r * y.y, r * y.x);  // swapped: the next forward DFT acts as the inverse
+          }
+          if (gact) acc += part;
+          if (want_phys) {  // Eq. (phys-error), once per call: a rolled loop
+            float el = 0.f, ed = 0.f;
+#pragma unroll 1
+            for (int i = 0; i < 32; ++i) {
+              const float ir = sa2[T * i] * ir_scale;  // reconstructed intensity
+              const float iv = icol[T * i];
+              if (iv > 0.f) {
+                const float it = iv * it_scale;
+                const float rel = fabsf(it - ir) / it;
+                if (rel - kTolLit > 0.f) el += kTolDark * rel / kTolLit - kTolDark;
+              } else if (ir - kTolDark > 0.f) {
+                ed += ir - kTolDark;
+              }
+            }
+            if (gact) {
+              acc_l += el;
+              acc_d += ed;
+            }
+            grp.sync();
+          }
+          if (want_grad) {
+            group_fft<LN>(v, grp, stw);
+            if (gact) {
+#pragma unroll
+              for (int i = 0; i < 32; ++i) blk[L::boff(t + T * i, gidx)] = v[i];
+            }
+          }
+        }
+        if (want_grad) {
+          __syncthreads();
+          if (threadIdx.x == 0) {
+            fence_proxy_async_smem();
+            bulk_s2g(p.B + static_cast<size_t>(cb) * L::BLOCK, blk, L::BLOCK * 8u);
+            bulk_commit();
           }
         }
       }
-      group_fft<LN>(v, grp, stw);  // = swap(N z)
-      // Im(conj(x) z) = x.re z.im - x.im z.re, with z = (v.y, v.x) / N
-      float2* su = grp.sm + t;
+      if (want_grad && threadIdx.x == 0) bulk_wait_all();
+    }
+    {
+      const int G = gridDim.x;
+      // FP32 within the block, FP64 across blocks (below)
+      const double tot = block_sum_f(acc, sh);
+      if (threadIdx.x == 0) p.partials[kRowLoss * G + b] = tot;
+      if (want_phys) {
+        const double tl = block_sum_f(acc_l, sh);
+        if (threadIdx.x == 0) p.partials[kRowEl * G + b] = tl;
+        const double td = block_sum_f(acc_d, sh);
+        if (threadIdx.x == 0) p.partials[kRowEd * G + b] = td;
+      }
+    }
+    if (!loss_sync(p, target, sh)) {
+      if (threadIdx.x == 0 && sh.pending) mbar_wait_bounded(&sh.mbar, sh.pending_phase);
+      return;
+    }
+    // Block 0 reads the partials here and reaches the barrier that lets the
+    // other blocks write the next step's partials only after that.
+    if (b == 0 && threadIdx.x < 32) {
+      const int G = gridDim.x;
+      for (int row = kRowLoss; row <= (want_phys ? kRowEd : kRowLoss); ++row) {
+        double s = 0.0;
+        for (int c = threadIdx.x; c < G; c += 32) s += p.partials[row * G + c];
 #pragma unroll
-      for (int i = 0; i < 32; ++i) su[T * i] = v[i];
-      cp_async_wait_all();
-      if (valid && !adam) {
-        float* gr = p.grad + static_cast<size_t>(idx) * N + t;
-#pragma unroll 4
-        for (int i = 0; i < 32; ++i) {
-          float s, c;
-          sincosf(sph[kThreads * i], &s, &c);
-          const float a = p.p_slm ? spp[kThreads * i] : 1.f;  // x = p exp(i phi)
-          const float2 w = su[T * i];
-          gr[T * i] = scale * a * (c * w.x - s * w.y);
-        }
-      } else if (valid) {
-        const size_t e0 = static_cast<size_t>(idx) * N + t;
-#pragma unroll 4
-        for (int i = 0; i < 32; ++i) {
-          float s, c;
-          sincosf(sph[kThreads * i], &s, &c);
-          const float a = p.p_slm ? spp[kThreads * i] : 1.f;
-          const float2 w = su[T * i];
-          const float g = scale * a * (c * w.x - s * w.y);
-          const size_t e = e0 + T * i;
-          const float m0 = smm ? smm[kThreads * i] : p.m[e];
-          const float v0 = smv ? smv[kThreads * i] : p.v[e];
-          const float mi = fmaf(p.beta1, m0, (1.f - p.beta1) * g);
-          const float vi = fmaf(p.beta2, v0, (1.f - p.beta2) * g * g);
-          p.m[e] = mi;
-          p.v[e] = vi;
-          p.phase[e] = sph[kThreads * i] - adam_step * mi / (sqrtf(vi) * adam_rb2 + p.eps);
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (threadIdx.x == 0) {
+          if (row == kRowLoss) p.loss[k] = s;
+          else p.phys[row - kRowEl] = s;
         }
       }
-      grp.sync();
     }
-  }
+    if (!want_grad) return;
+
+    // Pass 3 (rows): N z = IDFT_x(B), grad = 4 Im(conj(x) z) with x = exp(i phi);
+    // with the fused update, the Adam step of gs_adam_step on every element
+    // instead of its gradient output (the phase of a row is read into shared
+    // memory before the thread that owns each element updates it). When
+    // another step follows, the same pass also does its pass 1 for the rows it
+    // owns (the rows are split over the blocks as in pass 1): exp(i phi) of
+    // the updated phase, straight from the update, then B = DFT_x through a
+    // second turn of the transform loop.
+    const bool fuse = k + 1 < steps;
+    int adam_t = 0;
+    float adam_step = 0.f, adam_rb2 = 0.f;
+    if (adam) {
+      adam_t = t_done + 1 + k;
+      const float b1 = 1.f - powf(p.beta1, static_cast<float>(adam_t));
+      const float b2 = 1.f - powf(p.beta2, static_cast<float>(adam_t));
+      adam_step = p.lr / b1;
+      adam_rb2 = 1.f / sqrtf(b2);
+    }
+    {
+      const int lo = split(b, gridDim.x, N);
+      const int hi = split(b + 1, gridDim.x, N);
+      const float scale = 4.f * p.inv_n;
+      for (int base = lo; base < hi; base += NG) {
+        const int idx = base + gidx;
+        const bool valid = idx < hi;
+        const int ridx = valid ? idx : base;
+        float2 v[32];
+#pragma unroll
+        for (int i = 0; i < 32; ++i) v[i] = p.B[L::off(ridx, t + T * i)];
+        // phi (and p) of this row by cp.async into the field staging buffer
+        // (free in this pass), in flight behind the transform
+        float* sph = reinterpret_cast<float*>(blk) + threadIdx.x;
+        float* spp = sph + 32 * kThreads;
+        // the fused update with p = 1: the row's moments too, into the laser
+        // amplitude's buffer and the staged target's (free in this pass)
+        float* const smm = (adam && !p.p_slm) ? spp : nullptr;
+        float* const smv = (adam && !p.p_slm) ? its + threadIdx.x : nullptr;
+        {
+          const size_t r0 = static_cast<size_t>(ridx) * N + t;
+          const float* ph = p.phi + r0;
+#pragma unroll
+          for (int i = 0; i < 32; ++i) cp_async4(sph + kThreads * i, ph + T * i);
+          if (p.p_slm) {
+            const float* pp = p.p_slm + r0;
+#pragma unroll
+            for (int i = 0; i < 32; ++i) cp_async4(spp + kThreads * i, pp + T * i);
+          }
+          if (smm != nullptr) {
+#pragma unroll
+            for (int i = 0; i < 32; ++i) {
+              cp_async4(smm + kThreads * i, p.m + r0 + T * i);
+              cp_async4(smv + kThreads * i, p.v + r0 + T * i);
+            }
+          }
+        }
+        // one copy of the transform for both turns (instruction fetch is this
+        // kernel's top stall)
+#pragma unroll 1
+        for (int h = 0; h < (fuse ? 2 : 1); ++h) {
+          group_fft<LN>(v, grp, stw);  // h = 0: swap(N z); h = 1: the next step's row DFT
+          if (h == 1) {
+            if (valid) {
+#pragma unroll
+              for (int i = 0; i < 32; ++i) p.B[L::off(idx, t + T * i)] = v[i];
+            }
+            break;
+          }
+          // Im(conj(x) z) = x.re z.im - x.im z.re, with z = (v.y, v.x) / N
+          float2* su = grp.sm + t;
+#pragma unroll
+          for (int i = 0; i < 32; ++i) su[T * i] = v[i];
+          cp_async_wait_all();
+          if (valid && !adam) {
+            float* gr = p.grad + static_cast<size_t>(idx) * N + t;
+#pragma unroll 4
+            for (int i = 0; i < 32; ++i) {
+              float s, c;
+              sincosf(sph[kThreads * i], &s, &c);
+              const float a = p.p_slm ? spp[kThreads * i] : 1.f;  // x = p exp(i phi)
+              const float2 w = su[T * i];
+              gr[T * i] = scale * a * (c * w.x - s * w.y);
+            }
+          } else if (valid) {
+            const size_t e0 = static_cast<size_t>(idx) * N + t;
+#pragma unroll 4
+            for (int i = 0; i < 32; ++i) {
+              float s, c;
+              sincosf(sph[kThreads * i], &s, &c);
+              const float a = p.p_slm ? spp[kThreads * i] : 1.f;
+              const float2 w = su[T * i];
+              const float g = scale * a * (c * w.x - s * w.y);
+              const size_t e = e0 + T * i;
+              const float m0 = smm ? smm[kThreads * i] : p.m[e];
+              const float v0 = smv ? smv[kThreads * i] : p.v[e];
+              const float mi = fmaf(p.beta1, m0, (1.f - p.beta1) * g);
+              const float vi = fmaf(p.beta2, v0, (1.f - p.beta2) * g * g);
+              p.m[e] = mi;
+              p.v[e] = vi;
+              const float ph = sph[kThreads * i] - adam_step * mi / (sqrtf(vi) * adam_rb2 + p.eps);
+              p.phase[e] = ph;
+              if (fuse) {  // x = p exp(i phi) of the next step, in place of w
+                sincosf(ph, &s, &c);
+                su[T * i] = make_float2(a * c, a * s);
+              }
+            }
+          }
+          if (fuse) {  // a group with no row of its own transforms what it holds and stores nothing
+#pragma unroll
+            for (int i = 0; i < 32; ++i) v[i] = su[T * i];
+            grp.sync();
+          }
+        }
+        grp.sync();
+      }
+    }
+    if (fuse && !loss_sync(p, target, sh)) return;
+  }  // steps
   if (adam) {  // the last block to finish advances the step count (every block has read it)
     __syncthreads();
     if (threadIdx.x == 0) {
       __threadfence();
       if (atomicAdd(p.state + 1, 1) == static_cast<int>(gridDim.x) - 1) {
-        p.state[0] = adam_t;
+        p.state[0] = t_done + steps;
         p.state[1] = 0;
       }
     }

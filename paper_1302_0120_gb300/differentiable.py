@@ -7,16 +7,13 @@ Both the loss and its gradient come from one launch of the library
 (gs_loss_grad): the gradient is produced by the adjoint passes in the forward
 call and scaled by the incoming gradient in ``backward``. Adam itself is
 torch's optimiser acting on the phase tensor there; ``optimize_phase``
-replays optimiser steps (each one launch: loss, gradient and Adam update) as
-a CUDA graph.
+runs the library's own optimiser steps instead (loss, gradient and Adam
+update, many steps per launch).
 """
 
 from __future__ import annotations
 
 from . import _binding as B
-
-# optimiser steps captured in one graph by optimize_phase
-GRAPH_CHUNK = 16
 
 
 class LossContext:
@@ -129,27 +126,25 @@ def intensity_loss(phase, target, lctx: LossContext):
 
 
 def optimize_phase(target, phase0, steps: int = 200, lr: float = 0.05, betas=(0.9, 0.999), eps: float = 1e-8,
-                   lctx: LossContext | None = None, record_every: int = 1, graph: bool = True):
+                   lctx: LossContext | None = None, record_every: int = 1, fused: bool = True):
     """Adam on the phase. Returns (phase, losses) with losses[k] the loss
     before step k (and the final loss last).
 
-    With ``graph`` (the default) the target is staged once (gs_loss_prepare)
-    and a step is a single launch forming the loss and the gradient on the
-    staged target and applying the Adam update of gs_adam_step in place
-    (gs_loss_adam_prepared); after three eager steps, GRAPH_CHUNK consecutive
-    steps are captured once as a CUDA graph and replayed (the remainder runs
-    eagerly), every step writing its loss into the record on the device; the
-    context then needs its own (non-default) stream, and one is created when
-    ``lctx`` is None. Otherwise every step goes through the autograd function
-    above and torch's Adam."""
+    With ``fused`` (the default) the target is staged once (gs_loss_prepare)
+    and the library runs every step (gs_loss_adam_run: the loss and the
+    gradient on the staged target with the Adam update of gs_adam_step
+    applied in the gradient pass, all steps in one launch of up to 1024),
+    writing each step's loss into the record on the device. Otherwise every
+    step goes through the autograd function above and torch's Adam."""
     import torch
 
     if lctx is None:
-        lctx = LossContext(phase0.shape[-1], stream=torch.cuda.Stream() if graph else None)
-    if not graph or lctx.stream.cuda_stream == 0 or steps < 4:
+        lctx = LossContext(phase0.shape[-1])
+    if not fused:
         return _optimize_eager(target, phase0, steps, lr, betas, eps, lctx, record_every)
     s = lctx.stream
-    s.wait_stream(torch.cuda.current_stream())
+    cur = torch.cuda.current_stream(phase0.device)
+    s.wait_stream(cur)
     with torch.cuda.stream(s):
         phase = phase0.detach().clone()
         m = torch.zeros_like(phase)
@@ -157,41 +152,20 @@ def optimize_phase(target, phase0, steps: int = 200, lr: float = 0.05, betas=(0.
         state = torch.zeros(2, dtype=torch.int32, device=phase.device)
         record = torch.zeros(steps + 1, dtype=torch.float64, device=phase.device)
         # the target is validated and staged once; every step runs only the
-        # three transform passes on it
+        # transform passes on it
         rc = B.gs_loss_prepare(lctx.handle, target.data_ptr())
         if rc != B.GS_OK:
             raise B.GSError(rc, "gs_loss_prepare")
-
-        def step(loss_ptr):  # loss, gradient and Adam update in one launch
-            rc = B.gs_loss_adam_prepared(lctx.handle, phase.data_ptr(), m.data_ptr(), v.data_ptr(), state.data_ptr(),
-                                         lr, betas[0], betas[1], eps, loss_ptr)
+        if steps > 0:
+            rc = B.gs_loss_adam_run(lctx.handle, phase.data_ptr(), m.data_ptr(), v.data_ptr(), state.data_ptr(),
+                                    lr, betas[0], betas[1], eps, steps, record.data_ptr())
             if rc != B.GS_OK:
-                raise B.GSError(rc, "gs_loss_adam_prepared")
-
-        # eager steps write their loss straight into its record slot; the
-        # graph holds `chunk` consecutive steps writing into `lbuf`, copied
-        # into the record once per replay
-        rec = record.data_ptr()
-        warm = 3
-        for k in range(warm):
-            step(rec + 8 * k)
-        chunk = min(GRAPH_CHUNK, steps - warm)
-        lbuf = torch.zeros(chunk, dtype=torch.float64, device=phase.device)
-        g = torch.cuda.CUDAGraph()
-        with torch.cuda.graph(g, stream=s):
-            for j in range(chunk):
-                step(lbuf.data_ptr() + 8 * j)
-        k = warm
-        while k + chunk <= steps:
-            g.replay()
-            record[k:k + chunk].copy_(lbuf)
-            k += chunk
-        for k in range(k, steps):
-            step(rec + 8 * k)
-        rc = B.gs_loss_grad_prepared(lctx.handle, phase.data_ptr(), rec + 8 * steps, 0)
+                raise B.GSError(rc, "gs_loss_adam_run")
+        rc = B.gs_loss_grad_prepared(lctx.handle, phase.data_ptr(), record.data_ptr() + 8 * steps, 0)
         if rc != B.GS_OK:
             raise B.GSError(rc, "gs_loss_grad_prepared")
-    torch.cuda.current_stream().wait_stream(s)
+    cur.wait_stream(s)
+    phase.record_stream(cur)  # allocated on the context's stream, used on the caller's
     keep = list(range(0, steps, record_every)) + [steps]
     return phase.detach(), record.cpu().numpy()[keep]
 

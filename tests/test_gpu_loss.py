@@ -199,45 +199,128 @@ def test_fused_adam_step_matches_separate_launches(n):
         B.gs_destroy(h2)
 
 
-@pytest.mark.parametrize("steps", [4, 40])
-def test_graph_chunks_match_single_launches(steps):
-    """optimize_phase's graph of consecutive steps (three eager steps, whole
-    chunks replayed, the remainder eager; 40 = 3 + 2 x 16 + 5) against the
-    same launches issued one at a time: bit-identical losses and phase."""
+def single_launch_steps(h, I, phi0, steps, n):
+    """`steps` gs_loss_adam_prepared launches from phi0 on the staged target I,
+    then the final loss: (losses, phase, m, v, state) on the host."""
     import torch
 
     from paper_1302_0120_gb300 import _binding as B
-    from paper_1302_0120_gb300.differentiable import GRAPH_CHUNK, LossContext, optimize_phase
 
-    assert GRAPH_CHUNK == 16
-    n = 256
+    assert B.gs_loss_prepare(h, I.data_ptr()) == 0
+    ph = phi0.clone()
+    m, v = torch.zeros_like(ph), torch.zeros_like(ph)
+    st = torch.zeros(2, dtype=torch.int32, device="cuda")
+    rec = torch.zeros(steps + 1, dtype=torch.float64, device="cuda")
+    for k in range(steps):
+        assert B.gs_loss_adam_prepared(h, ph.data_ptr(), m.data_ptr(), v.data_ptr(), st.data_ptr(),
+                                       0.05, 0.9, 0.999, 1e-8, rec[k:].data_ptr()) == 0
+    assert B.gs_loss_grad_prepared(h, ph.data_ptr(), rec[steps:].data_ptr(), 0) == 0
+    assert B.gs_status(h) == 0
+    return rec.cpu().numpy(), ph, m, v, st.tolist()
+
+
+@pytest.mark.parametrize("n,steps", [(256, 1), (256, 2), (256, 40), (1024, 12)])
+def test_fused_run_matches_single_launches(n, steps):
+    """optimize_phase (gs_loss_adam_run: all steps in one launch, each step's
+    gradient pass forming the next step's row transforms) against the same
+    steps as single gs_loss_adam_prepared launches: bit-identical losses and
+    phase."""
+    import torch
+
+    from paper_1302_0120_gb300 import _binding as B
+    from paper_1302_0120_gb300.differentiable import LossContext, optimize_phase
+
     I = torch.from_numpy(normalized_target(27, n, 30)).cuda()
     phi0 = torch.from_numpy(S.random_phase(28, n, n)).cuda()
     lc = LossContext(n, stream=torch.cuda.Stream())
-    ph_g, loss_g = optimize_phase(I, phi0, steps=steps, lr=0.05, lctx=lc)
+    ph_f, loss_f = optimize_phase(I, phi0, steps=steps, lr=0.05, lctx=lc)
     assert lc.status() == 0
     h = B.gs_create(n, n)
     try:
-        assert B.gs_loss_prepare(h, I.data_ptr()) == 0
-        ph = phi0.clone()
-        m, v = torch.zeros_like(ph), torch.zeros_like(ph)
-        st = torch.zeros(2, dtype=torch.int32, device="cuda")
-        rec = torch.zeros(steps + 1, dtype=torch.float64, device="cuda")
-        for k in range(steps):
-            assert B.gs_loss_adam_prepared(h, ph.data_ptr(), m.data_ptr(), v.data_ptr(), st.data_ptr(),
-                                           0.05, 0.9, 0.999, 1e-8, rec[k:].data_ptr()) == 0
-        assert B.gs_loss_grad_prepared(h, ph.data_ptr(), rec[steps:].data_ptr(), 0) == 0
-        assert B.gs_status(h) == 0
-        assert st.tolist() == [steps, 0]
-        assert np.array_equal(loss_g, rec.cpu().numpy())
-        assert torch.equal(ph_g, ph)
+        rec, ph, _, _, st = single_launch_steps(h, I, phi0, steps, n)
+        assert st == [steps, 0]
+        assert np.array_equal(loss_f, rec)
+        assert torch.equal(ph_f, ph)
     finally:
         B.gs_destroy(h)
         lc.close()
 
 
-def test_graph_adam_matches_eager():
-    """The graph-replayed step (library Adam) follows the eager autograd
+def test_adam_run_splits_long_runs():
+    """gs_loss_adam_run over more steps than one launch takes (1024): the
+    same losses, phase, moments and step count as single launches, bit for
+    bit; a second run continues from the state the first left."""
+    import torch
+
+    from paper_1302_0120_gb300 import _binding as B
+
+    n, steps = 64, 1030
+    I = torch.from_numpy(normalized_target(29, n, 6)).cuda()
+    phi0 = torch.from_numpy(S.random_phase(30, n, n)).cuda()
+    h1, h2 = B.gs_create(n, n), B.gs_create(n, n)
+    try:
+        rec, ph, m, v, st = single_launch_steps(h1, I, phi0, steps, n)
+        assert B.gs_loss_prepare(h2, I.data_ptr()) == 0
+        ph2 = phi0.clone()
+        m2, v2 = torch.zeros_like(ph2), torch.zeros_like(ph2)
+        st2 = torch.zeros(2, dtype=torch.int32, device="cuda")
+        rec2 = torch.zeros(steps + 1, dtype=torch.float64, device="cuda")
+        args = (ph2.data_ptr(), m2.data_ptr(), v2.data_ptr(), st2.data_ptr(), 0.05, 0.9, 0.999, 1e-8)
+        assert B.gs_loss_adam_run(h2, *args, 1000, rec2.data_ptr()) == 0
+        assert B.gs_loss_adam_run(h2, *args, 30, rec2[1000:].data_ptr()) == 0
+        assert B.gs_loss_grad_prepared(h2, ph2.data_ptr(), rec2[steps:].data_ptr(), 0) == 0
+        assert B.gs_status(h2) == 0
+        assert st2.tolist() == st == [steps, 0]
+        assert np.array_equal(rec2.cpu().numpy(), rec)
+        assert torch.equal(ph2, ph) and torch.equal(m2, m) and torch.equal(v2, v)
+        assert rec[-1] < 0.5 * rec[0]
+        # the same steps as one call, split by the library into two launches
+        ph3, m3, v3 = phi0.clone(), torch.zeros_like(ph2), torch.zeros_like(ph2)
+        st3 = torch.zeros(2, dtype=torch.int32, device="cuda")
+        rec3 = torch.zeros(steps, dtype=torch.float64, device="cuda")
+        assert B.gs_loss_adam_run(h2, ph3.data_ptr(), m3.data_ptr(), v3.data_ptr(), st3.data_ptr(), 0.05, 0.9, 0.999,
+                                  1e-8, steps, rec3.data_ptr()) == 0
+        assert B.gs_status(h2) == 0
+        assert st3.tolist() == [steps, 0]
+        assert np.array_equal(rec3.cpu().numpy(), rec[:steps]) and torch.equal(ph3, ph)
+        # arguments the call refuses
+        assert B.gs_loss_adam_run(h2, *args, 0, rec2.data_ptr()) == B.GS_EINVAL
+        assert B.gs_loss_adam_run(h2, *args, 3, 0) == B.GS_EINVAL
+    finally:
+        B.gs_destroy(h1)
+        B.gs_destroy(h2)
+
+
+def test_adam_run_nonfinite_target():
+    """A staged target with a NaN: every loss of the run is NaN, the phase,
+    moments and step count are left as they were, and the status says so."""
+    import torch
+
+    from paper_1302_0120_gb300 import _binding as B
+
+    n = 64
+    I = normalized_target(31, n, 6)
+    I[3, 9] = np.nan
+    It = torch.from_numpy(I).cuda()
+    phi0 = torch.from_numpy(S.random_phase(32, n, n)).cuda()
+    h = B.gs_create(n, n)
+    try:
+        assert B.gs_loss_prepare(h, It.data_ptr()) == 0
+        ph = phi0.clone()
+        m, v = torch.zeros_like(ph), torch.zeros_like(ph)
+        st = torch.tensor([5, 0], dtype=torch.int32, device="cuda")
+        rec = torch.zeros(7, dtype=torch.float64, device="cuda")
+        assert B.gs_loss_adam_run(h, ph.data_ptr(), m.data_ptr(), v.data_ptr(), st.data_ptr(), 0.05, 0.9, 0.999,
+                                  1e-8, 7, rec.data_ptr()) == 0
+        assert B.gs_status(h) == B.GS_ENUMERIC
+        assert np.all(np.isnan(rec.cpu().numpy()))
+        assert torch.equal(ph, phi0) and not m.any() and not v.any() and st.tolist() == [5, 0]
+    finally:
+        B.gs_destroy(h)
+
+
+def test_fused_adam_matches_eager():
+    """The library's fused steps (its own Adam) follow the eager autograd
     path with torch's Adam: same losses to 1e-2 over 30 steps, and the loss
     falls."""
     import torch
@@ -250,7 +333,7 @@ def test_graph_adam_matches_eager():
     lc_g = LossContext(n, stream=torch.cuda.Stream())
     ph_g, loss_g = optimize_phase(I, phi0, steps=30, lr=0.05, lctx=lc_g)
     lc_e = LossContext(n)
-    ph_e, loss_e = optimize_phase(I, phi0, steps=30, lr=0.05, lctx=lc_e, graph=False)
+    ph_e, loss_e = optimize_phase(I, phi0, steps=30, lr=0.05, lctx=lc_e, fused=False)
     assert lc_g.status() == 0 and lc_e.status() == 0
     assert loss_g.shape == loss_e.shape == (31,)
     assert np.allclose(loss_g, loss_e, rtol=1e-2, atol=0), np.max(np.abs(loss_g / loss_e - 1))
@@ -260,11 +343,12 @@ def test_graph_adam_matches_eager():
 
 
 def test_side_stream_eager_steps_match_current_stream():
-    """optimize_phase with its defaults and fewer than four steps runs the
-    eager path on a context with its own stream while torch's Adam writes the
-    phase on the current stream: the two are ordered, so the result equals an
-    eager run whose context uses the current stream. A user-built context on
-    a side stream gives the same loss as one on the current stream."""
+    """The eager path on a context with its own stream, while torch's Adam
+    writes the phase on the current stream: the two are ordered, so the
+    result equals an eager run whose context uses the current stream. The
+    fused path on a side stream equals the fused path on the current one. A
+    user-built context on a side stream gives the same loss as one on the
+    current stream."""
     import torch
 
     from paper_1302_0120_gb300.differentiable import LossContext, intensity_loss, optimize_phase
@@ -272,12 +356,18 @@ def test_side_stream_eager_steps_match_current_stream():
     n = 256
     I = torch.from_numpy(normalized_target(17, n, 30)).cuda()
     phi0 = torch.from_numpy(S.random_phase(18, n, n)).cuda()
-    ph_side, loss_side = optimize_phase(I, phi0, steps=3, lr=0.05)  # graph=True, lctx=None
+    lc_s = LossContext(n, stream=torch.cuda.Stream())
+    ph_side, loss_side = optimize_phase(I, phi0, steps=3, lr=0.05, lctx=lc_s, fused=False)
     lc_cur = LossContext(n)
-    ph_cur, loss_cur = optimize_phase(I, phi0, steps=3, lr=0.05, lctx=lc_cur, graph=False)
-    assert lc_cur.status() == 0
+    ph_cur, loss_cur = optimize_phase(I, phi0, steps=3, lr=0.05, lctx=lc_cur, fused=False)
+    assert lc_cur.status() == 0 and lc_s.status() == 0
     assert np.array_equal(loss_side, loss_cur)
     assert torch.equal(ph_side, ph_cur)
+    ph_fs, loss_fs = optimize_phase(I, phi0, steps=5, lr=0.05, lctx=lc_s)
+    ph_fc, loss_fc = optimize_phase(I, phi0, steps=5, lr=0.05)  # lctx None: the current stream
+    assert lc_s.status() == 0
+    assert np.array_equal(loss_fs, loss_fc) and torch.equal(ph_fs, ph_fc)
+    lc_s.close()
     lc_side = LossContext(n, stream=torch.cuda.Stream())
     for _ in range(3):
         phi = phi0 * 1.01  # written on the current stream just before the call
