@@ -476,11 +476,12 @@ def run_gpu(args):
             raise RuntimeError("loss kernel failed")
         differentiable = {"n": nx, "spots": 100, "adam_steps": args.adam_steps, "lr": 0.05,
                           "ms_per_step": round(e0.elapsed_time(e1) / args.adam_steps, 4),
-                          # the step's 64 B/px (one launch: phase twice, the field three
-                          # times each way, the staged target, the moments read and
-                          # written, the phase written) over the whole step
+                          # a step's 60 B/px (the column pass: the field both ways and
+                          # the staged target; the row pass: the field read, the phase
+                          # and both moments read and written, the next step's row
+                          # transforms written) over the whole call
                           "loss_kernel_gbs_lower_bound": round(
-                              64 * n * args.adam_steps / (e0.elapsed_time(e1) * 1e6), 1),
+                              60 * n * args.adam_steps / (e0.elapsed_time(e1) * 1e6), 1),
                           "loss_first": float(losses[0]), "loss_last": float(losses[-1])}
         lc.close()
 
