@@ -12,6 +12,10 @@
 //   rows     N z = IDFT_x(B); grad = 4 Im(conj(x) z)            (adjoint)
 // The target is staged like the amplitude of the iteration kernel
 // (transposed [nx][ny], read per column block). FP64 only for the sums.
+// With the Adam update fused into the third pass, one launch can run many
+// optimiser steps: the third pass of a step, which owns the same rows as the
+// first, also forms the next step's x = exp(i phi) and B = DFT_x(x), so every
+// step after the first is a column pass and a row pass.
 // With a laser amplitude p on the SLM the field is x = p exp(i phi); the
 // gradient formula is unchanged (dy_k/dphi_j = F_kj i x_j still holds).
 //
@@ -74,7 +78,7 @@ static __device__ bool loss_sync(const LossParams& p, unsigned& target, Shared& 
 // then the three passes (one call does everything). kLossPrepare: validate
 // and stage the target only, and reduce its statistics into row kRowStaged.
 // kLossStep: the three passes on the staged target (the target of the last
-// kLossPrepare launch).
+// kLossPrepare launch); with the Adam update, p.steps optimiser steps.
 
 template <int LN, int MODE>
 __global__ void __launch_bounds__(kThreads, 1) gs_loss_kernel(const LossParams p) {
