@@ -104,6 +104,10 @@ def test_null_context_calls(lib):
     n = ctypes.c_int(0)
     assert lib.gs_get_trace(None, None, 0, ctypes.byref(n), ctypes.byref(n)) == B.GS_EINVAL
     assert B.gs_adam_step(0, 0, 0, 0, 16, 0, 0.05, 0.9, 0.999, 1e-8) == B.GS_EINVAL
+    assert B.gs_loss_prepare(0, 0) == B.GS_EINVAL
+    assert B.gs_loss_grad_prepared(0, 0, 0, 0) == B.GS_EINVAL
+    assert B.gs_loss_adam_prepared(0, 0, 0, 0, 0, 0.05, 0.9, 0.999, 1e-8, 0) == B.GS_EINVAL
+    assert B.gs_loss_adam_run(0, 0, 0, 0, 0, 0.05, 0.9, 0.999, 1e-8, 10, 0) == B.GS_EINVAL
 
 
 def test_create_mixed_validates_before_cuda(lib):
