@@ -138,6 +138,8 @@ def optimize_phase(target, phase0, steps: int = 200, lr: float = 0.05, betas=(0.
     step goes through the autograd function above and torch's Adam."""
     import torch
 
+    if steps < 0 or record_every < 1:
+        raise ValueError("steps must be >= 0 and record_every >= 1")
     if lctx is None:
         lctx = LossContext(phase0.shape[-1])
     if not fused:

@@ -156,3 +156,11 @@ def test_missing_library_fails_loudly(monkeypatch, tmp_path):
     monkeypatch.setattr(B, "LIB_PATH", str(tmp_path / "nope.so"))
     with pytest.raises(RuntimeError, match="no CPU fallback"):
         B.lib()
+
+
+def test_optimize_phase_validates_before_cuda():
+    from paper_1302_0120_gb300.differentiable import optimize_phase
+
+    for kw in ({"steps": -1}, {"steps": 5, "record_every": 0}):
+        with pytest.raises(ValueError):
+            optimize_phase(None, None, **kw)
